@@ -1,0 +1,253 @@
+"""Python access to the FP64 CPU oracle (test infrastructure only).
+
+The oracle is plain C in ``vpath_oracle.c``.  Only the tests,
+``__graft_entry__.smoke()`` and the ``cpu_baseline`` / ``--impl reference``
+legs of ``bench.py`` import this package; the product path (the CUDA library
+and its binding) never does.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "vpath_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "libvpath_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle (gcc, OpenMP, no FMA contraction)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        tmp = _LIB_PATH + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-O2", "-std=c11", "-fopenmp", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+               _SRC, "-o", tmp, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+class OrSystem(C.Structure):
+    _fields_ = [
+        ("n", C.c_int32), ("n_solute", C.c_int32), ("n_cv", C.c_int32), ("n_types", C.c_int32),
+        ("mass", C.c_void_p), ("charge", C.c_void_p), ("sigma", C.c_void_p), ("epsilon", C.c_void_p),
+        ("gamma", C.c_void_p), ("type", C.c_void_p),
+        ("n_bonds", C.c_int32), ("bonds", C.c_void_p), ("bond_r0", C.c_void_p), ("bond_k", C.c_void_p),
+        ("n_angles", C.c_int32), ("angles", C.c_void_p), ("angle_t0", C.c_void_p), ("angle_k", C.c_void_p),
+        ("n_excl", C.c_int32), ("excl", C.c_void_p),
+        ("box", C.c_double), ("native", C.c_void_p),
+    ]
+
+
+class OrParams(C.Structure):
+    _fields_ = [
+        ("dt", C.c_double), ("temperature", C.c_double), ("gamma", C.c_double), ("r_cut", C.c_double),
+        ("skin", C.c_double), ("nstlist", C.c_int32),
+        ("eps_rf", C.c_double), ("k_ratchet", C.c_double), ("cv_r0", C.c_double), ("cv_r_switch", C.c_double),
+        ("cv_r_cut", C.c_double), ("cv_min_sep", C.c_int32),
+    ]
+
+
+class OrRunOut(C.Structure):
+    _fields_ = [
+        ("z", C.c_void_p), ("zm", C.c_void_p), ("a", C.c_void_p), ("phi_step", C.c_void_p),
+        ("frames", C.c_void_p), ("record_every", C.c_int32),
+        ("pos_out", C.c_void_p), ("vel_out", C.c_void_p),
+        ("Phi", C.c_double), ("energies", C.c_double * 6), ("force_out", C.c_void_p),
+    ]
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = build()
+            L = C.CDLL(path)
+            vp = C.c_void_p
+            L.or_philox4x32_10.argtypes = [vp, vp, vp]
+            L.or_normal3.argtypes = [C.c_uint64, C.c_int64, C.c_int64, C.c_uint32, vp]
+            L.or_contact.argtypes = [C.c_double, C.c_double, C.c_double, C.c_double, vp]
+            L.or_cv.argtypes = [vp, vp, C.c_int32, C.c_double, C.c_double, C.c_double, C.c_double, C.c_int32, vp]
+            L.or_cv.restype = C.c_double
+            L.or_pairlist.argtypes = [C.POINTER(OrSystem), vp, C.c_double, vp, C.c_int64]
+            L.or_pairlist.restype = C.c_int64
+            L.or_forces.argtypes = [C.POINTER(OrSystem), C.POINTER(OrParams), vp, C.c_int32, vp, vp]
+            L.or_forces.restype = C.c_int
+            L.or_initial_velocities.argtypes = [C.POINTER(OrSystem), C.c_double, C.c_uint64, vp]
+            L.or_run.argtypes = [C.POINTER(OrSystem), C.POINTER(OrParams), C.c_uint64, vp, vp, C.c_int32,
+                                 C.POINTER(OrRunOut)]
+            L.or_run.restype = C.c_int
+            L.or_phi_frames.argtypes = [C.POINTER(OrSystem), C.POINTER(OrParams), vp, C.c_int32, vp, vp, vp]
+            L.or_phi_frames.restype = C.c_double
+            L.or_num_threads.restype = C.c_int32
+            L.or_set_num_threads.argtypes = [C.c_int32]
+            _lib = L
+    return _lib
+
+
+def _p(a):
+    return None if a is None else a.ctypes.data
+
+
+class _Sys:
+    """Keeps the numpy arrays behind an OrSystem alive."""
+
+    def __init__(self, s):
+        self.keep = dict(
+            mass=np.ascontiguousarray(s.mass, np.float64), charge=np.ascontiguousarray(s.charge, np.float64),
+            sigma=np.ascontiguousarray(s.sigma, np.float64), epsilon=np.ascontiguousarray(s.epsilon, np.float64),
+            gamma=None if s.gamma is None else np.ascontiguousarray(s.gamma, np.float64),
+            type=np.ascontiguousarray(s.lj_type, np.int32),
+            bonds=np.ascontiguousarray(s.bonds, np.int32).reshape(-1), bond_r0=np.ascontiguousarray(s.bond_r0, np.float64),
+            bond_k=np.ascontiguousarray(s.bond_k, np.float64),
+            angles=np.ascontiguousarray(s.angles, np.int32).reshape(-1),
+            angle_t0=np.ascontiguousarray(s.angle_t0, np.float64), angle_k=np.ascontiguousarray(s.angle_k, np.float64),
+            excl=None if s.excl_pairs is None else np.ascontiguousarray(s.excl_pairs, np.int32).reshape(-1),
+            native=np.ascontiguousarray(s.native_pos, np.float64).reshape(-1),
+        )
+        k = self.keep
+        self.c = OrSystem(
+            n=s.n_atoms, n_solute=s.n_solute, n_cv=s.n_cv, n_types=len(s.sigma),
+            mass=_p(k["mass"]), charge=_p(k["charge"]), sigma=_p(k["sigma"]), epsilon=_p(k["epsilon"]),
+            gamma=_p(k["gamma"]), type=_p(k["type"]),
+            n_bonds=len(s.bonds), bonds=_p(k["bonds"]), bond_r0=_p(k["bond_r0"]), bond_k=_p(k["bond_k"]),
+            n_angles=len(s.angles), angles=_p(k["angles"]), angle_t0=_p(k["angle_t0"]), angle_k=_p(k["angle_k"]),
+            n_excl=0 if s.excl_pairs is None else len(s.excl_pairs), excl=_p(k["excl"]),
+            box=float(s.box), native=_p(k["native"]))
+
+
+def _params(p):
+    return OrParams(dt=p.dt, temperature=p.temperature, gamma=p.gamma, r_cut=p.r_cut, skin=p.skin,
+                    nstlist=p.nstlist, eps_rf=p.eps_rf, k_ratchet=p.k_ratchet, cv_r0=p.cv_r0,
+                    cv_r_switch=p.cv_r_switch, cv_r_cut=p.cv_r_cut, cv_min_sep=p.cv_min_sep)
+
+
+# ---------------------------------------------------------------------------
+# thin wrappers
+# ---------------------------------------------------------------------------
+
+def philox4x32_10(ctr, key):
+    c = np.asarray(ctr, np.uint32)
+    k = np.asarray(key, np.uint32)
+    out = np.zeros(4, np.uint32)
+    lib().or_philox4x32_10(c.ctypes.data, k.ctypes.data, out.ctypes.data)
+    return out
+
+
+def normal3(seed, atom, step, stream):
+    out = np.zeros(3)
+    lib().or_normal3(int(seed), int(atom), int(step), int(stream), out.ctypes.data)
+    return out
+
+
+def contact(r, r0=0.75, rs=1.0, rc=1.2):
+    out = np.zeros(4)
+    lib().or_contact(float(r), float(r0), float(rs), float(rc), out.ctypes.data)
+    return out  # C, C~, dC/dr, dC~/dr
+
+
+def cv(s, p, pos):
+    """z and grad z (n_cv, 3) at the given positions."""
+    X = np.ascontiguousarray(np.asarray(pos, np.float64)[: s.n_cv].reshape(-1))
+    nat = np.ascontiguousarray(s.native_pos, np.float64).reshape(-1)
+    g = np.zeros(3 * s.n_cv)
+    z = lib().or_cv(X.ctypes.data, nat.ctypes.data, s.n_cv, float(s.box), p.cv_r0, p.cv_r_switch, p.cv_r_cut,
+                    p.cv_min_sep, g.ctypes.data)
+    return z, g.reshape(-1, 3)
+
+
+def pairlist(s, posf, r_list):
+    """Sorted (i<j) pairs of the FP32 list rule from float positions."""
+    ss = _Sys(s)
+    pf = np.ascontiguousarray(np.asarray(posf, np.float32).reshape(-1))
+    cap = max(1024, s.n_atoms * 400)
+    out = np.zeros(2 * cap, np.int32)
+    n = lib().or_pairlist(C.byref(ss.c), pf.ctypes.data, float(r_list), out.ctypes.data, cap)
+    if n > cap:
+        out = np.zeros(2 * n, np.int32)
+        n = lib().or_pairlist(C.byref(ss.c), pf.ctypes.data, float(r_list), out.ctypes.data, n)
+    return out[: 2 * n].reshape(-1, 2)
+
+
+def forces(s, p, pos, use_list=False):
+    """(F (n,3), energies[4] = E_LJ, E_RF, E_bond, E_angle) of -grad U."""
+    ss = _Sys(s)
+    pp = _params(p)
+    X = np.ascontiguousarray(np.asarray(pos, np.float64).reshape(-1))
+    F = np.zeros(3 * s.n_atoms)
+    e = np.zeros(4)
+    rc = lib().or_forces(C.byref(ss.c), C.byref(pp), X.ctypes.data, int(bool(use_list)), F.ctypes.data,
+                         e.ctypes.data)
+    if rc != 0:
+        raise RuntimeError(f"or_forces failed ({rc})")
+    return F.reshape(-1, 3), e
+
+
+def initial_velocities(s, temperature, seed):
+    ss = _Sys(s)
+    v = np.zeros(3 * s.n_atoms)
+    lib().or_initial_velocities(C.byref(ss.c), float(temperature), int(seed), v.ctypes.data)
+    return v.reshape(-1, 3)
+
+
+def run(s, p, seed, n_steps, pos=None, vel=None, record_every=0, want_force=False):
+    """One trial of n_steps biased BAOAB steps.  Returns a dict with per-step
+    z, z_m, a, phi, the final state, Phi and the final energies."""
+    ss = _Sys(s)
+    pp = _params(p)
+    n = s.n_atoms
+    X = np.ascontiguousarray(np.asarray(s.pos if pos is None else pos, np.float64).reshape(-1))
+    V = None
+    if vel is not None or s.vel is not None:
+        V = np.ascontiguousarray(np.asarray(vel if vel is not None else s.vel, np.float64).reshape(-1))
+    z = np.zeros(n_steps + 1)
+    zm = np.zeros(n_steps + 1)
+    a = np.zeros(n_steps + 1)
+    ph = np.zeros(n_steps + 1)
+    frames = None
+    if record_every > 0:
+        frames = np.zeros((n_steps // record_every + 1, 3 * n))
+    po = np.zeros(3 * n)
+    vo = np.zeros(3 * n)
+    fo = np.zeros(3 * n) if want_force else None
+    out = OrRunOut(z=z.ctypes.data, zm=zm.ctypes.data, a=a.ctypes.data, phi_step=ph.ctypes.data,
+                   frames=_p(frames), record_every=record_every, pos_out=po.ctypes.data, vel_out=vo.ctypes.data,
+                   force_out=_p(fo))
+    rc = lib().or_run(C.byref(ss.c), C.byref(pp), int(seed), X.ctypes.data, None if V is None else V.ctypes.data,
+                      int(n_steps), C.byref(out))
+    res = dict(status=rc, z=z, zm=zm, a=a, phi_step=ph, Phi=out.Phi, energies=np.array(out.energies[:]),
+               pos=po.reshape(-1, 3), vel=vo.reshape(-1, 3))
+    if frames is not None:
+        res["frames"] = frames.reshape(frames.shape[0], n, 3)
+    if fo is not None:
+        res["force"] = fo.reshape(-1, 3)
+    return res
+
+
+def phi_frames(s, p, frames):
+    """Bias functional along frames (n_frames, n_cv, 3); returns (Phi, z, a, phi)."""
+    ss = _Sys(s)
+    pp = _params(p)
+    Fr = np.ascontiguousarray(np.asarray(frames, np.float64)[:, : s.n_cv, :].reshape(-1))
+    nf = int(np.asarray(frames).shape[0])
+    z = np.zeros(nf)
+    a = np.zeros(nf)
+    ph = np.zeros(nf)
+    Phi = lib().or_phi_frames(C.byref(ss.c), C.byref(pp), Fr.ctypes.data, nf, z.ctypes.data, a.ctypes.data,
+                              ph.ctypes.data)
+    return Phi, z, a, ph
+
+
+def num_threads():
+    return int(lib().or_num_threads())
+
+
+def set_num_threads(k):
+    lib().or_set_num_threads(int(k))
