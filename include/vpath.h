@@ -1,0 +1,193 @@
+/*
+ * vpath.h -- C ABI of the GB300 trial-path generator of the variational
+ * pathway scheme (arXiv:1405.6104): many biased Langevin trial trajectories
+ * in explicit solvent, advanced together on one GPU, each scored by the bias
+ * functional whose least value selects the optimal path.
+ *
+ * The method (paper references are to its equations and sections):
+ *   - Eq. Lang: Langevin dynamics m x'' = -m gamma x' - grad U + eta for the
+ *     solute X (atoms [0, n_solute)) and the solvent Y (the other atoms);
+ *     integrated with BAOAB, white noise from Philox4x32-10.
+ *   - Eq. VR: ratchet-and-pawl bias on the solute only,
+ *     F_i = -(k_R/2) (z - z_m) grad_i z when z > z_m, 0 otherwise, with z_m
+ *     the running minimum of z and z_m(0) = z(X_0).
+ *   - SM "Collective coordinate": z(X) = sum_{i<j, j-i > cv_min_sep}
+ *     [C~_ij(X) - C~_ij(X_native)]^2, C(r) = (1-(r/r0)^6)/(1-(r/r0)^10),
+ *     C~ = C * S(r) with S a quintic switch from 1 at cv_r_switch to 0 at
+ *     cv_r_cut.
+ *   - Eq. VMDcondition: Phi = int dt sum_{i in solute} |F_i^bias|^2/(gamma_i m_i),
+ *     accumulated every step; the trial with the least Phi is the optimum
+ *     (Sec. "Results", selection per initial condition).
+ *
+ * Conventions for every entry point:
+ *   - Units: nm, ps, amu, kJ/mol, e, K.
+ *   - Return value 0 (SIM_OK) or a negative SIM_E* code; sim_last_error()
+ *     then describes the failure.  No entry point aborts the process.
+ *   - All pointer arguments are HOST pointers, owned by the caller, read or
+ *     written only during the call.  The library owns all device memory it
+ *     allocates (cudaMalloc at sim_create, freed by sim_destroy).
+ *   - A handle is not thread-safe; calls on one handle must be serialised.
+ *   - Atom indices are the caller's order within a system; trials are
+ *     numbered system by system (all trials of system 0 first).
+ */
+#ifndef VPATH_H
+#define VPATH_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define SIM_OK 0
+#define SIM_EINVAL (-1)          /* invalid argument or system description */
+#define SIM_ECUDA (-2)           /* a CUDA call failed */
+#define SIM_ELIST_OVERFLOW (-3)  /* a cluster's neighbour list or a grid column exceeded capacity */
+#define SIM_ESKIN (-4)           /* an atom moved more than skin/2 between list rebuilds (SIM_STRICT_SKIN) */
+#define SIM_ENONFINITE (-5)      /* a position, velocity or z became non-finite */
+#define SIM_ETIMEOUT (-6)        /* a bounded device wait gave up */
+
+/* sim_params.flags */
+#define SIM_STRICT_SKIN 1        /* treat skin violations as errors instead of counting them */
+#define SIM_NO_GRAPH 2           /* launch every kernel directly instead of replaying CUDA graphs */
+
+typedef struct sim_handle sim_handle;
+
+/* One periodic system.  Arrays are read at sim_create only. */
+typedef struct sim_system {
+  int32_t n_atoms;         /* total atoms (solute + solvent), >= 1 */
+  int32_t n_solute;        /* solute X = atoms [0, n_solute) */
+  int32_t n_cv;            /* atoms of the reaction coordinate = [0, n_cv), n_cv <= n_solute */
+  const double *pos;       /* [3*n_atoms] start positions, nm (stored as FP32 on the device) */
+  const double *vel;       /* [3*n_atoms] start velocities nm/ps, or NULL: Maxwell-Boltzmann
+                              draw per trial (Philox stream 1) with the centre of mass at rest */
+  const double *mass;      /* [n_atoms] amu, > 0 */
+  const double *charge;    /* [n_atoms] e */
+  const int32_t *lj_type;  /* [n_atoms] index into sigma/epsilon */
+  int32_t n_types;
+  const double *sigma;     /* [n_types] nm; Lorentz-Berthelot mixing */
+  const double *epsilon;   /* [n_types] kJ/mol */
+  int32_t n_bonds;
+  const int32_t *bonds;    /* [2*n_bonds] atom pairs, V = k/2 (r - r0)^2 */
+  const double *bond_r0;   /* [n_bonds] nm */
+  const double *bond_k;    /* [n_bonds] kJ/mol/nm^2 */
+  int32_t n_angles;
+  const int32_t *angles;   /* [3*n_angles] (i, vertex, k), V = k/2 (theta - theta0)^2 */
+  const double *angle_t0;  /* [n_angles] rad */
+  const double *angle_k;   /* [n_angles] kJ/mol/rad^2 */
+  int32_t n_excl;
+  const int32_t *excl;     /* [2*n_excl] extra excluded pairs; 1-2 and 1-3 pairs are excluded automatically */
+  double box;              /* cubic periodic box side, nm (rounded to FP32); > 2 (r_cut + skin) */
+  const double *native_pos;/* [3*n_cv] target structure X_native of the contact map (plain distances) */
+  const double *gamma;     /* [n_atoms] friction 1/ps, or NULL: sim_params.gamma for every atom */
+} sim_system;
+
+/* Run parameters shared by all trials. */
+typedef struct sim_params {
+  double dt;               /* ps */
+  double temperature;      /* K */
+  double gamma;            /* 1/ps, default friction */
+  double r_cut;            /* LJ and reaction-field cut-off, nm */
+  double skin;             /* Verlet buffer, nm: lists hold pairs within r_cut + skin */
+  int32_t nstlist;         /* steps between list rebuilds, >= 1 */
+  double eps_rf;           /* reaction-field dielectric; <= 0 means infinity */
+  double k_ratchet;        /* k_R of Eq. VR, kJ/mol */
+  double cv_r0;            /* r0 of the contact function, nm */
+  double cv_r_switch;      /* switching of C~ starts, nm */
+  double cv_r_cut;         /* C~ = 0 beyond, nm */
+  int32_t cv_min_sep;      /* contact pairs have j - i > cv_min_sep */
+  uint64_t seed;           /* trial t uses seed + t unless trial_seeds is given */
+  int32_t flags;           /* SIM_* flags */
+} sim_params;
+
+/* Creates a batch: trials_per_system[s] independent trials of each system
+ * (trial seeds from trial_seeds[total trials] or params->seed + t).  Uploads
+ * the systems, draws velocities where vel is NULL, builds cells and lists,
+ * computes the first forces and sets z_m = z(X_0), Phi = 0 for every trial.
+ * cuda_stream: the caller's stream (or NULL); the library orders its own
+ * stream after it at every call and synchronises before returning.
+ * On success *out receives the handle.  On failure *out may still receive a
+ * handle that only sim_last_error and sim_destroy accept (or NULL). */
+int sim_create(const sim_system *systems, int32_t n_systems, const int32_t *trials_per_system,
+               const uint64_t *trial_seeds, const sim_params *params, void *cuda_stream, sim_handle **out);
+
+/* Advances every trial by n_steps BAOAB steps with the rMD bias and the
+ * per-step accumulation of Phi (Eqs. Lang, VR, VMDcondition).  Blocks until
+ * the device error flags are read.  n_steps >= 0. */
+int sim_step_batch(sim_handle *h, int32_t n_steps);
+
+/* Bias functional of every trial (phi[total trials], may be NULL) and the
+ * index of the trial with the least Phi among trials whose current z is
+ * <= z_max (z_max < 0: all trials); *argmin = -1 if none qualifies; ties go
+ * to the lowest index (selection of Sec. "Results"). */
+int bias_functional(sim_handle *h, double z_max, double *phi, int32_t *argmin);
+
+/* Energies and forces of one trial at its current state, without advancing
+ * it: energies[6] = {E_LJ, E_RF, E_bond, E_angle, E_kin, E_bias} with
+ * E_bias = (k_R/4) (z - z_m)_+^2; forces[3*n_atoms] (or NULL) = -grad U plus
+ * the ratchet force, in the caller's atom order. */
+int energy_forces(sim_handle *h, int32_t trial, double *energies, double *forces);
+
+/* State of one trial: pos, vel [3*n_atoms] (either may be NULL; positions
+ * are wrapped into the box at list rebuilds), cv[4] = {z, z_m, a, Phi} (may
+ * be NULL) where a = (z - z_m_previous)_+ of the last force evaluation. */
+int sim_get_state(sim_handle *h, int32_t trial, double *pos, double *vel, double *cv);
+
+/* Replaces the state of one trial (trial >= 0) or of all trials (trial = -1,
+ * arrays concatenated in trial order).  pos and vel must both be given.
+ * cv_state = {z_m, Phi} per affected trial, or NULL to restart the functional
+ * (z_m = z(X), Phi = 0).  Lists are rebuilt and forces recomputed for the
+ * whole batch; the step counter is unchanged. */
+int sim_set_state(sim_handle *h, int32_t trial, const double *pos, const double *vel, const double *cv_state);
+
+/* Steps taken since creation (the Philox counter of the next step is this + 1). */
+int64_t sim_step_count(const sim_handle *h);
+/* Sets the step counter (resume from a checkpoint); list rebuilds happen at
+ * multiples of nstlist of this counter. */
+int sim_set_step_count(sim_handle *h, int64_t step);
+
+int32_t sim_num_trials(const sim_handle *h);
+int32_t sim_num_atoms(const sim_handle *h, int32_t trial);
+
+/* Per-step record of {z, z_m, a, phi} for every trial: capacity entries per
+ * trial (0 disables); entry of step n at index n % capacity.  Enabling
+ * clears the record. */
+int sim_record(sim_handle *h, int32_t capacity);
+int sim_get_record(sim_handle *h, int32_t trial, double *out /* [4*capacity] */);
+
+/* Test and diagnostics hooks.
+ * sim_pairlist: the atom pairs (i < j, caller's indices) that the current
+ *   cluster lists hold for one trial (list rule at the last rebuild);
+ *   *n_pairs receives the count, pairs beyond cap are dropped.
+ * sim_diagnostics: out[4] = {skin violations counted, max list entries of a
+ *   cluster, list capacity per cluster, clusters in use (all trials)}. */
+int sim_pairlist(sim_handle *h, int32_t trial, int32_t *pairs, int64_t cap, int64_t *n_pairs);
+int sim_diagnostics(sim_handle *h, int64_t *out);
+
+/* Kernel timing: with on != 0 the next sim_step_batch calls launch kernels
+ * directly and time each launch with CUDA events on the library stream.
+ * sim_kernel_times fills up to cap entries of names (static strings), total
+ * milliseconds and launch counts, returns the number of kernels, and resets
+ * the accumulators. */
+int sim_set_timing(sim_handle *h, int32_t on);
+int sim_kernel_times(sim_handle *h, const char **names, double *ms, int64_t *counts, int32_t cap);
+
+/* The counter-based noise as the integrator draws it, for atoms 0..n-1 of a
+ * trial with the given seed at one step and stream (0: Langevin noise,
+ * 1: initial velocities): raw[4n] Philox4x32-10 outputs for counter
+ * (atom, step_lo, step_hi, stream) and key (seed_lo, seed_hi), normals[3n]
+ * the FP32 Box-Muller normals widened to double.  Either output may be NULL.
+ * Runs on the current device; allocates and frees its own scratch. */
+int sim_philox_normals(uint64_t seed, int64_t step, uint32_t stream, int32_t n, uint32_t *raw, double *normals);
+
+/* The cudaStream_t the library launches on. */
+void *sim_stream(sim_handle *h);
+
+void sim_destroy(sim_handle *h);
+const char *sim_last_error(const sim_handle *h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* VPATH_H */

@@ -1,0 +1,899 @@
+// vp_capi.cu -- host side of the C ABI declared in include/vpath.h: batch
+// construction, the per-step launch sequence, CUDA-graph capture of list
+// intervals, state transfer and diagnostics.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/vpath.h"
+#include "vp_dev.cuh"
+
+#define VP_API extern "C" __attribute__((visibility("default")))
+
+using namespace vp;
+
+namespace {
+
+struct Timer {
+  const char *name;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;
+  double ms = 0.0;
+  long long count = 0;
+};
+
+}  // namespace
+
+struct sim_handle {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  cudaStream_t caller = nullptr;
+  cudaEvent_t entry_ev = nullptr;
+  Dev d{};
+  SimConst c{};
+  sim_params params{};
+  int n_sys = 0, n_trials = 0;
+  std::vector<TrialInfo> tinfo;
+  std::vector<int> trial_sys;
+  long long step = 0;
+  float rl2_bbox = 0.f, half_skin2 = 0.f;
+  int strict_skin = 0;
+  bool use_graph = true;
+  cudaGraphExec_t chunk = nullptr;
+  bool timing = false;
+  std::vector<Timer> timers;
+  std::map<std::string, int> timer_idx;
+  std::vector<void *> allocs;
+  std::string err;
+  int rec_cap = 0;
+  // staging
+  double *dbuf = nullptr;
+  size_t dbuf_n = 0;
+  int32_t *d_argmin = nullptr;
+  unsigned long long *d_count = nullptr;
+  int max_atoms = 0;
+};
+
+namespace {
+
+int fail(sim_handle *h, int code, const std::string &msg) {
+  if (h) h->err = msg;
+  return code;
+}
+
+#define CK(call)                                                                             \
+  do {                                                                                       \
+    cudaError_t e_ = (call);                                                                 \
+    if (e_ != cudaSuccess) return fail(h, SIM_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+template <class T>
+int dalloc(sim_handle *h, T **p, size_t n) {
+  *p = nullptr;
+  if (n == 0) n = 1;
+  cudaError_t e = cudaMalloc((void **)p, n * sizeof(T));
+  if (e != cudaSuccess) return fail(h, SIM_ECUDA, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  h->allocs.push_back(*p);
+  cudaMemset(*p, 0, n * sizeof(T));
+  return SIM_OK;
+}
+
+template <class T>
+int upload(sim_handle *h, T **p, const std::vector<T> &v) {
+  int r = dalloc(h, p, v.size());
+  if (r) return r;
+  if (!v.empty()) {
+    cudaError_t e = cudaMemcpy(*p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return fail(h, SIM_ECUDA, std::string("cudaMemcpy: ") + cudaGetErrorString(e));
+  }
+  return SIM_OK;
+}
+
+void ff_split(double v, float &hi, float &lo) {
+  hi = (float)v;
+  lo = (float)(v - (double)hi);
+}
+
+// kernel launch with optional CUDA-event timing
+template <class F>
+void timed(sim_handle *h, const char *name, F &&f) {
+  if (!h->timing) {
+    f();
+    return;
+  }
+  auto it = h->timer_idx.find(name);
+  int k;
+  if (it == h->timer_idx.end()) {
+    k = (int)h->timers.size();
+    h->timer_idx[name] = k;
+    h->timers.push_back(Timer{name, {}, 0.0, 0});
+  } else {
+    k = it->second;
+  }
+  cudaEvent_t a, b;
+  cudaEventCreate(&a);
+  cudaEventCreate(&b);
+  cudaEventRecord(a, h->stream);
+  f();
+  cudaEventRecord(b, h->stream);
+  h->timers[k].ev.emplace_back(a, b);
+}
+
+void harvest_timers(sim_handle *h) {
+  for (auto &t : h->timers) {
+    for (auto &pr : t.ev) {
+      float ms = 0.f;
+      cudaEventSynchronize(pr.second);
+      cudaEventElapsedTime(&ms, pr.first, pr.second);
+      t.ms += ms;
+      t.count += 1;
+      cudaEventDestroy(pr.first);
+      cudaEventDestroy(pr.second);
+    }
+    t.ev.clear();
+  }
+}
+
+void rebuild(sim_handle *h) {
+  cudaStream_t s = h->stream;
+  timed(h, "bin", [&] { launch_bin(h->d, h->c, h->half_skin2, h->strict_skin, s); });
+  timed(h, "colscan", [&] { launch_colscan(h->d, s); });
+  timed(h, "colfill", [&] { launch_colfill(h->d, s); });
+  timed(h, "colsort", [&] { launch_colsort(h->d, s); });
+  timed(h, "list", [&] { launch_list(h->d, h->c, h->rl2_bbox, s); });
+}
+
+void forces(sim_handle *h, FinMode mode) {
+  cudaStream_t s = h->stream;
+  timed(h, "pair", [&] { launch_pair(h->d, h->c, false, -1, s); });
+  timed(h, "cv", [&] { launch_cv(h->d, h->c, s); });
+  timed(h, "cvfin", [&] { launch_cvfin(h->d, h->c, mode, s); });
+}
+
+void one_step(sim_handle *h, bool with_rebuild) {
+  timed(h, "update", [&] { launch_update(h->d, h->c, UPD_DRIFT, h->stream); });
+  if (with_rebuild) rebuild(h);
+  forces(h, FIN_STEP);
+}
+
+int check_flags(sim_handle *h) {
+  int flags = 0;
+  CK(cudaMemcpyAsync(&flags, h->d.err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  if (flags & ERR_NONFINITE) return fail(h, SIM_ENONFINITE, "non-finite position, velocity or reaction coordinate");
+  if (flags & (ERR_LIST | ERR_COL | ERR_CAPACITY))
+    return fail(h, SIM_ELIST_OVERFLOW, "cluster list, grid column or cluster capacity exceeded");
+  if (flags & ERR_SKIN) return fail(h, SIM_ESKIN, "an atom moved more than skin/2 between list rebuilds");
+  return SIM_OK;
+}
+
+int enter(sim_handle *h) {
+  if (!h) return SIM_EINVAL;
+  CK(cudaSetDevice(h->device));
+  if (h->caller) {
+    CK(cudaEventRecord(h->entry_ev, h->caller));
+    CK(cudaStreamWaitEvent(h->stream, h->entry_ev, 0));
+  }
+  return SIM_OK;
+}
+
+int ensure_dbuf(sim_handle *h, size_t n) {
+  if (h->dbuf_n >= n) return SIM_OK;
+  if (h->dbuf) cudaFree(h->dbuf);
+  h->dbuf = nullptr;
+  cudaError_t e = cudaMalloc(&h->dbuf, n * sizeof(double));
+  if (e != cudaSuccess) return fail(h, SIM_ECUDA, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  h->dbuf_n = n;
+  return SIM_OK;
+}
+
+int capture_chunk(sim_handle *h) {
+  if (h->chunk) return SIM_OK;
+  cudaGraph_t g;
+  CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+  for (int k = 0; k < h->params.nstlist; ++k) one_step(h, k == 0);
+  CK(cudaStreamEndCapture(h->stream, &g));
+  cudaError_t e = cudaGraphInstantiate(&h->chunk, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    h->chunk = nullptr;
+    return fail(h, SIM_ECUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+  }
+  return SIM_OK;
+}
+
+// validation of one system description
+std::string check_system(const sim_system &s, const sim_params &p) {
+  if (s.n_atoms < 1) return "n_atoms < 1";
+  if (s.n_solute < 0 || s.n_solute > s.n_atoms) return "n_solute out of range";
+  if (s.n_cv < 0 || s.n_cv > s.n_solute) return "n_cv out of range";
+  if (!s.pos || !s.mass || !s.charge || !s.lj_type || !s.sigma || !s.epsilon) return "missing atom arrays";
+  if (s.n_cv > 0 && !s.native_pos) return "missing native_pos";
+  if (s.n_types < 1) return "n_types < 1";
+  double rl = p.r_cut + p.skin;
+  if (!(s.box > 2.0 * rl)) return "box must exceed 2 (r_cut + skin)";
+  for (int i = 0; i < s.n_atoms; ++i) {
+    if (!(s.mass[i] > 0.0)) return "non-positive mass";
+    if (s.lj_type[i] < 0 || s.lj_type[i] >= s.n_types) return "lj_type out of range";
+    for (int k = 0; k < 3; ++k)
+      if (!std::isfinite(s.pos[3 * i + k])) return "non-finite position";
+  }
+  for (int b = 0; b < s.n_bonds; ++b)
+    for (int k = 0; k < 2; ++k)
+      if (s.bonds[2 * b + k] < 0 || s.bonds[2 * b + k] >= s.n_atoms) return "bond index out of range";
+  for (int a = 0; a < s.n_angles; ++a)
+    for (int k = 0; k < 3; ++k)
+      if (s.angles[3 * a + k] < 0 || s.angles[3 * a + k] >= s.n_atoms) return "angle index out of range";
+  for (int x = 0; x < s.n_excl; ++x)
+    for (int k = 0; k < 2; ++k)
+      if (s.excl[2 * x + k] < 0 || s.excl[2 * x + k] >= s.n_atoms) return "exclusion index out of range";
+  return "";
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+
+VP_API int sim_create(const sim_system *systems, int32_t n_systems, const int32_t *trials_per_system,
+                      const uint64_t *trial_seeds, const sim_params *params, void *cuda_stream, sim_handle **out) {
+  if (!out) return SIM_EINVAL;
+  *out = nullptr;
+  if (!systems || n_systems < 1 || !trials_per_system || !params) return SIM_EINVAL;
+  sim_handle *h = new sim_handle();
+  auto bail = [&](int code) {
+    *out = h;  // keep the handle so that sim_last_error works; caller destroys it
+    return code;
+  };
+  const sim_params &p = *params;
+  h->params = p;
+  if (!(p.dt > 0) || !(p.temperature >= 0) || !(p.r_cut > 0) || !(p.skin >= 0) || p.nstlist < 1 ||
+      !(p.cv_r0 > 0) || !(p.cv_r_cut > p.cv_r_switch) || !(p.cv_r_switch > 0))
+    return bail(fail(h, SIM_EINVAL, "invalid sim_params"));
+  int total_trials = 0;
+  for (int s = 0; s < n_systems; ++s) {
+    if (trials_per_system[s] < 0) return bail(fail(h, SIM_EINVAL, "negative trial count"));
+    std::string m = check_system(systems[s], p);
+    if (!m.empty()) return bail(fail(h, SIM_EINVAL, "system " + std::to_string(s) + ": " + m));
+    total_trials += trials_per_system[s];
+  }
+  if (total_trials < 1) return bail(fail(h, SIM_EINVAL, "no trials"));
+  cudaError_t ce = cudaGetDevice(&h->device);
+  if (ce != cudaSuccess) return bail(fail(h, SIM_ECUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(ce)));
+  if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess)
+    return bail(fail(h, SIM_ECUDA, "cudaStreamCreate failed"));
+  cudaEventCreateWithFlags(&h->entry_ev, cudaEventDisableTiming);
+  h->caller = (cudaStream_t)cuda_stream;
+  h->n_sys = n_systems;
+  h->n_trials = total_trials;
+  h->use_graph = !(p.flags & SIM_NO_GRAPH);
+  h->strict_skin = (p.flags & SIM_STRICT_SKIN) ? 1 : 0;
+
+  // ---- constants -------------------------------------------------------------
+  const double kT = KB * p.temperature;
+  const double rl = p.r_cut + p.skin;
+  SimConst &c = h->c;
+  c.dt = (float)p.dt;
+  c.half_dt = (float)(0.5 * p.dt);
+  c.dt_d = p.dt;
+  c.rc2 = (float)(p.r_cut * p.r_cut);
+  c.rl2 = (float)(rl * rl);
+  double krf, crf;
+  if (p.eps_rf <= 0.0) {
+    krf = 1.0 / (2.0 * p.r_cut * p.r_cut * p.r_cut);
+    crf = 3.0 / (2.0 * p.r_cut);
+  } else {
+    krf = (p.eps_rf - 1.0) / ((2.0 * p.eps_rf + 1.0) * p.r_cut * p.r_cut * p.r_cut);
+    crf = 1.0 / p.r_cut + krf * p.r_cut * p.r_cut;
+  }
+  c.krf = (float)krf;
+  c.crf = (float)crf;
+  c.two_krf = (float)(2.0 * krf);
+  c.kR_half = (float)(0.5 * p.k_ratchet);
+  c.kR_half_d = 0.5 * p.k_ratchet;
+  c.list_cap = 512;
+  ff_split(1.0 / (p.cv_r0 * p.cv_r0), c.cv_inv_r0sq_hi, c.cv_inv_r0sq_lo);
+  ff_split(p.cv_r_switch, c.cv_rs_hi, c.cv_rs_lo);
+  ff_split(1.0 / (p.cv_r_cut - p.cv_r_switch), c.cv_inv_w_hi, c.cv_inv_w_lo);
+  c.cv_rs2 = (float)(p.cv_r_switch * p.cv_r_switch);
+  c.cv_rc2_far = (float)(p.cv_r_cut * p.cv_r_cut * (1.0 + 1e-4));
+  c.cv_r0_d = p.cv_r0;
+  c.cv_rs_d = p.cv_r_switch;
+  c.cv_rc_d = p.cv_r_cut;
+  c.cv_min_sep = p.cv_min_sep;
+  c.rec_cap = 0;
+  h->rl2_bbox = (float)((rl + 1e-3) * (rl + 1e-3));
+  h->half_skin2 = (float)(0.25 * p.skin * p.skin);
+
+  // ---- LJ types: de-duplicate (sigma, epsilon) over all systems -------------
+  std::vector<std::pair<double, double>> gtypes;
+  std::vector<std::vector<int>> tmap(n_systems);
+  for (int s = 0; s < n_systems; ++s) {
+    const sim_system &S = systems[s];
+    tmap[s].resize(S.n_types);
+    for (int k = 0; k < S.n_types; ++k) {
+      std::pair<double, double> key(S.sigma[k], S.epsilon[k]);
+      int g = -1;
+      for (size_t q = 0; q < gtypes.size(); ++q)
+        if (gtypes[q] == key) { g = (int)q; break; }
+      if (g < 0) {
+        g = (int)gtypes.size();
+        gtypes.push_back(key);
+      }
+      tmap[s][k] = g;
+    }
+  }
+  if ((int)gtypes.size() > MAX_TYPES) return bail(fail(h, SIM_EINVAL, "more than 64 distinct LJ types"));
+  const int NT = (int)gtypes.size();
+  c.n_types = NT;
+  std::vector<float2> ljtab(NT * NT);
+  std::vector<float> ljshift(NT * NT);
+  for (int a = 0; a < NT; ++a)
+    for (int b = 0; b < NT; ++b) {
+      double sig = 0.5 * (gtypes[a].first + gtypes[b].first);
+      double eps = std::sqrt(gtypes[a].second * gtypes[b].second);
+      double s6 = std::pow(sig, 6.0);
+      double c6 = 4.0 * eps * s6, c12 = 4.0 * eps * s6 * s6;
+      if (!(eps > 0.0 && sig > 0.0)) c6 = c12 = 0.0;
+      ljtab[a * NT + b] = make_float2((float)(6.0 * c6), (float)(12.0 * c12));
+      double rc6 = std::pow(p.r_cut, 6.0);
+      ljshift[a * NT + b] = (float)(c12 / (rc6 * rc6) - c6 / rc6);
+    }
+
+  // ---- per-system tables ------------------------------------------------------
+  std::vector<int> sysatom0(n_systems + 1, 0);
+  for (int s = 0; s < n_systems; ++s) sysatom0[s + 1] = sysatom0[s] + systems[s].n_atoms;
+  const int total_sys_atoms = sysatom0[n_systems];
+  std::vector<AtomSys> asys(total_sys_atoms);
+  std::vector<double> gm(total_sys_atoms);
+  std::vector<int32_t> excl((size_t)total_sys_atoms * MAX_EXCL, -1), excl_n(total_sys_atoms, 0);
+  std::vector<int32_t> bt_start(total_sys_atoms + 1, 0);
+  std::vector<BTerm> bterm;
+  std::vector<int2> tiles;
+  std::vector<int32_t> sys_tile0(n_systems), sys_ntiles(n_systems), sys_ncv(n_systems), sys_minsep(n_systems),
+      tile_sys, sys_nat0(n_systems);
+  std::vector<double> native_all;
+  const double sqf = std::sqrt(FCOUL);
+  for (int s = 0; s < n_systems; ++s) {
+    const sim_system &S = systems[s];
+    const int a0 = sysatom0[s];
+    for (int i = 0; i < S.n_atoms; ++i) {
+      double g = S.gamma ? S.gamma[i] : p.gamma;
+      double c1 = std::exp(-g * p.dt);
+      asys[a0 + i].invm = (float)(1.0 / S.mass[i]);
+      asys[a0 + i].c1 = (float)c1;
+      asys[a0 + i].c2sd = (float)std::sqrt((1.0 - c1 * c1) * kT / S.mass[i]);
+      asys[a0 + i].qs = (float)(S.charge[i] * sqf);
+      gm[a0 + i] = g * S.mass[i];
+      if (i < S.n_cv && !(g > 0.0)) return bail(fail(h, SIM_EINVAL, "reaction-coordinate atoms need gamma > 0"));
+    }
+    // exclusions: 1-2, 1-3 and the extra pairs
+    auto add_ex = [&](int i, int j) -> bool {
+      if (i == j) return true;
+      int *e = &excl[(size_t)(a0 + i) * MAX_EXCL];
+      int &n = excl_n[a0 + i];
+      for (int k = 0; k < n; ++k)
+        if (e[k] == j) return true;
+      if (n >= MAX_EXCL) return false;
+      e[n++] = j;
+      return true;
+    };
+    bool ok = true;
+    for (int b = 0; b < S.n_bonds; ++b) {
+      int i = S.bonds[2 * b], j = S.bonds[2 * b + 1];
+      ok &= add_ex(i, j) && add_ex(j, i);
+    }
+    for (int a = 0; a < S.n_angles; ++a) {
+      int i = S.angles[3 * a], j = S.angles[3 * a + 1], k = S.angles[3 * a + 2];
+      ok &= add_ex(i, j) && add_ex(j, i) && add_ex(j, k) && add_ex(k, j) && add_ex(i, k) && add_ex(k, i);
+    }
+    for (int x = 0; x < S.n_excl; ++x) {
+      int i = S.excl[2 * x], j = S.excl[2 * x + 1];
+      ok &= add_ex(i, j) && add_ex(j, i);
+    }
+    if (!ok) return bail(fail(h, SIM_EINVAL, "more than 16 excluded partners for an atom"));
+    // bonded terms, owner computes
+    std::vector<std::vector<BTerm>> per(S.n_atoms);
+    for (int b = 0; b < S.n_bonds; ++b) {
+      int i = S.bonds[2 * b], j = S.bonds[2 * b + 1];
+      per[i].push_back(BTerm{0, j, -1, (float)S.bond_r0[b], (float)S.bond_k[b]});
+      per[j].push_back(BTerm{0, i, -1, (float)S.bond_r0[b], (float)S.bond_k[b]});
+    }
+    for (int a = 0; a < S.n_angles; ++a) {
+      int i = S.angles[3 * a], j = S.angles[3 * a + 1], k = S.angles[3 * a + 2];
+      float t0 = (float)S.angle_t0[a], kk = (float)S.angle_k[a];
+      per[i].push_back(BTerm{1, j, k, t0, kk});
+      per[k].push_back(BTerm{1, j, i, t0, kk});
+      per[j].push_back(BTerm{2, i, k, t0, kk});
+    }
+    for (int i = 0; i < S.n_atoms; ++i) {
+      bt_start[a0 + i] = (int)bterm.size();
+      for (auto &t : per[i]) bterm.push_back(t);
+    }
+    // reaction-coordinate tiles
+    sys_ncv[s] = S.n_cv;
+    sys_minsep[s] = p.cv_min_sep;
+    sys_tile0[s] = (int)tiles.size();
+    sys_nat0[s] = (int)(native_all.size() / 3);
+    for (int i = 0; i < 3 * S.n_cv; ++i) native_all.push_back(S.native_pos[i]);
+    int nb = (S.n_cv + CV_T - 1) / CV_T;
+    for (int bi = 0; bi < nb; ++bi)
+      for (int bj = bi; bj < nb; ++bj) {
+        int maxj = std::min(bj * CV_T + CV_T - 1, S.n_cv - 1);
+        if (maxj - bi * CV_T > p.cv_min_sep) {
+          tiles.push_back(make_int2(bi, bj));
+          tile_sys.push_back(s);
+        }
+      }
+    sys_ntiles[s] = (int)tiles.size() - sys_tile0[s];
+  }
+  bt_start[total_sys_atoms] = (int)bterm.size();
+
+  // ---- per-trial layout ---------------------------------------------------------
+  std::vector<int> slot_trial, clus_trial, col_trial;
+  std::vector<int2> work;
+  int slot0 = 0, col0 = 0, atom0 = 0, cv0 = 0;
+  int tcount = 0;
+  for (int s = 0; s < n_systems; ++s) {
+    const sim_system &S = systems[s];
+    const float Lf = (float)S.box;
+    const double L = (double)Lf;
+    const double rho = S.n_atoms / (L * L * L);
+    int ncol = (int)std::lround(L / std::cbrt((double)CL / rho));
+    ncol = std::max(1, std::min(ncol, 64));
+    for (int r = 0; r < trials_per_system[s]; ++r, ++tcount) {
+      TrialInfo T{};
+      T.sys = s;
+      T.atom0 = atom0;
+      T.sysatom0 = sysatom0[s];
+      T.n_atoms = S.n_atoms;
+      T.n_cv = S.n_cv;
+      T.slot0 = slot0;
+      T.clus0 = slot0 / CL;
+      T.max_clus = (S.n_atoms + (CL - 1) * ncol * ncol + CL - 1) / CL + 1;
+      T.ncol = ncol;
+      T.col0 = col0;
+      T.cv0 = cv0;
+      T.work0 = (int)work.size();
+      T.n_work = sys_ntiles[s];
+      T.systile0 = sys_tile0[s];
+      T.box = Lf;
+      T.inv_box = (float)(1.0 / L);
+      T.col_w = (float)(L / ncol);
+      T.inv_col_w = (float)(ncol / L);
+      uint64_t seed = trial_seeds ? trial_seeds[tcount] : p.seed + (uint64_t)tcount;
+      T.key0 = (uint32_t)seed;
+      T.key1 = (uint32_t)(seed >> 32);
+      for (int k = 0; k < sys_ntiles[s]; ++k) work.push_back(make_int2(tcount, sys_tile0[s] + k));
+      for (int k = 0; k < T.max_clus * CL; ++k) slot_trial.push_back(tcount);
+      for (int k = 0; k < T.max_clus; ++k) clus_trial.push_back(tcount);
+      for (int k = 0; k < ncol * ncol; ++k) col_trial.push_back(tcount);
+      h->tinfo.push_back(T);
+      h->trial_sys.push_back(s);
+      slot0 += T.max_clus * CL;
+      col0 += ncol * ncol;
+      atom0 += S.n_atoms;
+      cv0 += S.n_cv;
+      h->max_atoms = std::max(h->max_atoms, S.n_atoms);
+    }
+  }
+  Dev &d = h->d;
+  d.n_trials = total_trials;
+  d.n_sys = n_systems;
+  d.total_slots = slot0;
+  d.total_clus = slot0 / CL;
+  d.total_cols = col0;
+  d.total_work = (int)work.size();
+  const int total_atoms = atom0, total_cv = cv0;
+
+  // ---- initial slot contents (caller order, padded) --------------------------------
+  std::vector<float4> pos(slot0), vel(slot0);
+  std::vector<int32_t> orig(slot0, -1), type(slot0, 0), slot_of(total_atoms > 0 ? total_atoms : 1);
+  std::vector<float4> ref(total_atoms > 0 ? total_atoms : 1);
+  std::vector<TrialState> tstate(total_trials);
+  std::vector<int32_t> need_vel(total_trials, 0);
+  for (int t = 0; t < total_trials; ++t) {
+    const TrialInfo &T = h->tinfo[t];
+    const sim_system &S = systems[T.sys];
+    for (int o = 0; o < S.n_atoms; ++o) {
+      int sl = T.slot0 + o;
+      float4 pp = make_float4((float)S.pos[3 * o], (float)S.pos[3 * o + 1], (float)S.pos[3 * o + 2],
+                              asys[T.sysatom0 + o].qs);
+      pos[sl] = pp;
+      vel[sl] = make_float4(S.vel ? (float)S.vel[3 * o] : 0.f, S.vel ? (float)S.vel[3 * o + 1] : 0.f,
+                            S.vel ? (float)S.vel[3 * o + 2] : 0.f, asys[T.sysatom0 + o].invm);
+      orig[sl] = o;
+      type[sl] = tmap[T.sys][S.lj_type[o]];
+      slot_of[T.atom0 + o] = sl;
+      ref[T.atom0 + o] = make_float4(pp.x, pp.y, pp.z, 0.f);
+    }
+    tstate[t].n_clus = (S.n_atoms + CL - 1) / CL;
+    need_vel[t] = S.vel ? 0 : 1;
+  }
+
+  // ---- device allocation and upload ---------------------------------------------
+  int r = 0;
+  std::vector<int32_t> ncv_v(sys_ncv), ms_v(sys_minsep);
+  r |= upload(h, &d.tinfo, h->tinfo);
+  r |= upload(h, &d.tstate, tstate);
+  r |= upload(h, &d.pos, pos);
+  r |= upload(h, &d.vel, vel);
+  r |= dalloc(h, &d.pos_b, slot0);
+  r |= dalloc(h, &d.vel_b, slot0);
+  r |= upload(h, &d.orig, orig);
+  r |= upload(h, &d.type, type);
+  r |= dalloc(h, &d.orig_b, slot0);
+  r |= dalloc(h, &d.type_b, slot0);
+  r |= upload(h, &d.slot_trial, slot_trial);
+  r |= dalloc(h, &d.slot_col, slot0);
+  r |= dalloc(h, &d.fx, slot0);
+  r |= dalloc(h, &d.fy, slot0);
+  r |= dalloc(h, &d.fz, slot0);
+  r |= upload(h, &d.clus_trial, clus_trial);
+  r |= dalloc(h, &d.bb_lo, d.total_clus);
+  r |= dalloc(h, &d.bb_hi, d.total_clus);
+  r |= dalloc(h, &d.list, (size_t)d.total_clus * c.list_cap);
+  r |= dalloc(h, &d.list_n, d.total_clus);
+  r |= upload(h, &d.col_trial, col_trial);
+  r |= dalloc(h, &d.col_count, col0);
+  r |= dalloc(h, &d.col_start, col0);
+  r |= dalloc(h, &d.col_cstart, col0);
+  r |= dalloc(h, &d.col_fill, col0);
+  r |= dalloc(h, &d.bucket, total_atoms);
+  r |= upload(h, &d.slot_of, slot_of);
+  r |= upload(h, &d.ref_pos, ref);
+  r |= dalloc(h, &d.gx, total_cv);
+  r |= dalloc(h, &d.gy, total_cv);
+  r |= dalloc(h, &d.gz, total_cv);
+  r |= dalloc(h, &d.z_part, work.size());
+  r |= upload(h, &d.asys, asys);
+  r |= upload(h, &d.gm, gm);
+  r |= upload(h, &d.excl, excl);
+  r |= upload(h, &d.excl_n, excl_n);
+  r |= upload(h, &d.bt_start, bt_start);
+  r |= upload(h, &d.bterm, bterm);
+  r |= upload(h, &d.tiles, tiles);
+  r |= upload(h, &d.work, work);
+  r |= dalloc(h, &d.cnat, tiles.size() * CV_T * CV_T);
+  r |= upload(h, &d.sys_ncv, ncv_v);
+  r |= upload(h, &d.sys_minsep, ms_v);
+  r |= upload(h, &d.ljtab, ljtab);
+  r |= upload(h, &d.ljshift, ljshift);
+  r |= dalloc(h, &d.err, 1);
+  r |= dalloc(h, &d.step, 1);
+  r |= dalloc(h, &d.kick, 1);
+  r |= dalloc(h, &d.done, 1);
+  r |= dalloc(h, &d.energy, (size_t)total_trials * 5);
+  r |= dalloc(h, &d.skin_count, 1);
+  r |= dalloc(h, &h->d_argmin, 1);
+  r |= dalloc(h, &h->d_count, 1);
+  if (r) return bail(SIM_ECUDA);
+  float half = 0.5f;
+  if (cudaMemcpy(d.kick, &half, sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess)
+    return bail(fail(h, SIM_ECUDA, "cudaMemcpy kick"));
+
+  // ---- native contact map, velocities, first lists and forces -------------------------
+  int32_t *d_need = nullptr, *d_nat0 = nullptr, *d_tsys = nullptr, *d_st0 = nullptr, *d_snt = nullptr;
+  double *d_native = nullptr;
+  r |= upload(h, &d_need, need_vel);
+  r |= upload(h, &d_native, native_all);
+  r |= upload(h, &d_nat0, sys_nat0);
+  r |= upload(h, &d_tsys, tile_sys);
+  r |= upload(h, &d_st0, sys_tile0);
+  r |= upload(h, &d_snt, sys_ntiles);
+  if (r) return bail(SIM_ECUDA);
+  cudaStream_t st = h->stream;
+  launch_cnat(d, c, d_native, d_nat0, (int)tiles.size(), d_tsys, st);
+  launch_zconst(d, d_st0, d_snt, st);
+  launch_init_vel(d, (float)kT, d_need, st);
+  rebuild(h);
+  forces(h, FIN_INIT);
+  if (cudaStreamSynchronize(st) != cudaSuccess || cudaGetLastError() != cudaSuccess)
+    return bail(fail(h, SIM_ECUDA, std::string("initialisation kernels failed: ") +
+                                       cudaGetErrorString(cudaGetLastError())));
+  int fr = check_flags(h);
+  if (fr) return bail(fr);
+  *out = h;
+  return SIM_OK;
+}
+
+VP_API int sim_step_batch(sim_handle *h, int32_t n_steps) {
+  int r = enter(h);
+  if (r) return r;
+  if (n_steps < 0) return fail(h, SIM_EINVAL, "n_steps < 0");
+  if (n_steps == 0) return SIM_OK;
+  CK(cudaMemsetAsync(h->d.err, 0, sizeof(int), h->stream));
+  const int nst = h->params.nstlist;
+  int left = n_steps;
+  while (left > 0) {
+    const long long next = h->step + 1;
+    const bool aligned = (next % nst) == 0;
+    if (h->use_graph && !h->timing && aligned && left >= nst) {
+      r = capture_chunk(h);
+      if (r) return r;
+      CK(cudaGraphLaunch(h->chunk, h->stream));
+      h->step += nst;
+      left -= nst;
+    } else {
+      one_step(h, aligned);
+      h->step += 1;
+      left -= 1;
+    }
+  }
+  timed(h, "update_final", [&] { launch_update(h->d, h->c, UPD_FINAL, h->stream); });
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(h->stream));
+  if (h->timing) harvest_timers(h);
+  return check_flags(h);
+}
+
+VP_API int bias_functional(sim_handle *h, double z_max, double *phi, int32_t *argmin) {
+  int r = enter(h);
+  if (r) return r;
+  r = ensure_dbuf(h, (size_t)h->n_trials);
+  if (r) return r;
+  launch_select(h->d, z_max, h->dbuf, h->d_argmin, h->stream);
+  int32_t am = -1;
+  std::vector<double> tmp(h->n_trials);
+  CK(cudaMemcpyAsync(tmp.data(), h->dbuf, sizeof(double) * h->n_trials, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaMemcpyAsync(&am, h->d_argmin, sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  if (phi) std::memcpy(phi, tmp.data(), sizeof(double) * h->n_trials);
+  if (argmin) *argmin = am;
+  return SIM_OK;
+}
+
+VP_API int energy_forces(sim_handle *h, int32_t trial, double *energies, double *forces_out) {
+  int r = enter(h);
+  if (r) return r;
+  if (trial < 0 || trial >= h->n_trials) return fail(h, SIM_EINVAL, "trial out of range");
+  const TrialInfo &T = h->tinfo[trial];
+  if (energies) {
+    CK(cudaMemsetAsync(h->d.energy + (size_t)trial * 5, 0, 5 * sizeof(long long), h->stream));
+    launch_pair(h->d, h->c, true, trial, h->stream);
+    launch_kinetic(h->d, trial, h->stream);
+    long long e[5];
+    TrialState S;
+    CK(cudaMemcpyAsync(e, h->d.energy + (size_t)trial * 5, sizeof(e), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaMemcpyAsync(&S, h->d.tstate + trial, sizeof(S), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    for (int k = 0; k < 5; ++k) energies[k] = (double)e[k] / E_SCALE;
+    energies[5] = 0.5 * h->c.kR_half_d * S.a * S.a;
+  }
+  if (forces_out) {
+    r = ensure_dbuf(h, (size_t)3 * T.n_atoms);
+    if (r) return r;
+    launch_forces_out(h->d, h->c, trial, h->dbuf, T.n_atoms, h->stream);
+    CK(cudaMemcpyAsync(forces_out, h->dbuf, sizeof(double) * 3 * T.n_atoms, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+  }
+  CK(cudaGetLastError());
+  return SIM_OK;
+}
+
+VP_API int sim_get_state(sim_handle *h, int32_t trial, double *pos, double *vel, double *cv) {
+  int r = enter(h);
+  if (r) return r;
+  if (trial < 0 || trial >= h->n_trials) return fail(h, SIM_EINVAL, "trial out of range");
+  const TrialInfo &T = h->tinfo[trial];
+  const size_t n3 = (size_t)3 * T.n_atoms;
+  r = ensure_dbuf(h, 2 * n3);
+  if (r) return r;
+  launch_gather_state(h->d, trial, h->dbuf, h->dbuf + n3, T.n_atoms, h->stream);
+  if (pos) CK(cudaMemcpyAsync(pos, h->dbuf, sizeof(double) * n3, cudaMemcpyDeviceToHost, h->stream));
+  if (vel) CK(cudaMemcpyAsync(vel, h->dbuf + n3, sizeof(double) * n3, cudaMemcpyDeviceToHost, h->stream));
+  TrialState S;
+  CK(cudaMemcpyAsync(&S, h->d.tstate + trial, sizeof(S), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  if (cv) { cv[0] = S.z; cv[1] = S.zm; cv[2] = S.a; cv[3] = S.Phi; }
+  return SIM_OK;
+}
+
+VP_API int sim_set_state(sim_handle *h, int32_t trial, const double *pos, const double *vel, const double *cv_state) {
+  int r = enter(h);
+  if (r) return r;
+  if (!pos || !vel) return fail(h, SIM_EINVAL, "pos and vel are required");
+  if (trial < -1 || trial >= h->n_trials) return fail(h, SIM_EINVAL, "trial out of range");
+  int t0 = trial < 0 ? 0 : trial, t1 = trial < 0 ? h->n_trials : trial + 1;
+  size_t n = 0;
+  for (int t = t0; t < t1; ++t) n += (size_t)h->tinfo[t].n_atoms;
+  for (size_t k = 0; k < 3 * n; ++k)
+    if (!std::isfinite(pos[k]) || !std::isfinite(vel[k])) return fail(h, SIM_EINVAL, "non-finite state");
+  r = ensure_dbuf(h, 6 * n);
+  if (r) return r;
+  CK(cudaMemcpyAsync(h->dbuf, pos, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, h->stream));
+  CK(cudaMemcpyAsync(h->dbuf + 3 * n, vel, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, h->stream));
+  launch_scatter_state(h->d, trial, h->dbuf, h->dbuf + 3 * n, (int)n, h->stream);
+  // functional bookkeeping of the affected trials
+  std::vector<TrialState> S(h->n_trials);
+  CK(cudaMemcpyAsync(S.data(), h->d.tstate, sizeof(TrialState) * h->n_trials, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  for (int t = t0; t < t1; ++t) {
+    if (cv_state) {
+      S[t].zm = cv_state[2 * (t - t0)];
+      S[t].Phi = cv_state[2 * (t - t0) + 1];
+    } else {
+      S[t].zm = INFINITY;
+      S[t].Phi = 0.0;
+    }
+  }
+  CK(cudaMemcpyAsync(h->d.tstate, S.data(), sizeof(TrialState) * h->n_trials, cudaMemcpyHostToDevice, h->stream));
+  const Dev &d = h->d;
+  CK(cudaMemsetAsync(d.fx, 0, sizeof(long long) * d.total_slots, h->stream));
+  CK(cudaMemsetAsync(d.fy, 0, sizeof(long long) * d.total_slots, h->stream));
+  CK(cudaMemsetAsync(d.fz, 0, sizeof(long long) * d.total_slots, h->stream));
+  size_t ncv = 0;
+  for (auto &T : h->tinfo) ncv += T.n_cv;
+  if (ncv) {
+    CK(cudaMemsetAsync(d.gx, 0, sizeof(long long) * ncv, h->stream));
+    CK(cudaMemsetAsync(d.gy, 0, sizeof(long long) * ncv, h->stream));
+    CK(cudaMemsetAsync(d.gz, 0, sizeof(long long) * ncv, h->stream));
+  }
+  CK(cudaMemsetAsync(d.err, 0, sizeof(int), h->stream));
+  float half = 0.5f;
+  CK(cudaMemcpyAsync(d.kick, &half, sizeof(float), cudaMemcpyHostToDevice, h->stream));
+  rebuild(h);
+  forces(h, FIN_RESTORE);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(h->stream));
+  return check_flags(h);
+}
+
+VP_API int64_t sim_step_count(const sim_handle *h) { return h ? h->step : -1; }
+
+VP_API int sim_set_step_count(sim_handle *h, int64_t step) {
+  int r = enter(h);
+  if (r) return r;
+  if (step < 0) return fail(h, SIM_EINVAL, "negative step");
+  long long s = step;
+  CK(cudaMemcpyAsync(h->d.step, &s, sizeof(s), cudaMemcpyHostToDevice, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  h->step = step;
+  return SIM_OK;
+}
+
+VP_API int32_t sim_num_trials(const sim_handle *h) { return h ? h->n_trials : 0; }
+
+VP_API int32_t sim_num_atoms(const sim_handle *h, int32_t trial) {
+  if (!h || trial < 0 || trial >= h->n_trials) return 0;
+  return h->tinfo[trial].n_atoms;
+}
+
+VP_API int sim_record(sim_handle *h, int32_t capacity) {
+  int r = enter(h);
+  if (r) return r;
+  if (capacity < 0) return fail(h, SIM_EINVAL, "negative capacity");
+  if (h->d.rec) {
+    cudaFree(h->d.rec);
+    h->d.rec = nullptr;
+  }
+  h->rec_cap = capacity;
+  h->c.rec_cap = capacity;
+  if (h->chunk) {
+    cudaGraphExecDestroy(h->chunk);
+    h->chunk = nullptr;
+  }
+  if (capacity > 0) {
+    size_t n = (size_t)h->n_trials * capacity * 4;
+    CK(cudaMalloc(&h->d.rec, n * sizeof(double)));
+    CK(cudaMemset(h->d.rec, 0, n * sizeof(double)));
+  }
+  return SIM_OK;
+}
+
+VP_API int sim_get_record(sim_handle *h, int32_t trial, double *out) {
+  int r = enter(h);
+  if (r) return r;
+  if (trial < 0 || trial >= h->n_trials || !out || h->rec_cap <= 0) return fail(h, SIM_EINVAL, "no record");
+  size_t n = (size_t)h->rec_cap * 4;
+  CK(cudaMemcpyAsync(out, h->d.rec + (size_t)trial * n, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return SIM_OK;
+}
+
+VP_API int sim_pairlist(sim_handle *h, int32_t trial, int32_t *pairs, int64_t cap, int64_t *n_pairs) {
+  int r = enter(h);
+  if (r) return r;
+  if (trial < 0 || trial >= h->n_trials || cap < 0) return fail(h, SIM_EINVAL, "bad arguments");
+  TrialState S;
+  CK(cudaMemcpyAsync(&S, h->d.tstate + trial, sizeof(S), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaMemsetAsync(h->d_count, 0, sizeof(unsigned long long), h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  int32_t *dp = nullptr;
+  size_t nbytes = (size_t)std::max<int64_t>(cap, 1) * 2 * sizeof(int32_t);
+  CK(cudaMalloc(&dp, nbytes));
+  launch_extract_pairs(h->d, h->c.list_cap, trial, S.n_clus, dp, cap, h->d_count, h->stream);
+  unsigned long long cnt = 0;
+  cudaMemcpyAsync(&cnt, h->d_count, sizeof(cnt), cudaMemcpyDeviceToHost, h->stream);
+  cudaStreamSynchronize(h->stream);
+  int64_t keep = std::min<int64_t>((int64_t)cnt, cap);
+  cudaError_t e = cudaSuccess;
+  if (keep > 0 && pairs) e = cudaMemcpy(pairs, dp, (size_t)keep * 2 * sizeof(int32_t), cudaMemcpyDeviceToHost);
+  cudaFree(dp);
+  if (e != cudaSuccess) return fail(h, SIM_ECUDA, cudaGetErrorString(e));
+  if (n_pairs) *n_pairs = (int64_t)cnt;
+  return SIM_OK;
+}
+
+VP_API int sim_diagnostics(sim_handle *h, int64_t *out) {
+  int r = enter(h);
+  if (r) return r;
+  if (!out) return fail(h, SIM_EINVAL, "out is NULL");
+  long long skin = 0;
+  std::vector<int32_t> ln(h->d.total_clus);
+  std::vector<TrialState> S(h->n_trials);
+  CK(cudaMemcpyAsync(&skin, h->d.skin_count, sizeof(skin), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaMemcpyAsync(ln.data(), h->d.list_n, sizeof(int32_t) * ln.size(), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaMemcpyAsync(S.data(), h->d.tstate, sizeof(TrialState) * S.size(), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  int mx = 0;
+  for (int v : ln) mx = std::max(mx, v);
+  long long used = 0;
+  for (auto &s : S) used += s.n_clus;
+  out[0] = skin;
+  out[1] = mx;
+  out[2] = h->c.list_cap;
+  out[3] = used;
+  return SIM_OK;
+}
+
+VP_API int sim_set_timing(sim_handle *h, int32_t on) {
+  if (!h) return SIM_EINVAL;
+  h->timing = on != 0;
+  return SIM_OK;
+}
+
+VP_API int sim_kernel_times(sim_handle *h, const char **names, double *ms, int64_t *counts, int32_t cap) {
+  if (!h) return SIM_EINVAL;
+  int n = (int)h->timers.size();
+  for (int k = 0; k < n && k < cap; ++k) {
+    if (names) names[k] = h->timers[k].name;
+    if (ms) ms[k] = h->timers[k].ms;
+    if (counts) counts[k] = h->timers[k].count;
+  }
+  for (auto &t : h->timers) { t.ms = 0.0; t.count = 0; }
+  return n;
+}
+
+VP_API int sim_philox_normals(uint64_t seed, int64_t step, uint32_t stream, int32_t n, uint32_t *raw,
+                              double *normals) {
+  if (n < 0 || step < 0) return SIM_EINVAL;
+  if (n == 0) return SIM_OK;
+  uint32_t *draw = nullptr;
+  double *dnorm = nullptr;
+  if (cudaMalloc(&draw, sizeof(uint32_t) * 4 * (size_t)n) != cudaSuccess) return SIM_ECUDA;
+  if (cudaMalloc(&dnorm, sizeof(double) * 3 * (size_t)n) != cudaSuccess) {
+    cudaFree(draw);
+    return SIM_ECUDA;
+  }
+  launch_philox_normals(seed, (unsigned long long)step, stream, n, draw, dnorm, 0);
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e == cudaSuccess && raw) e = cudaMemcpy(raw, draw, sizeof(uint32_t) * 4 * (size_t)n, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && normals)
+    e = cudaMemcpy(normals, dnorm, sizeof(double) * 3 * (size_t)n, cudaMemcpyDeviceToHost);
+  cudaFree(draw);
+  cudaFree(dnorm);
+  return e == cudaSuccess ? SIM_OK : SIM_ECUDA;
+}
+
+VP_API void *sim_stream(sim_handle *h) { return h ? (void *)h->stream : nullptr; }
+
+VP_API void sim_destroy(sim_handle *h) {
+  if (!h) return;
+  cudaSetDevice(h->device);
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  if (h->chunk) cudaGraphExecDestroy(h->chunk);
+  for (void *p : h->allocs) cudaFree(p);
+  if (h->d.rec) cudaFree(h->d.rec);
+  if (h->dbuf) cudaFree(h->dbuf);
+  for (auto &t : h->timers)
+    for (auto &pr : t.ev) { cudaEventDestroy(pr.first); cudaEventDestroy(pr.second); }
+  if (h->entry_ev) cudaEventDestroy(h->entry_ev);
+  if (h->stream) cudaStreamDestroy(h->stream);
+  delete h;
+}
+
+VP_API const char *sim_last_error(const sim_handle *h) { return h ? h->err.c_str() : "null handle"; }

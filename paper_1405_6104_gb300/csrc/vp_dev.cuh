@@ -1,0 +1,87 @@
+// vp_dev.cuh -- the device buffers of one batch (passed by value to every
+// kernel) and the host launchers of all kernels.
+#pragma once
+#include "vp_internal.cuh"
+
+namespace vp {
+
+struct Dev {
+  int32_t n_trials, n_sys;
+  int32_t total_slots, total_clus, total_cols, total_work;
+  TrialInfo *tinfo;
+  TrialState *tstate;
+  // slots (cluster order); *_b are the targets of the re-sort at a rebuild
+  float4 *pos, *vel, *pos_b, *vel_b;   // pos.w = q*sqrt(f), vel.w = 1/m
+  int32_t *orig, *type, *orig_b, *type_b;
+  int32_t *slot_trial;                 // static: trial of every slot
+  int32_t *slot_col;                   // grid column of every slot at binning (-1: none)
+  long long *fx, *fy, *fz;             // fixed-point force accumulators per slot
+  // clusters
+  int32_t *clus_trial;                 // static: trial of every i-cluster
+  float4 *bb_lo, *bb_hi;               // bounding boxes (wrapped positions at rebuild)
+  uint2 *list;                         // [total_clus * list_cap]
+  int32_t *list_n;
+  // grid columns
+  int32_t *col_trial;                  // static
+  int32_t *col_count, *col_start, *col_cstart, *col_fill;
+  int32_t *bucket;                     // [total trial atoms]
+  // per trial, caller-ordered
+  int32_t *slot_of;                    // [total trial atoms]
+  float4 *ref_pos;                     // positions at the last rebuild
+  long long *gx, *gy, *gz;             // CV gradient, fixed point, [total CV atoms]
+  double *z_part;                      // [total_work] per-tile partial sums of z
+  // per system, caller-ordered
+  AtomSys *asys;
+  double *gm;                          // gamma_i m_i
+  int32_t *excl, *excl_n;              // [sys atoms * MAX_EXCL], counts
+  int32_t *bt_start;                   // [total system atoms + 1] CSR of owner-computed bonded terms
+  BTerm *bterm;
+  // reaction coordinate
+  int2 *tiles;                         // per system tile (bi, bj), concatenated
+  int2 *work;                          // flat (trial, global tile) work items
+  double *cnat;                        // [tiles * 1024] C~ of the native structure in tile-skew order
+  int32_t *sys_ncv, *sys_minsep;
+  // Lennard-Jones pair table over de-duplicated types
+  float2 *ljtab;                       // (6 c6, 12 c12)
+  float *ljshift;                      // potential at r_cut
+  // globals
+  int32_t *err;
+  long long *step;
+  float *kick;
+  unsigned int *done;                  // block ticket of the per-trial finaliser
+  long long *energy;                   // [n_trials * 5] fixed point (2^24): LJ, RF, bond, angle, kin
+  long long *skin_count;
+  double *rec;                         // [n_trials * rec_cap * 4]
+};
+
+enum UpdateMode { UPD_DRIFT = 0, UPD_FINAL = 1 };
+enum FinMode { FIN_STEP = 0, FIN_INIT = 1, FIN_RESTORE = 2 };
+
+// rebuild (vp_rebuild.cu)
+void launch_bin(const Dev &d, const SimConst &c, float half_skin2, int strict_skin, cudaStream_t s);
+void launch_colscan(const Dev &d, cudaStream_t s);
+void launch_colfill(const Dev &d, cudaStream_t s);
+void launch_colsort(const Dev &d, cudaStream_t s);
+void launch_list(const Dev &d, const SimConst &c, float rl2_bbox, cudaStream_t s);
+// forces (vp_pair.cu)
+void launch_pair(const Dev &d, const SimConst &c, bool energy, int32_t only_trial, cudaStream_t s);
+// reaction coordinate and functional (vp_cv.cu)
+void launch_cnat(const Dev &d, const SimConst &c, const double *native, const int32_t *sys_nat0, int32_t n_tiles_total,
+                 const int32_t *tile_sys, cudaStream_t s);
+void launch_zconst(const Dev &d, const int32_t *sys_tile0, const int32_t *sys_ntiles, cudaStream_t s);
+void launch_cv(const Dev &d, const SimConst &c, cudaStream_t s);
+void launch_cvfin(const Dev &d, const SimConst &c, FinMode mode, cudaStream_t s);
+// integrator and state (vp_update.cu)
+void launch_update(const Dev &d, const SimConst &c, UpdateMode mode, cudaStream_t s);
+void launch_init_vel(const Dev &d, float kT, const int32_t *need, cudaStream_t s);
+void launch_scatter_state(const Dev &d, int32_t trial, const double *pos, const double *vel, int32_t n, cudaStream_t s);
+void launch_gather_state(const Dev &d, int32_t trial, double *pos, double *vel, int32_t n, cudaStream_t s);
+void launch_forces_out(const Dev &d, const SimConst &c, int32_t trial, double *out, int32_t n, cudaStream_t s);
+void launch_kinetic(const Dev &d, int32_t trial, cudaStream_t s);
+void launch_extract_pairs(const Dev &d, int32_t list_cap, int32_t trial, int32_t n_clus, int32_t *pairs,
+                          long long cap, unsigned long long *count, cudaStream_t s);
+void launch_philox_normals(uint64_t seed, unsigned long long step, uint32_t stream, int n, uint32_t *raw,
+                           double *normals, cudaStream_t s);
+void launch_select(const Dev &d, double z_max, double *phi_out, int32_t *argmin_out, cudaStream_t s);
+
+}  // namespace vp

@@ -1,0 +1,242 @@
+// vp_pair.cu -- nonbonded (LJ + reaction field) and bonded forces.
+//
+// One warp per 8-atom i-cluster.  Lane (g, b) = (lane >> 2, lane & 3) takes
+// list entry e0 + g and holds atom b of that entry's 4-atom j-cluster; it
+// loops over the 8 i-atoms (kept in registers), so the force on its j-atom
+// is complete after the loop and goes to memory with one 64-bit fixed-point
+// reduction per component.  i-forces stay in registers over the whole list
+// and are reduced across the warp at the end.  FP32 pair arithmetic,
+// order-independent int64 accumulation (2^32 units per kJ/mol/nm), so the
+// forces are bit-reproducible.  The same warp adds the bonded forces of its
+// 8 atoms (each atom computes its own share of every bond and angle it is
+// part of).
+#include "vp_dev.cuh"
+
+namespace vp {
+
+// displacement x_p - x_self under the minimum image, with the image shift
+// subtracted from x_p first (exact when the two are within a box length)
+__device__ __forceinline__ float3 min_disp(float4 self, float4 other, float L, float iL) {
+  float nx = rintf((other.x - self.x) * iL), ny = rintf((other.y - self.y) * iL), nz = rintf((other.z - self.z) * iL);
+  return make_float3((other.x - L * nx) - self.x, (other.y - L * ny) - self.y, (other.z - L * nz) - self.z);
+}
+
+// force on one atom from its bonded terms (bonds: V = k/2 (r - r0)^2, angles
+// V = k/2 (theta - theta0)^2); eb/ea receive this atom's share of the energy
+__device__ float3 bonded_force(const Dev &d, const TrialInfo &T, int o, float4 self, float &eb, float &ea) {
+  float3 F = make_float3(0.f, 0.f, 0.f);
+  const int sa = T.sysatom0 + o;
+  const int b0 = d.bt_start[sa], b1 = d.bt_start[sa + 1];
+  const float L = T.box, iL = T.inv_box;
+  for (int k = b0; k < b1; ++k) {
+    const BTerm bt = d.bterm[k];
+    if (bt.kind == 0) {
+      float4 pp = d.pos[d.slot_of[T.atom0 + bt.p1]];
+      float3 dp = min_disp(self, pp, L, iL);  // partner - self
+      float r = sqrtf(dp.x * dp.x + dp.y * dp.y + dp.z * dp.z);
+      float dr = r - bt.x0;
+      float fs = bt.k * dr / r;  // force on self = +k dr (partner - self)/r
+      F.x += fs * dp.x; F.y += fs * dp.y; F.z += fs * dp.z;
+      eb += 0.25f * bt.k * dr * dr;
+    } else {
+      float4 p1 = d.pos[d.slot_of[T.atom0 + bt.p1]];
+      float4 p2 = d.pos[d.slot_of[T.atom0 + bt.p2]];
+      float3 d1 = min_disp(self, p1, L, iL), d2 = min_disp(self, p2, L, iL);
+      float3 u, v;
+      if (bt.kind == 1) {  // self is an end; p1 vertex, p2 other end
+        u = make_float3(-d1.x, -d1.y, -d1.z);
+        v = make_float3(d2.x - d1.x, d2.y - d1.y, d2.z - d1.z);
+      } else {  // self is the vertex; p1, p2 the ends
+        u = d1;
+        v = d2;
+      }
+      float uu = u.x * u.x + u.y * u.y + u.z * u.z, vv = v.x * v.x + v.y * v.y + v.z * v.z;
+      float iuv = rsqrtf(uu * vv);
+      float cs = (u.x * v.x + u.y * v.y + u.z * v.z) * iuv;
+      cs = fminf(1.0f, fmaxf(-1.0f, cs));
+      float th = acosf(cs);
+      float dth = th - bt.x0;
+      float sn = fmaxf(sqrtf(fmaxf(0.0f, 1.0f - cs * cs)), 1e-6f);
+      float g = bt.k * dth / sn;
+      float iuu = 1.0f / uu, ivv = 1.0f / vv;
+      // d cos / d u and d cos / d v
+      float3 du = make_float3(v.x * iuv - cs * u.x * iuu, v.y * iuv - cs * u.y * iuu, v.z * iuv - cs * u.z * iuu);
+      if (bt.kind == 1) {
+        F.x += g * du.x; F.y += g * du.y; F.z += g * du.z;
+      } else {
+        float3 dv = make_float3(u.x * iuv - cs * v.x * ivv, u.y * iuv - cs * v.y * ivv, u.z * iuv - cs * v.z * ivv);
+        F.x -= g * (du.x + dv.x); F.y -= g * (du.y + dv.y); F.z -= g * (du.z + dv.z);
+      }
+      ea += (0.5f / 3.0f) * bt.k * dth * dth;
+    }
+  }
+  return F;
+}
+
+template <bool ENERGY>
+__global__ void __launch_bounds__(128) k_pair(Dev d, SimConst c, int only_trial) {
+  __shared__ float2 tab[MAX_TYPES * MAX_TYPES];
+  __shared__ float tshift[ENERGY ? MAX_TYPES * MAX_TYPES : 1];
+  const int nt2 = c.n_types * c.n_types;
+  for (int k = threadIdx.x; k < nt2; k += blockDim.x) {
+    tab[k] = d.ljtab[k];
+    if (ENERGY) tshift[k] = d.ljshift[k];
+  }
+  __syncthreads();
+  const int I = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (I >= d.total_clus) return;
+  const int t = d.clus_trial[I];
+  if (only_trial >= 0 && t != only_trial) return;
+  const TrialInfo T = d.tinfo[t];
+  if (I - T.clus0 >= d.tstate[t].n_clus) return;
+  const float L = T.box, iL = T.inv_box;
+  const int g = lane >> 2, b = lane & 3;
+
+  float xi[CL], yi[CL], zi[CL], qi[CL];
+  int tio[CL];
+#pragma unroll
+  for (int a = 0; a < CL; ++a) {
+    float4 p = d.pos[I * CL + a];
+    xi[a] = p.x; yi[a] = p.y; zi[a] = p.z; qi[a] = p.w;
+    tio[a] = d.type[I * CL + a] * c.n_types;
+  }
+  float fi[CL][3];
+#pragma unroll
+  for (int a = 0; a < CL; ++a) fi[a][0] = fi[a][1] = fi[a][2] = 0.0f;
+  float elj = 0.0f, erf = 0.0f;
+
+  const int n = d.list_n[I];
+  const uint2 *seg = d.list + (size_t)I * c.list_cap;
+  for (int e0 = 0; e0 < n; e0 += 8) {
+    const int e = e0 + g;
+    const uint2 ent = e < n ? seg[e] : make_uint2(0u, 0u);
+    const int sj = (int)(ent.x & J_MASK) * CJ + b;
+    const unsigned code = (ent.x >> 26) & 31u;
+    const bool exact = (ent.x >> 31) != 0u;
+    const float4 pj = d.pos[sj];
+    const int tj = d.type[sj];
+    const int cx = (int)(code % 3u) - 1, cy = (int)((code / 3u) % 3u) - 1, cz = (int)(code / 9u) - 1;
+    const float xj = pj.x - L * cx, yj = pj.y - L * cy, zj = pj.z - L * cz;
+    const unsigned mb = ent.y >> b;
+    float fjx = 0.f, fjy = 0.f, fjz = 0.f;
+#pragma unroll
+    for (int a = 0; a < CL; ++a) {
+      float dx = xj - xi[a], dy = yj - yi[a], dz = zj - zi[a];
+      if (exact) {
+        dx -= L * rintf(dx * iL);
+        dy -= L * rintf(dy * iL);
+        dz -= L * rintf(dz * iL);
+      }
+      const float r2 = dx * dx + dy * dy + dz * dz;
+      const bool in = ((mb >> (4 * a)) & 1u) && (r2 < c.rc2);
+      const float rinv = rsqrtf(r2);
+      const float rinv2 = rinv * rinv;
+      const float rinv6 = rinv2 * rinv2 * rinv2;
+      const float2 cc = tab[tio[a] + tj];
+      const float qq = qi[a] * pj.w;
+      float f = rinv2 * (rinv6 * fmaf(cc.y, rinv6, -cc.x) + qq * rinv) - qq * c.two_krf;
+      f = in ? f : 0.0f;
+      fi[a][0] -= f * dx; fi[a][1] -= f * dy; fi[a][2] -= f * dz;
+      fjx += f * dx; fjy += f * dy; fjz += f * dz;
+      if (ENERGY && in) {
+        elj += rinv6 * (cc.y * (1.0f / 12.0f) * rinv6 - cc.x * (1.0f / 6.0f)) - tshift[tio[a] + tj];
+        erf += qq * (rinv + c.krf * r2 - c.crf);
+      }
+    }
+    if (!ENERGY && (mb & 0x11111111u)) {
+      red_add(d.fx + sj, fx_from(fjx));
+      red_add(d.fy + sj, fx_from(fjy));
+      red_add(d.fz + sj, fx_from(fjz));
+    }
+  }
+
+  // bonded terms of the 8 i-atoms (lanes 0..7)
+  float eb = 0.f, ea = 0.f;
+  if (lane < CL) {
+    const int o = d.orig[I * CL + lane];
+    if (o >= 0) {
+      float4 self = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+      for (int a = 0; a < CL; ++a)
+        if (a == lane) self = make_float4(xi[a], yi[a], zi[a], 0.f);
+      float3 fb = bonded_force(d, T, o, self, eb, ea);
+#pragma unroll
+      for (int a = 0; a < CL; ++a)
+        if (a == lane) { fi[a][0] += fb.x; fi[a][1] += fb.y; fi[a][2] += fb.z; }
+    }
+  }
+
+  if (!ENERGY) {
+    // reduce the 24 i-force partials over the warp: halve the set per step
+    float v[24];
+#pragma unroll
+    for (int a = 0; a < CL; ++a) { v[3 * a] = fi[a][0]; v[3 * a + 1] = fi[a][1]; v[3 * a + 2] = fi[a][2]; }
+    // step 1 (xor 16): 24 -> 12
+    {
+      const bool up = lane & 16;
+#pragma unroll
+      for (int k = 0; k < 12; ++k) {
+        float send = up ? v[k] : v[k + 12];
+        float keep = up ? v[k + 12] : v[k];
+        v[k] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+      }
+    }
+    // step 2 (xor 8): 12 -> 6
+    {
+      const bool up = lane & 8;
+#pragma unroll
+      for (int k = 0; k < 6; ++k) {
+        float send = up ? v[k] : v[k + 6];
+        float keep = up ? v[k + 6] : v[k];
+        v[k] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+      }
+    }
+    // step 3 (xor 4): 6 -> 3
+    {
+      const bool up = lane & 4;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        float send = up ? v[k] : v[k + 3];
+        float keep = up ? v[k + 3] : v[k];
+        v[k] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+      }
+    }
+    // steps 4-5: full sums over the remaining 4 lanes
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      v[k] += __shfl_xor_sync(0xffffffffu, v[k], 2);
+      v[k] += __shfl_xor_sync(0xffffffffu, v[k], 1);
+    }
+    // lane bits 4,3,2 select which 3 of the 24 values this lane now holds
+    if ((lane & 3) == 0) {
+      int idx = ((lane & 16) ? 12 : 0) + ((lane & 8) ? 6 : 0) + ((lane & 4) ? 3 : 0);
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        int q = idx + k;
+        int a = q / 3, comp = q - 3 * a;
+        int s = I * CL + a;
+        long long val = fx_from(v[k]);
+        if (val != 0) red_add((comp == 0 ? d.fx : comp == 1 ? d.fy : d.fz) + s, val);
+      }
+    }
+  } else {
+    double e4[4] = {(double)elj, (double)erf, (double)eb, (double)ea};
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) e4[k] += __shfl_xor_sync(0xffffffffu, e4[k], off);
+    if (lane == 0)
+#pragma unroll
+      for (int k = 0; k < 4; ++k) red_add(d.energy + (size_t)t * 5 + k, __double2ll_rn(e4[k] * E_SCALE));
+  }
+}
+
+void launch_pair(const Dev &d, const SimConst &c, bool energy, int32_t only_trial, cudaStream_t s) {
+  long long threads = (long long)d.total_clus * 32;
+  unsigned blocks = (unsigned)((threads + 127) / 128);
+  if (energy) k_pair<true><<<blocks, 128, 0, s>>>(d, c, only_trial);
+  else k_pair<false><<<blocks, 128, 0, s>>>(d, c, only_trial);
+}
+
+}  // namespace vp

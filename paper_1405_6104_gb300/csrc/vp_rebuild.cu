@@ -1,0 +1,346 @@
+// vp_rebuild.cu -- cell binning, spatial sort into 8-atom clusters and the
+// cluster-pair Verlet list (every nstlist steps).
+//
+// Layout: per trial the box is cut into ncol x ncol columns along x and y;
+// atoms are sorted by (column, z) and cut into clusters of 8 (the last
+// cluster of a column is padded).  A list entry pairs an 8-atom i-cluster
+// with a 4-atom j-cluster (half of an i-cluster) and carries a 32-bit mask of
+// the atom pairs that satisfy the FP32 list rule and are not excluded; the
+// half list keeps j-clusters whose parent cluster index is >= the i-cluster
+// (upper triangle inside a cluster).
+#include "vp_dev.cuh"
+
+namespace vp {
+
+// ---------------------------------------------------------------------------
+// binning: wrap into the box, pick the column, count, skin check
+// ---------------------------------------------------------------------------
+__global__ void k_bin(Dev d, float half_skin2, int strict) {
+  int slot = blockIdx.x * blockDim.x + threadIdx.x;
+  if (slot >= d.total_slots) return;
+  int t = d.slot_trial[slot];
+  const TrialInfo T = d.tinfo[t];
+  int local = slot - T.slot0;
+  int o = d.orig[slot];
+  if (local >= d.tstate[t].n_clus * CL || o < 0) { d.slot_col[slot] = -1; return; }
+  float4 p = d.pos[slot];
+  const float L = T.box, iL = T.inv_box;
+  float x = p.x - L * floorf(p.x * iL), y = p.y - L * floorf(p.y * iL), z = p.z - L * floorf(p.z * iL);
+  x = x >= L ? x - L : (x < 0.0f ? x + L : x);
+  y = y >= L ? y - L : (y < 0.0f ? y + L : y);
+  z = z >= L ? z - L : (z < 0.0f ? z + L : z);
+  z += 0.0f;  // no negative zero in the sort key
+  // displacement since the last rebuild (minimum image)
+  float4 r = d.ref_pos[T.atom0 + o];
+  float ddx = x - r.x, ddy = y - r.y, ddz = z - r.z;
+  ddx -= L * rintf(ddx * iL);
+  ddy -= L * rintf(ddy * iL);
+  ddz -= L * rintf(ddz * iL);
+  if (ddx * ddx + ddy * ddy + ddz * ddz > half_skin2) {
+    atomicAdd(reinterpret_cast<unsigned long long *>(d.skin_count), 1ull);
+    if (strict) atomicOr(d.err, ERR_SKIN);
+  }
+  if (!(isfinite(x) && isfinite(y) && isfinite(z))) {
+    atomicOr(d.err, ERR_NONFINITE);
+    x = y = z = 0.0f;
+  }
+  d.ref_pos[T.atom0 + o] = make_float4(x, y, z, 0.0f);
+  d.pos[slot] = make_float4(x, y, z, p.w);
+  int cx = min((int)(x * T.inv_col_w), T.ncol - 1);
+  int cy = min((int)(y * T.inv_col_w), T.ncol - 1);
+  int c = cx * T.ncol + cy;
+  d.slot_col[slot] = c;
+  atomicAdd(&d.col_count[T.col0 + c], 1);
+}
+
+// ---------------------------------------------------------------------------
+// per trial: exclusive scans of column atom counts and cluster counts
+// ---------------------------------------------------------------------------
+__global__ void k_colscan(Dev d) {
+  constexpr int NT = 256;
+  __shared__ int s_a[NT], s_c[NT];
+  int t = blockIdx.x;
+  const TrialInfo T = d.tinfo[t];
+  int nc = T.ncol * T.ncol;
+  int per = (nc + NT - 1) / NT;
+  int b = threadIdx.x * per, e = min(b + per, nc);
+  int sa = 0, sc = 0, bad = 0;
+  for (int c = b; c < e; ++c) {
+    int n = d.col_count[T.col0 + c];
+    bad |= n > COL_CAP;
+    sa += n;
+    sc += (n + CL - 1) / CL;
+  }
+  s_a[threadIdx.x] = sa;
+  s_c[threadIdx.x] = sc;
+  __syncthreads();
+  // Hillis-Steele inclusive scan over the thread sums (fixed order)
+  for (int off = 1; off < NT; off <<= 1) {
+    int va = threadIdx.x >= off ? s_a[threadIdx.x - off] : 0;
+    int vc = threadIdx.x >= off ? s_c[threadIdx.x - off] : 0;
+    __syncthreads();
+    s_a[threadIdx.x] += va;
+    s_c[threadIdx.x] += vc;
+    __syncthreads();
+  }
+  int pa = s_a[threadIdx.x] - sa, pc = s_c[threadIdx.x] - sc;
+  for (int c = b; c < e; ++c) {
+    int n = d.col_count[T.col0 + c];
+    d.col_start[T.col0 + c] = pa;
+    d.col_cstart[T.col0 + c] = pc;
+    d.col_fill[T.col0 + c] = 0;
+    pa += n;
+    pc += (n + CL - 1) / CL;
+  }
+  if (bad) atomicOr(d.err, ERR_COL);
+  if (threadIdx.x == NT - 1) {
+    int total = s_c[NT - 1];
+    if (total > T.max_clus) {
+      atomicOr(d.err, ERR_CAPACITY);
+      total = T.max_clus;
+    }
+    d.tstate[t].n_clus = total;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// scatter slot indices into their column buckets (unordered)
+// ---------------------------------------------------------------------------
+__global__ void k_colfill(Dev d) {
+  int slot = blockIdx.x * blockDim.x + threadIdx.x;
+  if (slot >= d.total_slots) return;
+  int c = d.slot_col[slot];
+  if (c < 0) return;
+  int t = d.slot_trial[slot];
+  const TrialInfo &T = d.tinfo[t];
+  int cg = T.col0 + c;
+  int p = atomicAdd(&d.col_fill[cg], 1);
+  if (p < COL_CAP && d.col_count[cg] <= COL_CAP) d.bucket[T.atom0 + d.col_start[cg] + p] = slot;
+}
+
+// ---------------------------------------------------------------------------
+// per column: sort by (z, atom index), write the new cluster layout, update
+// slot_of, pad the last cluster and compute cluster bounding boxes
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_colsort(Dev d) {
+  __shared__ unsigned long long key[COL_CAP];
+  __shared__ int s_old[COL_CAP];
+  int cg = blockIdx.x;
+  int t = d.col_trial[cg];
+  const TrialInfo T = d.tinfo[t];
+  int n = d.col_count[cg];
+  if (n > COL_CAP) return;  // flagged by k_colscan
+  int start = d.col_start[cg], cstart = d.col_cstart[cg];
+  if (cstart + (n + CL - 1) / CL > T.max_clus) return;  // flagged by k_colscan
+  int np2 = 1;
+  while (np2 < n) np2 <<= 1;
+  for (int i = threadIdx.x; i < np2; i += blockDim.x) {
+    if (i < n) {
+      int s = d.bucket[T.atom0 + start + i];
+      float z = d.pos[s].z;
+      key[i] = ((unsigned long long)__float_as_uint(z) << 32) | (unsigned)d.orig[s];
+    } else {
+      key[i] = ~0ull;
+    }
+  }
+  __syncthreads();
+  // bitonic sort, ascending
+  for (int k = 2; k <= np2; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = threadIdx.x; i < np2; i += blockDim.x) {
+        int ixj = i ^ j;
+        if (ixj > i) {
+          unsigned long long a = key[i], b = key[ixj];
+          bool up = (i & k) == 0;
+          if ((a > b) == up) { key[i] = b; key[ixj] = a; }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  for (int r = threadIdx.x; r < n; r += blockDim.x) {
+    int o = (int)(key[r] & 0xffffffffu);
+    s_old[r] = d.slot_of[T.atom0 + o];
+  }
+  __syncthreads();
+  int ncl = (n + CL - 1) / CL;
+  int base = T.slot0 + cstart * CL;
+  for (int r = threadIdx.x; r < ncl * CL; r += blockDim.x) {
+    int ns = base + r;
+    if (r < n) {
+      int old = s_old[r];
+      int o = (int)(key[r] & 0xffffffffu);
+      d.pos_b[ns] = d.pos[old];
+      d.vel_b[ns] = d.vel[old];
+      d.orig_b[ns] = o;
+      d.type_b[ns] = d.type[old];
+      d.slot_of[T.atom0 + o] = ns;
+    } else {
+      d.pos_b[ns] = make_float4(0.f, 0.f, 0.f, 0.f);
+      d.vel_b[ns] = make_float4(0.f, 0.f, 0.f, 0.f);
+      d.orig_b[ns] = -1;
+      d.type_b[ns] = 0;
+    }
+  }
+  // bounding boxes (from the sorted keys' slots)
+  for (int k = threadIdx.x; k < ncl; k += blockDim.x) {
+    float3 lo = make_float3(3e38f, 3e38f, 3e38f), hi = make_float3(-3e38f, -3e38f, -3e38f);
+    for (int a = 0; a < CL; ++a) {
+      int r = k * CL + a;
+      if (r >= n) break;
+      float4 p = d.pos[s_old[r]];
+      lo.x = fminf(lo.x, p.x); lo.y = fminf(lo.y, p.y); lo.z = fminf(lo.z, p.z);
+      hi.x = fmaxf(hi.x, p.x); hi.y = fmaxf(hi.y, p.y); hi.z = fmaxf(hi.z, p.z);
+    }
+    int ci = T.clus0 + cstart + k;
+    d.bb_lo[ci] = make_float4(lo.x, lo.y, lo.z, 0.f);
+    d.bb_hi[ci] = make_float4(hi.x, hi.y, hi.z, 0.f);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// cluster-pair list
+// ---------------------------------------------------------------------------
+// distance between two intervals on a circle of length L
+__device__ __forceinline__ float periodic_gap(float a0, float a1, float b0, float b1, float L) {
+  float g = 3e38f;
+#pragma unroll
+  for (int k = -1; k <= 1; ++k) {
+    float s = k * L;
+    float gg = fmaxf(0.0f, fmaxf(b0 + s - a1, a0 - (b1 + s)));
+    g = fminf(g, gg);
+  }
+  return g;
+}
+
+// the FP32 list rule (no contraction): d = xj - xi; d -= L*rint(d*invL);
+// r2 = (dx*dx + dy*dy) + dz*dz; member iff r2 < rl2.  Also returns the
+// image counts n (x_j image = x_j - L n).
+__device__ __forceinline__ bool list_rule(float4 pi, float4 pj, float L, float iL, float rl2, int &nx, int &ny,
+                                          int &nz) {
+  float dx = __fsub_rn(pj.x, pi.x), dy = __fsub_rn(pj.y, pi.y), dz = __fsub_rn(pj.z, pi.z);
+  float qx = rintf(__fmul_rn(dx, iL)), qy = rintf(__fmul_rn(dy, iL)), qz = rintf(__fmul_rn(dz, iL));
+  dx = __fsub_rn(dx, __fmul_rn(L, qx));
+  dy = __fsub_rn(dy, __fmul_rn(L, qy));
+  dz = __fsub_rn(dz, __fmul_rn(L, qz));
+  float r2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+  nx = (int)qx; ny = (int)qy; nz = (int)qz;
+  return r2 < rl2;
+}
+
+__device__ __forceinline__ bool is_excluded(const Dev &d, int sysatom, int oj) {
+  int n = d.excl_n[sysatom];
+  const int *e = d.excl + (size_t)sysatom * MAX_EXCL;
+  for (int k = 0; k < n; ++k)
+    if (e[k] == oj) return true;
+  return false;
+}
+
+__global__ void __launch_bounds__(128) k_list(Dev d, SimConst c, float rl2_bbox) {
+  int I = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  if (I >= d.total_clus) return;
+  int t = d.clus_trial[I];
+  const TrialInfo T = d.tinfo[t];
+  int Il = I - T.clus0;
+  int ncl_t = d.tstate[t].n_clus;
+  if (Il >= ncl_t) {
+    if (lane == 0) d.list_n[I] = 0;
+    return;
+  }
+  const int a = lane >> 2, b = lane & 3;
+  const int si = I * CL + a;
+  const float4 pi = d.pos[si];
+  const int oi = d.orig[si];
+  const int sys_i = T.sysatom0 + oi;
+  const float4 lo = d.bb_lo[I], hi = d.bb_hi[I];
+  const float L = T.box, iL = T.inv_box, w = T.col_w;
+  const int nc2 = T.ncol * T.ncol;
+  uint2 *seg = d.list + (size_t)I * c.list_cap;
+  int cnt = 0;
+  for (int cb = 0; cb < nc2; cb += 32) {
+    int cc = cb + lane;
+    bool pass = false;
+    int ccs = 0, ncl = 0;
+    if (cc < nc2) {
+      int n = d.col_count[T.col0 + cc];
+      ccs = d.col_cstart[T.col0 + cc];
+      ncl = (n + CL - 1) / CL;
+      if (ncl > 0 && ccs + ncl - 1 >= Il) {
+        int cx = cc / T.ncol, cy = cc - cx * T.ncol;
+        float gx = periodic_gap(lo.x, hi.x, cx * w, (cx + 1) * w, L);
+        float gy = periodic_gap(lo.y, hi.y, cy * w, (cy + 1) * w, L);
+        pass = gx * gx + gy * gy < rl2_bbox;
+      }
+    }
+    unsigned bal = __ballot_sync(0xffffffffu, pass);
+    while (bal) {
+      int src = __ffs(bal) - 1;
+      bal &= bal - 1;
+      int c_s = __shfl_sync(0xffffffffu, ccs, src);
+      int n_s = __shfl_sync(0xffffffffu, ncl, src);
+      for (int J8 = max(c_s, Il); J8 < c_s + n_s; ++J8) {
+        const int JG = T.clus0 + J8;
+        const float4 jlo = d.bb_lo[JG], jhi = d.bb_hi[JG];
+        float gx = periodic_gap(lo.x, hi.x, jlo.x, jhi.x, L);
+        float gy = periodic_gap(lo.y, hi.y, jlo.y, jhi.y, L);
+        float gz = periodic_gap(lo.z, hi.z, jlo.z, jhi.z, L);
+        if (gx * gx + gy * gy + gz * gz >= rl2_bbox) continue;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int sj = JG * CL + h * CJ + b;
+          const float4 pj = d.pos[sj];
+          const int oj = d.orig[sj];
+          int nx, ny, nz;
+          bool inr = list_rule(pi, pj, L, iL, c.rl2, nx, ny, nz);
+          bool valid = inr && oi >= 0 && oj >= 0 && (J8 != Il || sj > si);
+          if (valid) valid = !is_excluded(d, sys_i, oj);
+          unsigned m = __ballot_sync(0xffffffffu, valid);
+          if (m) {
+            int first = __ffs(m) - 1;
+            int fx = __shfl_sync(0xffffffffu, nx, first);
+            int fy = __shfl_sync(0xffffffffu, ny, first);
+            int fz = __shfl_sync(0xffffffffu, nz, first);
+            bool same = !valid || (nx == fx && ny == fy && nz == fz);
+            bool all_same = __all_sync(0xffffffffu, same);
+            unsigned code = (unsigned)((fx + 1) + 3 * (fy + 1) + 9 * (fz + 1));
+            unsigned w0 = (unsigned)(2 * JG + h) | (code << 26) | (all_same ? 0u : 0x80000000u);
+            if (lane == 0 && cnt < c.list_cap) seg[cnt] = make_uint2(w0, m);
+            ++cnt;
+          }
+        }
+      }
+    }
+  }
+  if (lane == 0) {
+    d.list_n[I] = min(cnt, c.list_cap);
+    if (cnt > c.list_cap) atomicOr(d.err, ERR_LIST);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+void launch_bin(const Dev &d, const SimConst &c, float half_skin2, int strict_skin, cudaStream_t s) {
+  (void)c;
+  cudaMemsetAsync(d.col_count, 0, sizeof(int32_t) * (size_t)d.total_cols, s);
+  k_bin<<<(d.total_slots + 255) / 256, 256, 0, s>>>(d, half_skin2, strict_skin);
+}
+void launch_colscan(const Dev &d, cudaStream_t s) { k_colscan<<<d.n_trials, 256, 0, s>>>(d); }
+void launch_colfill(const Dev &d, cudaStream_t s) {
+  k_colfill<<<(d.total_slots + 255) / 256, 256, 0, s>>>(d);
+}
+void launch_colsort(const Dev &d, cudaStream_t s) {
+  k_colsort<<<d.total_cols, 256, 0, s>>>(d);
+  size_t n = (size_t)d.total_slots;
+  cudaMemcpyAsync(d.pos, d.pos_b, n * sizeof(float4), cudaMemcpyDeviceToDevice, s);
+  cudaMemcpyAsync(d.vel, d.vel_b, n * sizeof(float4), cudaMemcpyDeviceToDevice, s);
+  cudaMemcpyAsync(d.orig, d.orig_b, n * sizeof(int32_t), cudaMemcpyDeviceToDevice, s);
+  cudaMemcpyAsync(d.type, d.type_b, n * sizeof(int32_t), cudaMemcpyDeviceToDevice, s);
+}
+void launch_list(const Dev &d, const SimConst &c, float rl2_bbox, cudaStream_t s) {
+  long long threads = (long long)d.total_clus * 32;
+  k_list<<<(unsigned)((threads + 127) / 128), 128, 0, s>>>(d, c, rl2_bbox);
+}
+
+}  // namespace vp

@@ -1,0 +1,226 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle on the
+same seeded inputs.  Tolerances: forces 1e-5 relative RMS, positions after
+100 steps 1e-4 nm, bias functional 1e-6 relative, neighbour lists
+bit-exact, Philox raw outputs bit-exact."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1405_6104_gb300 import binding as B
+from paper_1405_6104_gb300 import systems as S
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    from paper_1405_6104_gb300 import build
+    build.build()
+    B.load()
+
+
+def min_image(d, L):
+    return d - L * np.round(d / L)
+
+
+def rel_rms(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+SYSTEMS = {
+    "tiny": lambda: S.tiny_chain(0),
+    "small": lambda: S.small_solvated(),
+    "ragged": lambda: S.small_solvated(n_solute=37, n_water=301, seed=8, cv_min_sep=3),
+}
+
+
+def oracle_total_force(s, p, pos, a):
+    """-grad U + F^bias with the ratchet amplitude a (Eq. VR)."""
+    F, e = O.forces(s, p, pos, use_list=False)
+    if s.n_cv:
+        _, g = O.cv(s, p, pos)
+        F[: s.n_cv] += -0.5 * p.k_ratchet * a * g
+    return F, e
+
+
+# ---------------------------------------------------------------------------
+
+def test_philox_raw_bitexact_and_normals():
+    n = 2000
+    for seed, step, stream in [(0, 1, 0), (123456789012345, 77, 0), (1000, 0, 1), (2 ** 40 + 3, 2 ** 33 + 5, 0)]:
+        raw, nor = B.sim_philox_normals(seed, step, stream, n)
+        key = [seed & 0xFFFFFFFF, seed >> 32]
+        for o in range(0, n, 97):
+            ctr = [o, step & 0xFFFFFFFF, step >> 32, stream]
+            assert np.array_equal(raw[o], O.philox4x32_10(ctr, key))
+            assert np.abs(nor[o] - O.normal3(seed, o, step, stream)).max() < 2e-6
+
+
+@pytest.mark.parametrize("name", list(SYSTEMS))
+def test_pairlist_bitexact(name):
+    s, p = SYSTEMS[name]()
+    with B.TrialBatch(s, p, [1]) as b:
+        for n_steps in (0, 30):
+            b.step(n_steps)
+            pos, _, _ = b.get_state(0)  # the positions the last rebuild used
+            gpu = {tuple(x) for x in B.sim_pairlist(b.h, 0).tolist()}
+            ref = {tuple(x) for x in O.pairlist(s, pos.astype(np.float32), p.r_cut + p.skin).tolist()}
+            assert len(gpu) == len(B.sim_pairlist(b.h, 0))  # no duplicates
+            assert gpu == ref
+
+
+@pytest.mark.parametrize("name", list(SYSTEMS))
+def test_forces_and_energies_parity(name):
+    s, p = SYSTEMS[name]()
+    with B.TrialBatch(s, p, [1]) as b:
+        for n_steps in (0, 30, 5):
+            b.step(n_steps)
+            pos, vel, cv = b.get_state(0)
+            e, F = b.energy_forces(0)
+            Fr, er = oracle_total_force(s, p, pos, cv[2])
+            assert rel_rms(F, Fr) < 1e-5
+            scale = np.abs(er).sum() + 1.0
+            assert np.abs(e[:4] - er).max() < 1e-5 * scale
+            ekin = 0.5 * (s.mass[:, None] * vel ** 2).sum()
+            assert e[4] == pytest.approx(ekin, rel=1e-6)
+            assert e[5] == pytest.approx(0.25 * p.k_ratchet * cv[2] ** 2, rel=1e-12, abs=1e-300)
+            z, _ = O.cv(s, p, pos)
+            assert cv[0] == pytest.approx(z, rel=1e-10, abs=1e-10)
+
+
+@pytest.mark.parametrize("name", ["tiny", "small"])
+def test_trajectory_parity_100_steps(name):
+    s, p = SYSTEMS[name]()
+    seed = 4242
+    with B.TrialBatch(s, p, [1], trial_seeds=[seed]) as b:
+        b.step(100)
+        pos, vel, cv = b.get_state(0)
+    r = O.run(s, p, seed, 100)
+    assert r["status"] == 0
+    d = min_image(pos - r["pos"], s.box)
+    assert np.abs(d).max() < 1e-4
+    assert np.abs(vel - r["vel"]).max() < 1e-2 * np.abs(r["vel"]).max()
+
+
+@pytest.mark.parametrize("name", ["tiny", "small", "ragged"])
+def test_functional_parity_on_shared_states(name):
+    """The GPU's own frames are fed to the oracle: per-step z, a and the
+    accumulated Phi must agree (Phi to 1e-6 relative)."""
+    s, p = SYSTEMS[name]()
+    n = 100
+    with B.TrialBatch(s, p, [1], trial_seeds=[17]) as b:
+        B.sim_record(b.h, n + 1)
+        frames = [b.get_state(0)[0]]
+        for _ in range(n):
+            b.step(1)
+            frames.append(b.get_state(0)[0])
+        _, _, cv = b.get_state(0)
+        rec = B.sim_get_record(b.h, 0, n + 1)
+    Phi, z, a, phi = O.phi_frames(s, p, np.stack(frames))
+    assert Phi > 0
+    assert cv[3] == pytest.approx(Phi, rel=1e-6)
+    assert np.allclose(rec[:, 0], z, rtol=1e-11, atol=1e-11)
+    assert np.allclose(rec[1:, 2], a[1:], rtol=1e-6, atol=1e-9 * max(1.0, z.max()))
+    assert np.allclose(rec[1:, 3], phi[1:], rtol=1e-5, atol=1e-12 * max(1.0, phi.max()))
+
+
+def test_batch_invariance_and_determinism():
+    s1, p = S.tiny_chain(0)
+    s2, _ = S.small_solvated()
+    seeds = [5, 6, 7, 8]
+    with B.TrialBatch([s1, s2], p, [3, 1], trial_seeds=seeds) as b:
+        b.step(47)
+        batch = [b.get_state(t) for t in range(4)]
+    with B.TrialBatch(s1, p, [1], trial_seeds=[6]) as b:
+        b.step(47)
+        alone = b.get_state(0)
+    assert np.array_equal(batch[1][0], alone[0]) and np.array_equal(batch[1][1], alone[1])
+    assert batch[1][2][3] == alone[2][3]
+    with B.TrialBatch(s2, p, [1], trial_seeds=[8]) as b:
+        b.step(47)
+        alone2 = b.get_state(0)
+    assert np.array_equal(batch[3][0], alone2[0]) and batch[3][2][3] == alone2[2][3]
+    # graphs vs direct launches, and run-to-run: bit-identical
+    p_ng = S.Params(**{**p.__dict__, "flags": B.SIM_NO_GRAPH})
+    with B.TrialBatch([s1, s2], p_ng, [3, 1], trial_seeds=seeds) as b:
+        b.step(20)
+        b.step(27)
+        again = [b.get_state(t) for t in range(4)]
+    for x, y in zip(batch, again):
+        assert np.array_equal(x[0], y[0]) and np.array_equal(x[1], y[1]) and x[2][3] == y[2][3]
+
+
+def test_energy_conservation_without_friction():
+    s, p = S.tiny_chain(0)
+    p.gamma, p.k_ratchet = 0.0, 0.0
+    es = []
+    with B.TrialBatch(s, p, [1], trial_seeds=[3]) as b:
+        for _ in range(21):
+            e, _ = b.energy_forces(0, want_forces=False)
+            es.append(e[:5])
+            b.step(50)
+    es = np.array(es)
+    etot, ekin = es.sum(1), es[:, 4]
+    assert np.std(etot) < 0.02 * np.std(ekin)
+    assert abs(etot[-1] - etot[0]) / (1000 * p.dt) / s.n_atoms < 1e-3
+
+
+def test_selection_and_no_cv_system():
+    s, p = S.tiny_chain(0)
+    with B.TrialBatch(s, p, [6], trial_seeds=list(range(100, 106))) as b:
+        b.step(60)
+        phi, am = b.bias_functional()
+        assert am == int(np.argmin(phi)) and np.all(phi >= 0) and phi.max() > 0
+        zs = np.array([b.get_state(t)[2][0] for t in range(6)])
+        zmax = float(np.median(zs))
+        _, am2 = b.bias_functional(zmax)
+        ok = np.where(zs <= zmax)[0]
+        assert am2 == int(ok[np.argmin(phi[ok])])
+        _, am3 = b.bias_functional(0.0)  # no trial has reached z = 0
+        assert am3 == -1
+    s0 = s.copy()
+    s0.n_cv = 0
+    s0.native_pos = np.zeros((0, 3))
+    with B.TrialBatch(s0, p, [2]) as b:
+        b.step(25)
+        phi, _ = b.bias_functional()
+        assert np.all(phi == 0.0) and b.get_state(0)[2][0] == 0.0
+
+
+def test_recorded_functional_bookkeeping_and_restart():
+    s, p = S.small_solvated()
+    with B.TrialBatch(s, p, [2], trial_seeds=[1, 2]) as b:
+        B.sim_record(b.h, 64)
+        b.step(40)
+        rec = B.sim_get_record(b.h, 1, 64)[1:41]
+        pos, vel, cv = b.get_state(1)
+        assert cv[3] == pytest.approx(p.dt * rec[:, 3].sum(), rel=1e-12)
+        z, zm, a = rec[:, 0], rec[:, 1], rec[:, 2]
+        assert np.all(np.diff(zm) <= 0) and np.all(zm <= z + 1e-15)
+        # restart trial 1 from its own state with the functional carried over
+        b.set_state(1, pos, vel, cv_state=[cv[1], cv[3]])
+        _, _, cv2 = b.get_state(1)
+        assert cv2[3] == cv[3] and cv2[1] == pytest.approx(cv[1], rel=1e-12)
+        assert cv2[0] == pytest.approx(cv[0], rel=1e-12)
+
+
+@pytest.mark.slow
+def test_full_size_batch_sampled():
+    """64 trials of the 11 040-atom system in one batch (the benchmarked
+    configuration): sampled trials checked element by element."""
+    s, p, seeds = S.batched_64(1)
+    with B.TrialBatch(s, p, [64], trial_seeds=seeds) as b:
+        b.step(10)  # ends on a list rebuild
+        diag = B.sim_diagnostics(b.h)
+        assert diag["max_list_entries"] < diag["list_capacity"]
+        for t in (0, 37, 63):
+            pos, vel, cv = b.get_state(t)
+            e, F = b.energy_forces(t)
+            Fr, er = oracle_total_force(s, p, pos, cv[2])
+            assert rel_rms(F, Fr) < 1e-5
+            z, _ = O.cv(s, p, pos)
+            assert cv[0] == pytest.approx(z, rel=1e-11)
+        pos, _, _ = b.get_state(63)
+        gpu = {tuple(x) for x in B.sim_pairlist(b.h, 63).tolist()}
+        ref = {tuple(x) for x in O.pairlist(s, pos.astype(np.float32), p.r_cut + p.skin).tolist()}
+        assert gpu == ref
