@@ -100,14 +100,15 @@ void or_philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2], uint32
 
 /* Three standard normals for (trial seed, atom, step, stream): key = seed,
  * counter = (atom, step_lo, step_hi, stream).  Uniforms on the open interval
- * (0,1) from the top 24 bits, then Box-Muller on (u0,u1) and (u2,u3). */
+ * (0,1) from the top 23 bits, u = ((x >> 9) + 1/2) 2^-23 (a value that is
+ * exact in single precision too), then Box-Muller on (u0,u1) and (u2,u3). */
 void or_normal3(uint64_t seed, int64_t atom, int64_t step, uint32_t stream, double out[3]) {
   uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
   uint32_t ctr[4] = {(uint32_t)atom, (uint32_t)step, (uint32_t)((uint64_t)step >> 32), stream};
   uint32_t x[4];
   or_philox4x32_10(ctr, key, x);
   double u[4];
-  for (int k = 0; k < 4; ++k) u[k] = ((double)(x[k] >> 8) + 0.5) * (1.0 / 16777216.0);
+  for (int k = 0; k < 4; ++k) u[k] = ((double)(x[k] >> 9) + 0.5) * (1.0 / 8388608.0);
   const double two_pi = 6.283185307179586476925286766559;
   double r01 = sqrt(-2.0 * log(u[0]));
   double r23 = sqrt(-2.0 * log(u[2]));

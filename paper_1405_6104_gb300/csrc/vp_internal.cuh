@@ -105,13 +105,13 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
   return c;
 }
 
-// three normals from (key, atom, step, stream): uniforms ((x>>8)+1/2) 2^-24,
-// Box-Muller on (u0,u1) and (u2,u3)
+// three normals from (key, atom, step, stream): uniforms ((x>>9)+1/2) 2^-23
+// (exact in FP32), Box-Muller on (u0,u1) and (u2,u3)
 __device__ __forceinline__ float3 normal3(uint32_t k0, uint32_t k1, uint32_t atom, uint64_t step, uint32_t stream) {
   uint4 x = philox4x32_10(make_uint4(atom, (uint32_t)step, (uint32_t)(step >> 32), stream), k0, k1);
-  const float s24 = 5.9604644775390625e-08f;
-  float u0 = ((float)(x.x >> 8) + 0.5f) * s24, u1 = ((float)(x.y >> 8) + 0.5f) * s24;
-  float u2 = ((float)(x.z >> 8) + 0.5f) * s24, u3 = ((float)(x.w >> 8) + 0.5f) * s24;
+  const float s23 = 1.1920928955078125e-07f;
+  float u0 = ((float)(x.x >> 9) + 0.5f) * s23, u1 = ((float)(x.y >> 9) + 0.5f) * s23;
+  float u2 = ((float)(x.z >> 9) + 0.5f) * s23, u3 = ((float)(x.w >> 9) + 0.5f) * s23;
   float r01 = sqrtf(-2.0f * logf(u0)), r23 = sqrtf(-2.0f * logf(u2));
   float s1, c1;
   sincospif(2.0f * u1, &s1, &c1);
