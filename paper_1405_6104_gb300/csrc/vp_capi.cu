@@ -367,8 +367,9 @@ VP_API int sim_create(const sim_system *systems, int32_t n_systems, const int32_
       asys[a0 + i].c1 = (float)c1;
       asys[a0 + i].c2sd = (float)std::sqrt((1.0 - c1 * c1) * kT / S.mass[i]);
       asys[a0 + i].qs = (float)(S.charge[i] * sqf);
-      gm[a0 + i] = g * S.mass[i];
-      if (i < S.n_cv && !(g > 0.0)) return bail(fail(h, SIM_EINVAL, "reaction-coordinate atoms need gamma > 0"));
+      gm[a0 + i] = g > 0.0 ? g * S.mass[i] : INFINITY;  // no friction: no bias weight (k_R must be 0)
+      if (i < S.n_cv && !(g > 0.0) && p.k_ratchet != 0.0)
+        return bail(fail(h, SIM_EINVAL, "reaction-coordinate atoms need gamma > 0 when k_ratchet != 0"));
     }
     // exclusions: 1-2, 1-3 and the extra pairs
     auto add_ex = [&](int i, int j) -> bool {

@@ -31,12 +31,16 @@ __device__ float3 bonded_force(const Dev &d, const TrialInfo &T, int o, float4 s
   for (int k = b0; k < b1; ++k) {
     const BTerm bt = d.bterm[k];
     if (bt.kind == 0) {
+      // stiff springs: the stretch r - r0 in float-float (exact coordinate
+      // differences), so that k (r - r0) keeps FP32 relative accuracy
       float4 pp = d.pos[d.slot_of[T.atom0 + bt.p1]];
-      float3 dp = min_disp(self, pp, L, iL);  // partner - self
-      float r = sqrtf(dp.x * dp.x + dp.y * dp.y + dp.z * dp.z);
-      float dr = r - bt.x0;
-      float fs = bt.k * dr / r;  // force on self = +k dr (partner - self)/r
-      F.x += fs * dp.x; F.y += fs * dp.y; F.z += fs * dp.z;
+      const float nx = rintf((pp.x - self.x) * iL), ny = rintf((pp.y - self.y) * iL), nz = rintf((pp.z - self.z) * iL);
+      const ff dx = ff_diff(pp.x - L * nx, self.x), dy = ff_diff(pp.y - L * ny, self.y), dz = ff_diff(pp.z - L * nz, self.z);
+      const ff r2 = ff_add(ff_add(ff_sqr(dx), ff_sqr(dy)), ff_sqr(dz));
+      const ff r = ff_sqrt(r2);
+      const float dr = ff_add_f(r, -bt.x0).hi;
+      const float fs = bt.k * dr / r.hi;  // force on self = +k dr (partner - self)/r
+      F.x += fs * dx.hi; F.y += fs * dy.hi; F.z += fs * dz.hi;
       eb += 0.25f * bt.k * dr * dr;
     } else {
       float4 p1 = d.pos[d.slot_of[T.atom0 + bt.p1]];
