@@ -214,6 +214,7 @@ std::string check_system(const sim_system &s, const sim_params &p) {
   if (s.n_types < 1) return "n_types < 1";
   double rl = p.r_cut + p.skin;
   if (!(s.box > 2.0 * rl)) return "box must exceed 2 (r_cut + skin)";
+  if (!(s.box < 60.0)) return "box must be below 60 nm";
   for (int i = 0; i < s.n_atoms; ++i) {
     if (!(s.mass[i] > 0.0)) return "non-positive mass";
     if (s.lj_type[i] < 0 || s.lj_type[i] >= s.n_types) return "lj_type out of range";
@@ -492,6 +493,7 @@ VP_API int sim_create(const sim_system *systems, int32_t n_systems, const int32_
 
   // ---- initial slot contents (caller order, padded) --------------------------------
   std::vector<float4> pos(slot0), vel(slot0);
+  for (int k = 0; k < slot0; ++k) pos[k] = pad_pos(k);
   std::vector<int32_t> orig(slot0, -1), type(slot0, 0), slot_of(total_atoms > 0 ? total_atoms : 1);
   std::vector<float4> ref(total_atoms > 0 ? total_atoms : 1);
   std::vector<TrialState> tstate(total_trials);

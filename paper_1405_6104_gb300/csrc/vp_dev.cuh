@@ -19,7 +19,7 @@ struct Dev {
   // clusters
   int32_t *clus_trial;                 // static: trial of every i-cluster
   float4 *bb_lo, *bb_hi;               // bounding boxes (wrapped positions at rebuild)
-  uint2 *list;                         // [total_clus * list_cap]
+  uint2 *list;                         // [total_clus * list_cap] entries (see vp_internal.cuh)
   int32_t *list_n;
   // grid columns
   int32_t *col_trial;                  // static

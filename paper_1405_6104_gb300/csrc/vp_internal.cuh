@@ -29,9 +29,26 @@ constexpr int ERR_NONFINITE = 4;
 constexpr int ERR_CAPACITY = 8;
 constexpr int ERR_SKIN = 16;
 
-// list entry: word0 = j-cluster (26 bits) | shift code (5 bits) | exact-image flag (bit 31)
-//             word1 = 32-bit interaction mask, bit (a*4 + b) for i-atom a, j-atom b
-constexpr uint32_t J_MASK = (1u << 26) - 1u;
+// list entry (uint2):
+//   x = 4-atom j-cluster index (bits 0-24) | image shift (bits 25-30: nx+1,
+//       ny+1, nz+1, two bits each; x_j image = x_j - L n) | E_EXACT (bit 31)
+//       when the pairs of the entry do not share one image (the kernel then
+//       takes the minimum image pair by pair)
+//   y = mask: bit (a*4 + b) set when i-atom a and j-atom b satisfy the FP32
+//       list rule, are not excluded, are real atoms and (for the cluster
+//       with itself) b's slot follows a's -- the Verlet list proper
+constexpr uint32_t J_BITS = 25;
+constexpr uint32_t J_MASK = (1u << J_BITS) - 1u;
+constexpr uint32_t E_EXACT = 1u << 31;
+
+// Padding slots sit far outside every box, on distinct points 64 nm apart,
+// so that no pair involving one can fall inside the cut-off (boxes < 60 nm).
+__host__ __device__ __forceinline__ float4 pad_pos(int slot) {
+  return make_float4(1.0e6f + 64.0f * (float)(slot & 0xffff), 1.0e6f + 64.0f * (float)((slot >> 16) & 0xffff),
+                     1.0e6f, 0.0f);
+}
+// stand-in j-atom for idle lanes: far from every real and padding slot
+__host__ __device__ __forceinline__ float4 idle_pos() { return make_float4(1.0e6f, 1.0e6f, 3.0e6f, 0.0f); }
 
 // ---------------------------------------------------------------------------
 // per-trial static description (device copy, read-only after create)

@@ -79,8 +79,10 @@ __device__ float3 bonded_force(const Dev &d, const TrialInfo &T, int o, float4 s
 
 template <bool ENERGY>
 __global__ void __launch_bounds__(128) k_pair(Dev d, SimConst c, int only_trial) {
-  __shared__ float2 tab[MAX_TYPES * MAX_TYPES];
-  __shared__ float tshift[ENERGY ? MAX_TYPES * MAX_TYPES : 1];
+  extern __shared__ float2 smem_tab[];
+  __shared__ float s_red[ENERGY ? 1 : 4][ENERGY ? 1 : 3 * CL * 33];
+  float2 *tab = smem_tab;
+  float *tshift = reinterpret_cast<float *>(smem_tab + c.n_types * c.n_types);
   const int nt2 = c.n_types * c.n_types;
   for (int k = threadIdx.x; k < nt2; k += blockDim.x) {
     tab[k] = d.ljtab[k];
@@ -112,47 +114,81 @@ __global__ void __launch_bounds__(128) k_pair(Dev d, SimConst c, int only_trial)
 
   const int n = d.list_n[I];
   const uint2 *seg = d.list + (size_t)I * c.list_cap;
+  // software pipeline: the entry two groups ahead and the j-atom of the next
+  // group are in flight while the current group is evaluated; idle lanes get
+  // an empty mask
+  uint2 ent = g < n ? seg[g] : make_uint2(0u, 0u);
+  uint2 ent_n = 8 + g < n ? seg[8 + g] : make_uint2(0u, 0u);
+  float4 pj = d.pos[(int)(ent.x & J_MASK) * CJ + b];
+  int tj = d.type[(int)(ent.x & J_MASK) * CJ + b];
   for (int e0 = 0; e0 < n; e0 += 8) {
-    const int e = e0 + g;
-    const uint2 ent = e < n ? seg[e] : make_uint2(0u, 0u);
+    const uint2 ent_nn = e0 + 16 + g < n ? seg[e0 + 16 + g] : make_uint2(0u, 0u);
+    const int sj_n = (int)(ent_n.x & J_MASK) * CJ + b;
+    const float4 pj_n = d.pos[sj_n];
+    const int tj_n = d.type[sj_n];
     const int sj = (int)(ent.x & J_MASK) * CJ + b;
-    const unsigned code = (ent.x >> 26) & 31u;
-    const bool exact = (ent.x >> 31) != 0u;
-    const float4 pj = d.pos[sj];
-    const int tj = d.type[sj];
-    const int cx = (int)(code % 3u) - 1, cy = (int)((code / 3u) % 3u) - 1, cz = (int)(code / 9u) - 1;
-    const float xj = pj.x - L * cx, yj = pj.y - L * cy, zj = pj.z - L * cz;
+    const unsigned sh = ent.x >> J_BITS;
+    const float xj = pj.x - L * (float)((int)(sh & 3u) - 1);
+    const float yj = pj.y - L * (float)((int)((sh >> 2) & 3u) - 1);
+    const float zj = pj.z - L * (float)((int)((sh >> 4) & 3u) - 1);
     const unsigned mb = ent.y >> b;
+    const bool exact = (ent.x & E_EXACT) != 0u;
     float fjx = 0.f, fjy = 0.f, fjz = 0.f;
+    if (!__any_sync(0xffffffffu, exact)) {
 #pragma unroll
-    for (int a = 0; a < CL; ++a) {
-      float dx = xj - xi[a], dy = yj - yi[a], dz = zj - zi[a];
-      if (exact) {
-        dx -= L * rintf(dx * iL);
-        dy -= L * rintf(dy * iL);
-        dz -= L * rintf(dz * iL);
+      for (int a = 0; a < CL; ++a) {
+        const float dx = xj - xi[a], dy = yj - yi[a], dz = zj - zi[a];
+        const float r2 = dx * dx + dy * dy + dz * dz;
+        const bool in = ((mb >> (4 * a)) & 1u) && (r2 < c.rc2);
+        const float rinv = rsqrtf(r2);
+        const float rinv2 = rinv * rinv;
+        const float rinv6 = rinv2 * rinv2 * rinv2;
+        const float2 cc = tab[tio[a] + tj];
+        const float qq = qi[a] * pj.w;
+        float f = rinv2 * (rinv6 * fmaf(cc.y, rinv6, -cc.x) + qq * rinv) - qq * c.two_krf;
+        f = in ? f : 0.0f;
+        fi[a][0] -= f * dx; fi[a][1] -= f * dy; fi[a][2] -= f * dz;
+        fjx += f * dx; fjy += f * dy; fjz += f * dz;
+        if (ENERGY && in) {
+          elj += rinv6 * (cc.y * (1.0f / 12.0f) * rinv6 - cc.x * (1.0f / 6.0f)) - tshift[tio[a] + tj];
+          erf += qq * (rinv + c.krf * r2 - c.crf);
+        }
       }
-      const float r2 = dx * dx + dy * dy + dz * dz;
-      const bool in = ((mb >> (4 * a)) & 1u) && (r2 < c.rc2);
-      const float rinv = rsqrtf(r2);
-      const float rinv2 = rinv * rinv;
-      const float rinv6 = rinv2 * rinv2 * rinv2;
-      const float2 cc = tab[tio[a] + tj];
-      const float qq = qi[a] * pj.w;
-      float f = rinv2 * (rinv6 * fmaf(cc.y, rinv6, -cc.x) + qq * rinv) - qq * c.two_krf;
-      f = in ? f : 0.0f;
-      fi[a][0] -= f * dx; fi[a][1] -= f * dy; fi[a][2] -= f * dz;
-      fjx += f * dx; fjy += f * dy; fjz += f * dz;
-      if (ENERGY && in) {
-        elj += rinv6 * (cc.y * (1.0f / 12.0f) * rinv6 - cc.x * (1.0f / 6.0f)) - tshift[tio[a] + tj];
-        erf += qq * (rinv + c.krf * r2 - c.crf);
+    } else {
+#pragma unroll
+      for (int a = 0; a < CL; ++a) {
+        float dx = xj - xi[a], dy = yj - yi[a], dz = zj - zi[a];
+        if (exact) {
+          dx -= L * rintf(dx * iL);
+          dy -= L * rintf(dy * iL);
+          dz -= L * rintf(dz * iL);
+        }
+        const float r2 = dx * dx + dy * dy + dz * dz;
+        const bool in = ((mb >> (4 * a)) & 1u) && (r2 < c.rc2);
+        const float rinv = rsqrtf(r2);
+        const float rinv2 = rinv * rinv;
+        const float rinv6 = rinv2 * rinv2 * rinv2;
+        const float2 cc = tab[tio[a] + tj];
+        const float qq = qi[a] * pj.w;
+        float f = rinv2 * (rinv6 * fmaf(cc.y, rinv6, -cc.x) + qq * rinv) - qq * c.two_krf;
+        f = in ? f : 0.0f;
+        fi[a][0] -= f * dx; fi[a][1] -= f * dy; fi[a][2] -= f * dz;
+        fjx += f * dx; fjy += f * dy; fjz += f * dz;
+        if (ENERGY && in) {
+          elj += rinv6 * (cc.y * (1.0f / 12.0f) * rinv6 - cc.x * (1.0f / 6.0f)) - tshift[tio[a] + tj];
+          erf += qq * (rinv + c.krf * r2 - c.crf);
+        }
       }
     }
-    if (!ENERGY && (mb & 0x11111111u)) {
+    if (!ENERGY && (fjx != 0.f || fjy != 0.f || fjz != 0.f)) {
       red_add(d.fx + sj, fx_from(fjx));
       red_add(d.fy + sj, fx_from(fjy));
       red_add(d.fz + sj, fx_from(fjz));
     }
+    ent = ent_n;
+    ent_n = ent_nn;
+    pj = pj_n;
+    tj = tj_n;
   }
 
   // bonded terms of the 8 i-atoms (lanes 0..7)
@@ -172,57 +208,19 @@ __global__ void __launch_bounds__(128) k_pair(Dev d, SimConst c, int only_trial)
   }
 
   if (!ENERGY) {
-    // reduce the 24 i-force partials over the warp: halve the set per step
-    float v[24];
+    // i-forces: column sums of the 32 lanes' partials in a fixed order
+    float *r = s_red[threadIdx.x >> 5];
 #pragma unroll
-    for (int a = 0; a < CL; ++a) { v[3 * a] = fi[a][0]; v[3 * a + 1] = fi[a][1]; v[3 * a + 2] = fi[a][2]; }
-    // step 1 (xor 16): 24 -> 12
-    {
-      const bool up = lane & 16;
+    for (int a = 0; a < CL; ++a)
 #pragma unroll
-      for (int k = 0; k < 12; ++k) {
-        float send = up ? v[k] : v[k + 12];
-        float keep = up ? v[k + 12] : v[k];
-        v[k] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
-      }
-    }
-    // step 2 (xor 8): 12 -> 6
-    {
-      const bool up = lane & 8;
-#pragma unroll
-      for (int k = 0; k < 6; ++k) {
-        float send = up ? v[k] : v[k + 6];
-        float keep = up ? v[k + 6] : v[k];
-        v[k] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
-      }
-    }
-    // step 3 (xor 4): 6 -> 3
-    {
-      const bool up = lane & 4;
-#pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        float send = up ? v[k] : v[k + 3];
-        float keep = up ? v[k + 3] : v[k];
-        v[k] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
-      }
-    }
-    // steps 4-5: full sums over the remaining 4 lanes
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      v[k] += __shfl_xor_sync(0xffffffffu, v[k], 2);
-      v[k] += __shfl_xor_sync(0xffffffffu, v[k], 1);
-    }
-    // lane bits 4,3,2 select which 3 of the 24 values this lane now holds
-    if ((lane & 3) == 0) {
-      int idx = ((lane & 16) ? 12 : 0) + ((lane & 8) ? 6 : 0) + ((lane & 4) ? 3 : 0);
-#pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        int q = idx + k;
-        int a = q / 3, comp = q - 3 * a;
-        int s = I * CL + a;
-        long long val = fx_from(v[k]);
-        if (val != 0) red_add((comp == 0 ? d.fx : comp == 1 ? d.fy : d.fz) + s, val);
-      }
+      for (int k = 0; k < 3; ++k) r[(3 * a + k) * 33 + lane] = fi[a][k];
+    __syncwarp();
+    if (lane < 3 * CL) {
+      float sum = 0.f;
+      for (int l = 0; l < 32; ++l) sum += r[lane * 33 + l];
+      const int a = lane / 3, comp = lane - 3 * a;
+      const long long val = fx_from(sum);
+      if (val != 0) red_add((comp == 0 ? d.fx : comp == 1 ? d.fy : d.fz) + I * CL + a, val);
     }
   } else {
     double e4[4] = {(double)elj, (double)erf, (double)eb, (double)ea};
@@ -239,8 +237,9 @@ __global__ void __launch_bounds__(128) k_pair(Dev d, SimConst c, int only_trial)
 void launch_pair(const Dev &d, const SimConst &c, bool energy, int32_t only_trial, cudaStream_t s) {
   long long threads = (long long)d.total_clus * 32;
   unsigned blocks = (unsigned)((threads + 127) / 128);
-  if (energy) k_pair<true><<<blocks, 128, 0, s>>>(d, c, only_trial);
-  else k_pair<false><<<blocks, 128, 0, s>>>(d, c, only_trial);
+  const size_t nt2 = (size_t)c.n_types * c.n_types;
+  if (energy) k_pair<true><<<blocks, 128, nt2 * (sizeof(float2) + sizeof(float)), s>>>(d, c, only_trial);
+  else k_pair<false><<<blocks, 128, nt2 * sizeof(float2), s>>>(d, c, only_trial);
 }
 
 }  // namespace vp

@@ -176,7 +176,7 @@ __global__ void __launch_bounds__(256) k_colsort(Dev d) {
       d.type_b[ns] = d.type[old];
       d.slot_of[T.atom0 + o] = ns;
     } else {
-      d.pos_b[ns] = make_float4(0.f, 0.f, 0.f, 0.f);
+      d.pos_b[ns] = pad_pos(ns);
       d.vel_b[ns] = make_float4(0.f, 0.f, 0.f, 0.f);
       d.orig_b[ns] = -1;
       d.type_b[ns] = 0;
@@ -228,93 +228,160 @@ __device__ __forceinline__ bool list_rule(float4 pi, float4 pj, float L, float i
   return r2 < rl2;
 }
 
-__device__ __forceinline__ bool is_excluded(const Dev &d, int sysatom, int oj) {
-  int n = d.excl_n[sysatom];
-  const int *e = d.excl + (size_t)sysatom * MAX_EXCL;
-  for (int k = 0; k < n; ++k)
-    if (e[k] == oj) return true;
-  return false;
-}
+constexpr int LIST_WARPS = 4;
+constexpr int CAND_MAX = 512;  // candidate 8-atom clusters per i-cluster (bounding-box pass)
 
-__global__ void __launch_bounds__(128) k_list(Dev d, SimConst c, float rl2_bbox) {
-  int I = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  int lane = threadIdx.x & 31;
+// One warp per i-cluster.  Phase 1: lanes test columns, then the clusters of
+// each passing column, against the i-cluster's bounding box and collect the
+// candidates in order (column-major, then z).  Phase 2: each lane takes one
+// candidate 4-atom j-cluster and evaluates the FP32 list rule for all 8 x 4
+// atom pairs itself, giving the entry's mask, image code and exact flag;
+// entries are written in candidate order (deterministic).
+__global__ void __launch_bounds__(LIST_WARPS * 32) k_list(Dev d, SimConst c, float rl2_bbox) {
+  __shared__ int s_cand[LIST_WARPS][CAND_MAX];
+  __shared__ int s_excl[LIST_WARPS][CL][MAX_EXCL];
+  __shared__ int s_nex[LIST_WARPS][CL];
+  const int wib = threadIdx.x >> 5;
+  const int I = blockIdx.x * LIST_WARPS + wib;
+  const int lane = threadIdx.x & 31;
   if (I >= d.total_clus) return;
-  int t = d.clus_trial[I];
+  const int t = d.clus_trial[I];
   const TrialInfo T = d.tinfo[t];
-  int Il = I - T.clus0;
-  int ncl_t = d.tstate[t].n_clus;
-  if (Il >= ncl_t) {
+  const int Il = I - T.clus0;
+  if (Il >= d.tstate[t].n_clus) {
     if (lane == 0) d.list_n[I] = 0;
     return;
   }
-  const int a = lane >> 2, b = lane & 3;
-  const int si = I * CL + a;
-  const float4 pi = d.pos[si];
-  const int oi = d.orig[si];
-  const int sys_i = T.sysatom0 + oi;
   const float4 lo = d.bb_lo[I], hi = d.bb_hi[I];
   const float L = T.box, iL = T.inv_box, w = T.col_w;
   const int nc2 = T.ncol * T.ncol;
-  uint2 *seg = d.list + (size_t)I * c.list_cap;
-  int cnt = 0;
+  int *cand = s_cand[wib];
+  int n_cand = 0;
+  bool overflow = false;
+  // ---- phase 1: candidate clusters ----
+  // lanes test 32 columns; the clusters (index >= Il) of the passing columns
+  // are then enumerated as one flat range, 32 per step, so that the
+  // bounding-box loads of a whole step are in flight together
   for (int cb = 0; cb < nc2; cb += 32) {
-    int cc = cb + lane;
-    bool pass = false;
-    int ccs = 0, ncl = 0;
+    const int cc = cb + lane;
+    int jlo = 0, cntc = 0;
     if (cc < nc2) {
-      int n = d.col_count[T.col0 + cc];
-      ccs = d.col_cstart[T.col0 + cc];
-      ncl = (n + CL - 1) / CL;
-      if (ncl > 0 && ccs + ncl - 1 >= Il) {
-        int cx = cc / T.ncol, cy = cc - cx * T.ncol;
-        float gx = periodic_gap(lo.x, hi.x, cx * w, (cx + 1) * w, L);
-        float gy = periodic_gap(lo.y, hi.y, cy * w, (cy + 1) * w, L);
-        pass = gx * gx + gy * gy < rl2_bbox;
+      const int n = d.col_count[T.col0 + cc];
+      const int ccs = d.col_cstart[T.col0 + cc];
+      const int ncl = (n + CL - 1) / CL;
+      jlo = max(ccs, Il);
+      if (ccs + ncl > jlo) {
+        const int cx = cc / T.ncol, cy = cc - cx * T.ncol;
+        const float gx = periodic_gap(lo.x, hi.x, cx * w, (cx + 1) * w, L);
+        const float gy = periodic_gap(lo.y, hi.y, cy * w, (cy + 1) * w, L);
+        if (gx * gx + gy * gy < rl2_bbox) cntc = ccs + ncl - jlo;
       }
     }
-    unsigned bal = __ballot_sync(0xffffffffu, pass);
-    while (bal) {
-      int src = __ffs(bal) - 1;
-      bal &= bal - 1;
-      int c_s = __shfl_sync(0xffffffffu, ccs, src);
-      int n_s = __shfl_sync(0xffffffffu, ncl, src);
-      for (int J8 = max(c_s, Il); J8 < c_s + n_s; ++J8) {
-        const int JG = T.clus0 + J8;
-        const float4 jlo = d.bb_lo[JG], jhi = d.bb_hi[JG];
-        float gx = periodic_gap(lo.x, hi.x, jlo.x, jhi.x, L);
-        float gy = periodic_gap(lo.y, hi.y, jlo.y, jhi.y, L);
-        float gz = periodic_gap(lo.z, hi.z, jlo.z, jhi.z, L);
-        if (gx * gx + gy * gy + gz * gz >= rl2_bbox) continue;
+    // inclusive scan of the per-column candidate counts
+    int incl = cntc;
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const int sj = JG * CL + h * CJ + b;
-          const float4 pj = d.pos[sj];
-          const int oj = d.orig[sj];
+    for (int off = 1; off < 32; off <<= 1) {
+      const int v = __shfl_up_sync(0xffffffffu, incl, off);
+      if (lane >= off) incl += v;
+    }
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    for (int t0 = 0; t0 < total; t0 += 32) {
+      const int tt = t0 + lane;
+      const int tq = min(tt, total - 1);
+      // owner column: first lane whose inclusive count exceeds tq (all lanes search)
+      int lo_l = 0, hi_l = 31;
+#pragma unroll
+      for (int it = 0; it < 5; ++it) {
+        const int mid = (lo_l + hi_l) >> 1;
+        const int v = __shfl_sync(0xffffffffu, incl, mid);
+        if (v > tq) hi_l = mid; else lo_l = mid + 1;
+      }
+      const int own_incl = __shfl_sync(0xffffffffu, incl, lo_l);
+      const int own_cnt = __shfl_sync(0xffffffffu, cntc, lo_l);
+      const int own_jlo = __shfl_sync(0xffffffffu, jlo, lo_l);
+      bool ok = false;
+      int J8 = 0;
+      if (tt < total) {
+        J8 = own_jlo + (tt - (own_incl - own_cnt));
+        const float4 jlo4 = d.bb_lo[T.clus0 + J8], jhi4 = d.bb_hi[T.clus0 + J8];
+        const float gx = periodic_gap(lo.x, hi.x, jlo4.x, jhi4.x, L);
+        const float gy = periodic_gap(lo.y, hi.y, jlo4.y, jhi4.y, L);
+        const float gz = periodic_gap(lo.z, hi.z, jlo4.z, jhi4.z, L);
+        ok = gx * gx + gy * gy + gz * gz < rl2_bbox;
+      }
+      const unsigned m = __ballot_sync(0xffffffffu, ok);
+      const int pos = n_cand + __popc(m & ((1u << lane) - 1u));
+      if (ok && pos < CAND_MAX) cand[pos] = J8;
+      n_cand += __popc(m);
+    }
+  }
+  if (n_cand > CAND_MAX) {
+    overflow = true;
+    n_cand = CAND_MAX;
+  }
+  // i-atoms and their exclusions
+  float xi[CL], yi[CL], zi[CL];
+  int oi[CL];
+#pragma unroll
+  for (int a = 0; a < CL; ++a) {
+    const float4 p = d.pos[I * CL + a];
+    xi[a] = p.x; yi[a] = p.y; zi[a] = p.z;
+    oi[a] = d.orig[I * CL + a];
+  }
+  if (lane < CL) {
+    const int o = d.orig[I * CL + lane];
+    const int sa = T.sysatom0 + (o < 0 ? 0 : o);
+    const int n = o < 0 ? 0 : d.excl_n[sa];
+    s_nex[wib][lane] = n;
+    for (int k = 0; k < n; ++k) s_excl[wib][lane][k] = d.excl[(size_t)sa * MAX_EXCL + k];
+  }
+  __syncwarp();
+  // ---- phase 2: one candidate 4-atom j-cluster per lane ----
+  uint2 *seg = d.list + (size_t)I * c.list_cap;
+  const float rl2 = c.rl2;
+  int cnt = 0;
+  for (int k0 = 0; k0 < 2 * n_cand; k0 += 32) {
+    const int k = k0 + lane;
+    unsigned mask = 0u, w0 = 0u;
+    if (k < 2 * n_cand) {
+      const int J8 = cand[k >> 1], h = k & 1;
+      const int JG = T.clus0 + J8;
+      const int sj0 = JG * CL + h * CJ;
+      int fnx = 0, fny = 0, fnz = 0;
+      bool have = false, same = true;
+#pragma unroll
+      for (int b = 0; b < CJ; ++b) {
+        const float4 pj = d.pos[sj0 + b];
+        const int oj = d.orig[sj0 + b];
+#pragma unroll
+        for (int a = 0; a < CL; ++a) {
           int nx, ny, nz;
-          bool inr = list_rule(pi, pj, L, iL, c.rl2, nx, ny, nz);
-          bool valid = inr && oi >= 0 && oj >= 0 && (J8 != Il || sj > si);
-          if (valid) valid = !is_excluded(d, sys_i, oj);
-          unsigned m = __ballot_sync(0xffffffffu, valid);
-          if (m) {
-            int first = __ffs(m) - 1;
-            int fx = __shfl_sync(0xffffffffu, nx, first);
-            int fy = __shfl_sync(0xffffffffu, ny, first);
-            int fz = __shfl_sync(0xffffffffu, nz, first);
-            bool same = !valid || (nx == fx && ny == fy && nz == fz);
-            bool all_same = __all_sync(0xffffffffu, same);
-            unsigned code = (unsigned)((fx + 1) + 3 * (fy + 1) + 9 * (fz + 1));
-            unsigned w0 = (unsigned)(2 * JG + h) | (code << 26) | (all_same ? 0u : 0x80000000u);
-            if (lane == 0 && cnt < c.list_cap) seg[cnt] = make_uint2(w0, m);
-            ++cnt;
+          const float4 pi = make_float4(xi[a], yi[a], zi[a], 0.f);
+          bool v = list_rule(pi, pj, L, iL, rl2, nx, ny, nz) && oi[a] >= 0 && oj >= 0 &&
+                   (J8 != Il || sj0 + b > I * CL + a);
+          if (v) {
+            const int ne = s_nex[wib][a];
+            for (int q = 0; q < ne; ++q)
+              if (s_excl[wib][a][q] == oj) { v = false; break; }
+          }
+          if (v) {
+            if (!have) { fnx = nx; fny = ny; fnz = nz; have = true; }
+            else same = same && nx == fnx && ny == fny && nz == fnz;
+            mask |= 1u << (a * CJ + b);
           }
         }
       }
+      w0 = (unsigned)(2 * JG + h) | ((unsigned)((fnx + 1) | ((fny + 1) << 2) | ((fnz + 1) << 4)) << J_BITS) |
+           (same ? 0u : E_EXACT);
     }
+    const unsigned bal = __ballot_sync(0xffffffffu, mask != 0u);
+    const int pos = cnt + __popc(bal & ((1u << lane) - 1u));
+    if (mask != 0u && pos < c.list_cap) seg[pos] = make_uint2(w0, mask);
+    cnt += __popc(bal);
   }
   if (lane == 0) {
     d.list_n[I] = min(cnt, c.list_cap);
-    if (cnt > c.list_cap) atomicOr(d.err, ERR_LIST);
+    if (cnt > c.list_cap || overflow) atomicOr(d.err, ERR_LIST);
   }
 }
 
@@ -339,8 +406,7 @@ void launch_colsort(const Dev &d, cudaStream_t s) {
   cudaMemcpyAsync(d.type, d.type_b, n * sizeof(int32_t), cudaMemcpyDeviceToDevice, s);
 }
 void launch_list(const Dev &d, const SimConst &c, float rl2_bbox, cudaStream_t s) {
-  long long threads = (long long)d.total_clus * 32;
-  k_list<<<(unsigned)((threads + 127) / 128), 128, 0, s>>>(d, c, rl2_bbox);
+  k_list<<<(unsigned)((d.total_clus + LIST_WARPS - 1) / LIST_WARPS), LIST_WARPS * 32, 0, s>>>(d, c, rl2_bbox);
 }
 
 }  // namespace vp
