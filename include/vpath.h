@@ -181,6 +181,28 @@ int sim_kernel_times(sim_handle *h, const char **names, double *ms, int64_t *cou
  * Runs on the current device; allocates and frees its own scratch. */
 int sim_philox_normals(uint64_t seed, int64_t step, uint32_t stream, int32_t n, uint32_t *raw, double *normals);
 
+/* Reaction coordinate z and its gradient for one configuration, allocating
+ * no device memory (the paper has no counterpart: this serves callers that
+ * must not allocate -- a host program whose device memory belongs to another
+ * allocator or a fixed budget, or a latency-critical path that cannot accept
+ * the device-wide synchronisation cudaMalloc/cudaFree may cause).
+ * Same z and gradient as the batched path (SM "Collective coordinate"), with
+ * the native contact map evaluated on the fly.
+ *   d_pos [3*n_cv] FP32 and d_native [3*n_cv] FP64: DEVICE pointers, read;
+ *   box: cubic side (rounded to FP32); params: cv_r0, cv_r_switch, cv_r_cut
+ *   and cv_min_sep are read (host pointer);
+ *   d_z [1] and d_grad [3*n_cv]: DEVICE pointers, written (FP64);
+ *   cuda_stream: the stream the three launches go to (NULL: legacy stream);
+ *     the call returns after queueing them -- synchronise before reading;
+ *   errbuf/errlen: optional host buffer for a message.
+ * Scratch lives in a static device array of fixed size (112 KiB, held by every
+ * GPU that loads the library until exit): n_cv above 2048 is rejected with
+ * SIM_EINVAL.  The first call on a device looks the array up on that device
+ * (do it before any stream capture there).  Calls share the array: calls that
+ * overlap on the GPU race.  Returns SIM_OK, SIM_EINVAL or SIM_ECUDA. */
+int cv_eval_noalloc(const float *d_pos, const double *d_native, int32_t n_cv, double box, const sim_params *params,
+                    double *d_z, double *d_grad, void *cuda_stream, char *errbuf, int32_t errlen);
+
 /* The cudaStream_t the library launches on. */
 void *sim_stream(sim_handle *h);
 

@@ -81,6 +81,8 @@ _SIGS = {
     "sim_set_timing": ([C.c_void_p, C.c_int32], C.c_int),
     "sim_kernel_times": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32], C.c_int),
     "sim_philox_normals": ([C.c_uint64, C.c_int64, C.c_uint32, C.c_int32, C.c_void_p, C.c_void_p], C.c_int),
+    "cv_eval_noalloc": ([C.c_void_p, C.c_void_p, C.c_int32, C.c_double, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                         C.c_char_p, C.c_int32], C.c_int),
     "sim_stream": ([C.c_void_p], C.c_void_p),
     "sim_destroy": ([C.c_void_p], None),
     "sim_last_error": ([C.c_void_p], C.c_char_p),
@@ -263,6 +265,19 @@ def sim_philox_normals(seed: int, step: int, stream: int, n: int):
     if rc != SIM_OK:
         raise SimError(rc, "sim_philox_normals failed")
     return raw, nor
+
+
+def cv_eval_noalloc(d_pos: int, d_native: int, n_cv: int, box: float, params, d_z: int, d_grad: int,
+                    cuda_stream: int = 0):
+    """z and grad z of one configuration without any device allocation (all
+    pointers are device addresses, e.g. ``tensor.data_ptr()``).  Returns the
+    status code and the library's message."""
+    ps = params_struct(params)
+    buf = C.create_string_buffer(256)
+    rc = load().cv_eval_noalloc(C.c_void_p(d_pos or None), C.c_void_p(d_native or None), int(n_cv), float(box),
+                                C.addressof(ps), C.c_void_p(d_z or None), C.c_void_p(d_grad or None),
+                                C.c_void_p(cuda_stream or None), buf, 256)
+    return rc, buf.value.decode()
 
 
 def sim_stream(h) -> int:

@@ -10,7 +10,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libvpath.so")
-SOURCES = ["vp_rebuild.cu", "vp_pair.cu", "vp_cv.cu", "vp_update.cu", "vp_capi.cu"]
+SOURCES = ["vp_rebuild.cu", "vp_pair.cu", "vp_cv.cu", "vp_update.cu", "vp_capi.cu", "vp_noalloc.cu"]
 HEADERS = ["vp_internal.cuh", "vp_dev.cuh", os.path.join("..", "..", "include", "vpath.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-fvisibility=hidden"]
