@@ -86,6 +86,8 @@ def lib():
             L.or_run.restype = C.c_int
             L.or_phi_frames.argtypes = [C.POINTER(OrSystem), C.POINTER(OrParams), vp, C.c_int32, vp, vp, vp]
             L.or_phi_frames.restype = C.c_double
+            L.or_phi_frames_grad.argtypes = [C.POINTER(OrSystem), C.POINTER(OrParams), vp, C.c_int32, vp]
+            L.or_phi_frames_grad.restype = C.c_double
             L.or_num_threads.restype = C.c_int32
             L.or_set_num_threads.argtypes = [C.c_int32]
             _lib = L
@@ -243,6 +245,17 @@ def phi_frames(s, p, frames):
     Phi = lib().or_phi_frames(C.byref(ss.c), C.byref(pp), Fr.ctypes.data, nf, z.ctypes.data, a.ctypes.data,
                               ph.ctypes.data)
     return Phi, z, a, ph
+
+
+def phi_frames_grad(s, p, frames):
+    """(Phi, dPhi/dframes (n_frames, n_cv, 3)) along frames (n_frames, >= n_cv, 3)."""
+    ss = _Sys(s)
+    pp = _params(p)
+    Fr = np.ascontiguousarray(np.asarray(frames, np.float64)[:, : s.n_cv, :].reshape(-1))
+    nf = int(np.asarray(frames).shape[0])
+    G = np.zeros(nf * 3 * s.n_cv)
+    Phi = lib().or_phi_frames_grad(C.byref(ss.c), C.byref(pp), Fr.ctypes.data, nf, G.ctypes.data)
+    return Phi, G.reshape(nf, s.n_cv, 3)
 
 
 def num_threads():

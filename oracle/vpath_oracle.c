@@ -642,6 +642,122 @@ double or_phi_frames(const or_system *s, const or_params *p, const double *frame
   return Phi;
 }
 
+/* ------------------------------------------------------------------------ */
+/* adjoint of the bias functional with respect to the frames                */
+/* ------------------------------------------------------------------------ */
+/* Second derivative of C~(r) = C(r) S(r) (closed forms of the rational C and
+ * the quintic switch). */
+static double contact_d2(double r, double r0, double rs, double rc) {
+  double s = (r / r0) * (r / r0);
+  double N = 1.0 + s + s * s, D = N + s * s * s + s * s * s * s;
+  double N1 = 1.0 + 2.0 * s, D1 = N1 + 3.0 * s * s + 4.0 * s * s * s;
+  double N2 = 2.0, D2 = 2.0 + 6.0 * s + 12.0 * s * s;
+  double Cs = (N1 * D - N * D1) / (D * D);
+  double Css = ((N2 * D - N * D2) * D - 2.0 * D1 * (N1 * D - N * D1)) / (D * D * D);
+  double ds = 2.0 * r / (r0 * r0);
+  double C = N / D, C1 = Cs * ds, C2 = Css * ds * ds + Cs * 2.0 / (r0 * r0);
+  if (r <= rs) return C2;
+  if (r >= rc) return 0.0;
+  double w = rc - rs, x = (r - rs) / w;
+  double S = 1.0 - x * x * x * (10.0 - 15.0 * x + 6.0 * x * x);
+  double S1 = -30.0 * x * x * (1.0 - x) * (1.0 - x) / w;
+  double S2 = (-60.0 * x + 180.0 * x * x - 120.0 * x * x * x) / (w * w);
+  return C2 * S + 2.0 * C1 * S1 + C * S2;
+}
+
+/* Hessian of z applied to w (both 3*n_cv): z = sum_p f_p(r_p) with
+ * f = (C~(r) - C~_nat)^2, so a pair adds K (w_j - w_i) to atom j and
+ * subtracts it from atom i, K v = f'' u (u.v) + (f'/r)(v - u (u.v)). */
+static void cv_hessian_vec(const double *pos, const double *native, int n_cv, double box, const or_params *p,
+                           const double *w, double *out) {
+  if (n_cv <= 0) return;
+  memset(out, 0, sizeof(double) * 3 * (size_t)n_cv);
+  for (int i = 0; i < n_cv; ++i)
+    for (int j = i + 1; j < n_cv; ++j) {
+      if (j - i <= p->cv_min_sep) continue;
+      double d[3], dn[3];
+      for (int k = 0; k < 3; ++k) {
+        d[k] = min_image(pos[3 * j + k] - pos[3 * i + k], box);
+        dn[k] = native[3 * j + k] - native[3 * i + k];
+      }
+      double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+      double rn = sqrt(dn[0] * dn[0] + dn[1] * dn[1] + dn[2] * dn[2]);
+      double c[4], cn[4];
+      or_contact(r, p->cv_r0, p->cv_r_switch, p->cv_r_cut, c);
+      or_contact(rn, p->cv_r0, p->cv_r_switch, p->cv_r_cut, cn);
+      double h = c[1] - cn[1];
+      double f1 = 2.0 * h * c[3];
+      double f2 = 2.0 * (c[3] * c[3] + h * contact_d2(r, p->cv_r0, p->cv_r_switch, p->cv_r_cut));
+      double u[3] = {d[0] / r, d[1] / r, d[2] / r};
+      double v[3] = {w[3 * j] - w[3 * i], w[3 * j + 1] - w[3 * i + 1], w[3 * j + 2] - w[3 * i + 2]};
+      double uv = u[0] * v[0] + u[1] * v[1] + u[2] * v[2];
+      for (int k = 0; k < 3; ++k) {
+        double kv = f2 * u[k] * uv + (f1 / r) * (v[k] - u[k] * uv);
+        out[3 * j + k] += kv;
+        out[3 * i + k] -= kv;
+      }
+    }
+}
+
+/* Gradient of Phi (as defined by or_phi_frames) with respect to every frame:
+ * Phi = sum_{n>=1} dt (k_R/2)^2 a_n^2 Q_n, a_n = (z_n - m_{n-1})_+,
+ * m_{n-1} = min_{k<n} z_k, Q_n = sum_i |grad_i z(X_n)|^2 / (gamma_i m_i).
+ *   dPhi/dX_n = dt (k_R/2)^2 [ 2 a_n Q_n g_n + a_n^2 2 H_z(X_n) w_n ]      (n >= 1)
+ *             - dt (k_R/2)^2 sum_{l : n is the first minimiser of z_0..z_{l-1}} 2 a_l Q_l g_n
+ * with g = grad z and w_i = g_i/(gamma_i m_i) (the running minimum is
+ * differentiated along its first minimiser).  Returns Phi. */
+double or_phi_frames_grad(const or_system *s, const or_params *p, const double *frames, int32_t n_frames,
+                          double *grad) {
+  int ncv = s->n_cv;
+  size_t fs = (size_t)3 * ncv;
+  double *g = (double *)malloc(sizeof(double) * fs * (size_t)(n_frames > 0 ? n_frames : 1));
+  double *z = (double *)malloc(sizeof(double) * (size_t)(n_frames > 0 ? n_frames : 1));
+  double *Q = (double *)calloc((size_t)(n_frames > 0 ? n_frames : 1), sizeof(double));
+  double *a = (double *)calloc((size_t)(n_frames > 0 ? n_frames : 1), sizeof(double));
+  double *route = (double *)calloc((size_t)(n_frames > 0 ? n_frames : 1), sizeof(double));
+  double *w = (double *)malloc(sizeof(double) * (fs > 0 ? fs : 1));
+  double *hw = (double *)malloc(sizeof(double) * (fs > 0 ? fs : 1));
+  double c = p->dt * 0.25 * p->k_ratchet * p->k_ratchet;
+  for (int f = 0; f < n_frames; ++f) {
+    z[f] = or_cv(frames + f * fs, s->native, ncv, s->box, p->cv_r0, p->cv_r_switch, p->cv_r_cut, p->cv_min_sep,
+                 g + f * fs);
+    double q = 0.0;
+    for (int i = 0; i < ncv; ++i) {
+      double gam = s->gamma ? s->gamma[i] : p->gamma;
+      double g2 = g[f * fs + 3 * i] * g[f * fs + 3 * i] + g[f * fs + 3 * i + 1] * g[f * fs + 3 * i + 1] +
+                  g[f * fs + 3 * i + 2] * g[f * fs + 3 * i + 2];
+      q += g2 / (gam * s->mass[i]);
+    }
+    Q[f] = q;
+  }
+  double Phi = 0.0;
+  double m = 0.0;
+  int arg = 0;
+  for (int f = 0; f < n_frames; ++f) {
+    if (f == 0) { m = z[0]; arg = 0; continue; }
+    a[f] = z[f] > m ? z[f] - m : 0.0;
+    Phi += c * a[f] * a[f] * Q[f];
+    if (a[f] > 0.0) route[arg] += 2.0 * a[f] * Q[f];
+    if (z[f] < m) { m = z[f]; arg = f; }
+  }
+  for (int f = 0; f < n_frames; ++f) {
+    const double *X = frames + f * fs;
+    double *G = grad + f * fs;
+    double cg = c * ((f > 0 ? 2.0 * a[f] * Q[f] : 0.0) - route[f]);
+    for (size_t k = 0; k < fs; ++k) G[k] = cg * g[f * fs + k];
+    if (f > 0 && a[f] > 0.0) {
+      for (int i = 0; i < ncv; ++i) {
+        double gam = s->gamma ? s->gamma[i] : p->gamma;
+        for (int k = 0; k < 3; ++k) w[3 * i + k] = g[f * fs + 3 * i + k] / (gam * s->mass[i]);
+      }
+      cv_hessian_vec(X, s->native, ncv, s->box, p, w, hw);
+      for (size_t k = 0; k < fs; ++k) G[k] += c * a[f] * a[f] * 2.0 * hw[k];
+    }
+  }
+  free(g); free(z); free(Q); free(a); free(route); free(w); free(hw);
+  return Phi;
+}
+
 int32_t or_num_threads(void) {
 #ifdef _OPENMP
   return (int32_t)omp_get_max_threads();

@@ -393,3 +393,57 @@ def test_full_tiny_run_is_finite():
     r = O.run(s, p, 0, 2000)
     assert r["status"] == 0 and np.isfinite(r["Phi"]) and r["Phi"] > 0
     assert r["zm"][-1] <= r["z"][0]
+
+
+# ---------------------------------------------------------------------------
+# adjoint of the functional with respect to the frames
+# ---------------------------------------------------------------------------
+
+def _biased_path(s, p, n=24):
+    """A path along which z rises (every step biased) with a dip in the
+    middle, so that the running minimum changes and routes gradient back."""
+    nat, X0 = s.native_pos, s.pos[: s.n_cv]
+    ts = np.concatenate([np.linspace(0.1, 0.6, n // 2), np.linspace(0.55, 1.0, n - n // 2)])
+    rng = np.random.default_rng(3)
+    return np.stack([nat + t * (X0 - nat) + 0.01 * rng.normal(size=nat.shape) for t in ts])
+
+
+def test_functional_adjoint_matches_finite_differences():
+    s, p = S.tiny_chain(0)
+    fr = _biased_path(s, p)
+    Phi, G = O.phi_frames_grad(s, p, fr)
+    assert Phi == pytest.approx(O.phi_frames(s, p, fr)[0], rel=1e-14)
+    _, z, a, _ = O.phi_frames(s, p, fr)
+    assert (a[1:] > 0).sum() >= len(a) // 2
+    h = 1e-6
+    rng = np.random.default_rng(4)
+    checked = 0
+    for _ in range(120):
+        f, i, k = rng.integers(len(fr)), rng.integers(s.n_cv), rng.integers(3)
+        A, Bm = fr.copy(), fr.copy()
+        A[f, i, k] += h
+        Bm[f, i, k] -= h
+        (PA, zA, aA, _), (PB, zB, aB, _) = O.phi_frames(s, p, A), O.phi_frames(s, p, Bm)
+        # skip coordinates where +-h flips a ratchet branch or the running minimum
+        if not (np.array_equal(aA > 0, a > 0) and np.array_equal(aB > 0, a > 0)):
+            continue
+        if not (np.array_equal(np.minimum.accumulate(zA) == zA, np.minimum.accumulate(z) == z)):
+            continue
+        fd = (PA - PB) / (2 * h)
+        assert G[f, i, k] == pytest.approx(fd, rel=1e-5, abs=1e-7 * max(1.0, np.abs(G).max()))
+        checked += 1
+    assert checked > 80
+    # the first frame only enters through the running minimum
+    assert np.abs(G[0]).max() > 0
+
+
+def test_functional_adjoint_zero_cases():
+    s, p = S.tiny_chain(0)
+    nat, X0 = s.native_pos, s.pos[: s.n_cv]
+    fr = np.stack([nat + t * (X0 - nat) for t in np.linspace(1.0, 0.1, 20)])  # toward the target
+    assert np.all(np.diff(O.phi_frames(s, p, fr)[1]) < 0)
+    Phi, G = O.phi_frames_grad(s, p, fr)
+    assert Phi == 0.0 and np.all(G == 0.0)
+    p0 = S.Params(**{**p.__dict__, "k_ratchet": 0.0})
+    Phi, G = O.phi_frames_grad(s, p0, _biased_path(s, p))
+    assert Phi == 0.0 and np.all(G == 0.0)
