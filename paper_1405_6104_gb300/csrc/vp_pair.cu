@@ -77,6 +77,50 @@ __device__ float3 bonded_force(const Dev &d, const TrialInfo &T, int o, float4 s
   return F;
 }
 
+// the 8 pairs of one lane: j-atom (xj, yj, zj, qj, type row tj) against the
+// warp's 8 i-atoms.  Explicit round-to-nearest intrinsics pin the operation
+// count (3 FADD, 6 FMUL, 12 FFMA, 1 RSQ, 1 LDS, 1 FSEL per pair).
+template <bool EXACT, bool ENERGY>
+__device__ __forceinline__ void pair_block(const float (&xi)[CL], const float (&yi)[CL], const float (&zi)[CL],
+                                           const float (&qi)[CL], const int (&tio)[CL], float xj, float yj,
+                                           float zj, float qj, int tj, unsigned mb, float L, float iL,
+                                           const SimConst &c, const float2 *tab, const float *tshift,
+                                           float (&fi)[CL][3], float &fjx, float &fjy, float &fjz, float &elj,
+                                           float &erf) {
+#pragma unroll
+  for (int a = 0; a < CL; ++a) {
+    float dx = __fsub_rn(xj, xi[a]), dy = __fsub_rn(yj, yi[a]), dz = __fsub_rn(zj, zi[a]);
+    if (EXACT) {
+      dx = __fmaf_rn(-L, rintf(__fmul_rn(dx, iL)), dx);
+      dy = __fmaf_rn(-L, rintf(__fmul_rn(dy, iL)), dy);
+      dz = __fmaf_rn(-L, rintf(__fmul_rn(dz, iL)), dz);
+    }
+    const float r2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
+    const bool in = ((mb >> (4 * a)) & 1u) && (r2 < c.rc2);
+    const float rinv = rsqrtf(r2);
+    const float rinv2 = __fmul_rn(rinv, rinv);
+    const float rinv6 = __fmul_rn(__fmul_rn(rinv2, rinv2), rinv2);
+    const float2 cc = tab[tio[a] + tj];
+    const float qq = __fmul_rn(qi[a], qj);
+    float t = __fmaf_rn(cc.y, rinv6, -cc.x);
+    t = __fmul_rn(t, rinv6);
+    t = __fmaf_rn(qq, rinv, t);
+    t = __fmul_rn(t, rinv2);
+    float f = __fmaf_rn(-qq, c.two_krf, t);
+    f = in ? f : 0.0f;
+    fi[a][0] = __fmaf_rn(-f, dx, fi[a][0]);
+    fi[a][1] = __fmaf_rn(-f, dy, fi[a][1]);
+    fi[a][2] = __fmaf_rn(-f, dz, fi[a][2]);
+    fjx = __fmaf_rn(f, dx, fjx);
+    fjy = __fmaf_rn(f, dy, fjy);
+    fjz = __fmaf_rn(f, dz, fjz);
+    if (ENERGY && in) {
+      elj += rinv6 * (cc.y * (1.0f / 12.0f) * rinv6 - cc.x * (1.0f / 6.0f)) - tshift[tio[a] + tj];
+      erf += qq * (rinv + c.krf * r2 - c.crf);
+    }
+  }
+}
+
 template <bool ENERGY>
 __global__ void __launch_bounds__(128) k_pair(Dev d, SimConst c, int only_trial) {
   extern __shared__ float2 smem_tab[];
@@ -134,52 +178,15 @@ __global__ void __launch_bounds__(128) k_pair(Dev d, SimConst c, int only_trial)
     const unsigned mb = ent.y >> b;
     const bool exact = (ent.x & E_EXACT) != 0u;
     float fjx = 0.f, fjy = 0.f, fjz = 0.f;
-    if (!__any_sync(0xffffffffu, exact)) {
-#pragma unroll
-      for (int a = 0; a < CL; ++a) {
-        const float dx = xj - xi[a], dy = yj - yi[a], dz = zj - zi[a];
-        const float r2 = dx * dx + dy * dy + dz * dz;
-        const bool in = ((mb >> (4 * a)) & 1u) && (r2 < c.rc2);
-        const float rinv = rsqrtf(r2);
-        const float rinv2 = rinv * rinv;
-        const float rinv6 = rinv2 * rinv2 * rinv2;
-        const float2 cc = tab[tio[a] + tj];
-        const float qq = qi[a] * pj.w;
-        float f = rinv2 * (rinv6 * fmaf(cc.y, rinv6, -cc.x) + qq * rinv) - qq * c.two_krf;
-        f = in ? f : 0.0f;
-        fi[a][0] -= f * dx; fi[a][1] -= f * dy; fi[a][2] -= f * dz;
-        fjx += f * dx; fjy += f * dy; fjz += f * dz;
-        if (ENERGY && in) {
-          elj += rinv6 * (cc.y * (1.0f / 12.0f) * rinv6 - cc.x * (1.0f / 6.0f)) - tshift[tio[a] + tj];
-          erf += qq * (rinv + c.krf * r2 - c.crf);
-        }
-      }
-    } else {
-#pragma unroll
-      for (int a = 0; a < CL; ++a) {
-        float dx = xj - xi[a], dy = yj - yi[a], dz = zj - zi[a];
-        if (exact) {
-          dx -= L * rintf(dx * iL);
-          dy -= L * rintf(dy * iL);
-          dz -= L * rintf(dz * iL);
-        }
-        const float r2 = dx * dx + dy * dy + dz * dz;
-        const bool in = ((mb >> (4 * a)) & 1u) && (r2 < c.rc2);
-        const float rinv = rsqrtf(r2);
-        const float rinv2 = rinv * rinv;
-        const float rinv6 = rinv2 * rinv2 * rinv2;
-        const float2 cc = tab[tio[a] + tj];
-        const float qq = qi[a] * pj.w;
-        float f = rinv2 * (rinv6 * fmaf(cc.y, rinv6, -cc.x) + qq * rinv) - qq * c.two_krf;
-        f = in ? f : 0.0f;
-        fi[a][0] -= f * dx; fi[a][1] -= f * dy; fi[a][2] -= f * dz;
-        fjx += f * dx; fjy += f * dy; fjz += f * dz;
-        if (ENERGY && in) {
-          elj += rinv6 * (cc.y * (1.0f / 12.0f) * rinv6 - cc.x * (1.0f / 6.0f)) - tshift[tio[a] + tj];
-          erf += qq * (rinv + c.krf * r2 - c.crf);
-        }
-      }
-    }
+    if (!__any_sync(0xffffffffu, exact))
+      pair_block<false, ENERGY>(xi, yi, zi, qi, tio, xj, yj, zj, pj.w, tj, mb, L, iL, c, tab, tshift, fi, fjx, fjy,
+                                fjz, elj, erf);
+    else if (exact)
+      pair_block<true, ENERGY>(xi, yi, zi, qi, tio, xj, yj, zj, pj.w, tj, mb, L, iL, c, tab, tshift, fi, fjx, fjy,
+                               fjz, elj, erf);
+    else
+      pair_block<false, ENERGY>(xi, yi, zi, qi, tio, xj, yj, zj, pj.w, tj, mb, L, iL, c, tab, tshift, fi, fjx, fjy,
+                                fjz, elj, erf);
     if (!ENERGY && (fjx != 0.f || fjy != 0.f || fjz != 0.f)) {
       red_add(d.fx + sj, fx_from(fjx));
       red_add(d.fy + sj, fx_from(fjy));

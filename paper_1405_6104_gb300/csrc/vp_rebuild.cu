@@ -214,17 +214,16 @@ __device__ __forceinline__ float periodic_gap(float a0, float a1, float b0, floa
 }
 
 // the FP32 list rule (no contraction): d = xj - xi; d -= L*rint(d*invL);
-// r2 = (dx*dx + dy*dy) + dz*dz; member iff r2 < rl2.  Also returns the
-// image counts n (x_j image = x_j - L n).
-__device__ __forceinline__ bool list_rule(float4 pi, float4 pj, float L, float iL, float rl2, int &nx, int &ny,
-                                          int &nz) {
+// r2 = (dx*dx + dy*dy) + dz*dz; member iff r2 < rl2.  Also returns the image
+// key 9 nx + 3 ny + nz of the counts n (x_j image = x_j - L n).
+__device__ __forceinline__ bool list_rule(float4 pi, float4 pj, float L, float iL, float rl2, float &key) {
   float dx = __fsub_rn(pj.x, pi.x), dy = __fsub_rn(pj.y, pi.y), dz = __fsub_rn(pj.z, pi.z);
-  float qx = rintf(__fmul_rn(dx, iL)), qy = rintf(__fmul_rn(dy, iL)), qz = rintf(__fmul_rn(dz, iL));
+  const float qx = rintf(__fmul_rn(dx, iL)), qy = rintf(__fmul_rn(dy, iL)), qz = rintf(__fmul_rn(dz, iL));
   dx = __fsub_rn(dx, __fmul_rn(L, qx));
   dy = __fsub_rn(dy, __fmul_rn(L, qy));
   dz = __fsub_rn(dz, __fmul_rn(L, qz));
-  float r2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
-  nx = (int)qx; ny = (int)qy; nz = (int)qz;
+  const float r2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+  key = __fmaf_rn(9.0f, qx, __fmaf_rn(3.0f, qy, qz));
   return r2 < rl2;
 }
 
@@ -241,6 +240,7 @@ __global__ void __launch_bounds__(LIST_WARPS * 32) k_list(Dev d, SimConst c, flo
   __shared__ int s_cand[LIST_WARPS][CAND_MAX];
   __shared__ int s_excl[LIST_WARPS][CL][MAX_EXCL];
   __shared__ int s_nex[LIST_WARPS][CL];
+  __shared__ int s_exlo[LIST_WARPS][CL], s_exhi[LIST_WARPS][CL];
   const int wib = threadIdx.x >> 5;
   const int I = blockIdx.x * LIST_WARPS + wib;
   const int lane = threadIdx.x & 31;
@@ -332,8 +332,16 @@ __global__ void __launch_bounds__(LIST_WARPS * 32) k_list(Dev d, SimConst c, flo
     const int o = d.orig[I * CL + lane];
     const int sa = T.sysatom0 + (o < 0 ? 0 : o);
     const int n = o < 0 ? 0 : d.excl_n[sa];
+    int lo_e = 0x7fffffff, hi_e = -1;
+    for (int k = 0; k < n; ++k) {
+      const int e = d.excl[(size_t)sa * MAX_EXCL + k];
+      s_excl[wib][lane][k] = e;
+      lo_e = min(lo_e, e);
+      hi_e = max(hi_e, e);
+    }
     s_nex[wib][lane] = n;
-    for (int k = 0; k < n; ++k) s_excl[wib][lane][k] = d.excl[(size_t)sa * MAX_EXCL + k];
+    s_exlo[wib][lane] = lo_e;
+    s_exhi[wib][lane] = hi_e;
   }
   __syncwarp();
   // ---- phase 2: one candidate 4-atom j-cluster per lane ----
@@ -347,32 +355,37 @@ __global__ void __launch_bounds__(LIST_WARPS * 32) k_list(Dev d, SimConst c, flo
       const int J8 = cand[k >> 1], h = k & 1;
       const int JG = T.clus0 + J8;
       const int sj0 = JG * CL + h * CJ;
-      int fnx = 0, fny = 0, fnz = 0;
-      bool have = false, same = true;
+      float kmin = 3e38f, kmax = -3e38f;
 #pragma unroll
       for (int b = 0; b < CJ; ++b) {
         const float4 pj = d.pos[sj0 + b];
         const int oj = d.orig[sj0 + b];
 #pragma unroll
         for (int a = 0; a < CL; ++a) {
-          int nx, ny, nz;
+          float key;
           const float4 pi = make_float4(xi[a], yi[a], zi[a], 0.f);
-          bool v = list_rule(pi, pj, L, iL, rl2, nx, ny, nz) && oi[a] >= 0 && oj >= 0 &&
+          bool v = list_rule(pi, pj, L, iL, rl2, key) && oi[a] >= 0 && oj >= 0 &&
                    (J8 != Il || sj0 + b > I * CL + a);
-          if (v) {
+          if (v && oj >= s_exlo[wib][a] && oj <= s_exhi[wib][a]) {
             const int ne = s_nex[wib][a];
             for (int q = 0; q < ne; ++q)
               if (s_excl[wib][a][q] == oj) { v = false; break; }
           }
           if (v) {
-            if (!have) { fnx = nx; fny = ny; fnz = nz; have = true; }
-            else same = same && nx == fnx && ny == fny && nz == fnz;
+            kmin = fminf(kmin, key);
+            kmax = fmaxf(kmax, key);
             mask |= 1u << (a * CJ + b);
           }
         }
       }
-      w0 = (unsigned)(2 * JG + h) | ((unsigned)((fnx + 1) | ((fny + 1) << 2) | ((fnz + 1) << 4)) << J_BITS) |
-           (same ? 0u : E_EXACT);
+      // image counts of the entry from the key 9 nx + 3 ny + nz (each in -1..1)
+      const int key = mask ? (int)kmin : 0;
+      const int kz = ((key % 3) + 4) % 3 - 1;
+      const int ky = (((key - kz) / 3) % 3 + 4) % 3 - 1;
+      const int kx = (key - kz - 3 * ky) / 9;
+      const bool same = kmin == kmax;
+      w0 = (unsigned)(2 * JG + h) | ((unsigned)((kx + 1) | ((ky + 1) << 2) | ((kz + 1) << 4)) << J_BITS) |
+           (same || !mask ? 0u : E_EXACT);
     }
     const unsigned bal = __ballot_sync(0xffffffffu, mask != 0u);
     const int pos = cnt + __popc(bal & ((1u << lane) - 1u));

@@ -230,3 +230,29 @@ def test_full_size_batch_sampled():
         gpu = {tuple(x) for x in B.sim_pairlist(b.h, 63).tolist()}
         ref = {tuple(x) for x in O.pairlist(s, pos.astype(np.float32), p.r_cut + p.skin).tolist()}
         assert gpu == ref
+
+
+def test_potential_autograd_backward_is_minus_force():
+    """U(X, Y) as a torch.autograd.Function: forward = FP64 energy total of the
+    kernels, backward = -F; checked against the FP64 oracle's -grad U."""
+    import torch
+    from paper_1405_6104_gb300.autograd import Evaluator, potential_energy
+    s, p = S.small_solvated()
+    ev = Evaluator(s, p)
+    try:
+        x = torch.tensor(s.pos, dtype=torch.float64, requires_grad=True)
+        U = potential_energy(x, ev)
+        L = 3.0 * U + 0.5 * (x ** 2).sum()
+        L.backward()
+        Fr, er = O.forces(s, p, s.pos)
+        assert float(U) == pytest.approx(er.sum(), rel=1e-5, abs=1e-5 * np.abs(er).sum())
+        g = x.grad.numpy()
+        assert rel_rms(g, -3.0 * Fr + s.pos) < 1e-5
+        assert rel_rms((g - s.pos) / 3.0, -Fr) < 1e-5
+        # a second evaluation at displaced positions reuses the handle
+        y = torch.tensor(s.pos + 0.001, dtype=torch.float64, requires_grad=True)
+        potential_energy(y, ev).backward()
+        Fr2, _ = O.forces(s, p, (s.pos + 0.001).astype(np.float32).astype(np.float64))
+        assert rel_rms(y.grad.numpy(), -Fr2) < 1e-5
+    finally:
+        ev.close()
