@@ -150,11 +150,38 @@ int sim_set_step_count(sim_handle *h, int64_t step);
 int32_t sim_num_trials(const sim_handle *h);
 int32_t sim_num_atoms(const sim_handle *h, int32_t trial);
 
-/* Per-step record of {z, z_m, a, phi} for every trial: capacity entries per
- * trial (0 disables); entry of step n at index n % capacity.  Enabling
- * clears the record. */
+/* Per-step record of {z, z_m, a, phi, Q} for every trial, where
+ * phi = (k_R/2)^2 a^2 Q and Q = sum_i |grad_i z|^2/(gamma_i m_i): capacity
+ * entries per trial (0 disables); entry of step n at index n % capacity.
+ * Enabling clears the record. */
 int sim_record(sim_handle *h, int32_t capacity);
-int sim_get_record(sim_handle *h, int32_t trial, double *out /* [4*capacity] */);
+int sim_get_record(sim_handle *h, int32_t trial, double *out /* [5*capacity] */);
+
+/* Per-step record of the reaction-coordinate atom positions of one trial
+ * (the frames X_n of the path): capacity frames, the frame of step n at index
+ * n % capacity, written after every force evaluation (also at sim_set_state).
+ * sim_get_frames copies [capacity][n_cv][3] (nm) to out. */
+int sim_record_frames(sim_handle *h, int32_t trial, int32_t capacity);
+int sim_get_frames(sim_handle *h, double *out);
+
+/* Gradient of the bias functional (Eq. VMDcondition, discretised as in
+ * bias_functional) with respect to the reaction-coordinate atoms of every
+ * frame of a path X_0 .. X_{n_frames-1} of one trial's system, dt apart:
+ *   dPhi/dX_n = A_n grad z(X_n) + B_n H_z(X_n) w_n,  w_i = grad_i z/(gamma_i m_i),
+ *   A_n = dt (k_R/2)^2 (2 a_n Q_n - R_n), B_n = 2 dt (k_R/2)^2 a_n^2,
+ * a_n = (z_n - min_{k<n} z_k)_+ (Eq. VR), R_n = sum of 2 a_l Q_l over the later
+ * frames l whose running minimum sits at frame n (its first minimiser).
+ *   frames [n_frames][n_cv][3] host; coef [2*n_frames] host (A_n, B_n) or NULL
+ *   to derive them from these frames with z_m starting at frame 0 (then *phi,
+ *   if not NULL, receives Phi along them); z [n_frames] (may be NULL) receives
+ *   z(X_n); grad [n_frames][n_cv][3] host output. */
+int phi_frames_adjoint(sim_handle *h, int32_t trial, const double *frames, int32_t n_frames, const double *coef,
+                       double *phi, double *z, double *grad);
+
+/* The coefficients (A_n, B_n) above and Phi from z_n and Q_n along a path of
+ * n frames (z_m starts at z_0; Q_0 is not used), e.g. from sim_record, so that
+ * phi_frames_adjoint can process a long path segment by segment. */
+int phi_adjoint_coefficients(sim_handle *h, const double *z, const double *Q, int32_t n, double *coef, double *phi);
 
 /* Test and diagnostics hooks.
  * sim_pairlist: the atom pairs (i < j, caller's indices) that the current

@@ -76,6 +76,11 @@ _SIGS = {
     "sim_num_atoms": ([C.c_void_p, C.c_int32], C.c_int32),
     "sim_record": ([C.c_void_p, C.c_int32], C.c_int),
     "sim_get_record": ([C.c_void_p, C.c_int32, C.c_void_p], C.c_int),
+    "sim_record_frames": ([C.c_void_p, C.c_int32, C.c_int32], C.c_int),
+    "sim_get_frames": ([C.c_void_p, C.c_void_p], C.c_int),
+    "phi_frames_adjoint": ([C.c_void_p, C.c_int32, C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p,
+                            C.c_void_p], C.c_int),
+    "phi_adjoint_coefficients": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p], C.c_int),
     "sim_pairlist": ([C.c_void_p, C.c_int32, C.c_void_p, C.c_int64, C.c_void_p], C.c_int),
     "sim_diagnostics": ([C.c_void_p, C.c_void_p], C.c_int),
     "sim_set_timing": ([C.c_void_p, C.c_int32], C.c_int),
@@ -222,9 +227,43 @@ def sim_record(h, capacity: int):
 
 
 def sim_get_record(h, trial: int, capacity: int):
-    out = np.zeros((capacity, 4))
+    """[capacity, 5]: z, z_m, a, phi, Q per step (index = step % capacity)."""
+    out = np.zeros((capacity, 5))
     _check(h, load().sim_get_record(h, int(trial), out.ctypes.data))
     return out
+
+
+def sim_record_frames(h, trial: int, capacity: int):
+    _check(h, load().sim_record_frames(h, int(trial), int(capacity)))
+
+
+def sim_get_frames(h, capacity: int, n_cv: int):
+    out = np.zeros((capacity, n_cv, 3))
+    _check(h, load().sim_get_frames(h, out.ctypes.data))
+    return out
+
+
+def phi_frames_adjoint(h, trial: int, frames, coef=None):
+    """(Phi or None, z per frame, dPhi/dframes) for frames (n_frames, n_cv, 3)."""
+    F = np.ascontiguousarray(np.asarray(frames, np.float64))
+    nf, ncv = F.shape[0], F.shape[1]
+    Cf = None if coef is None else np.ascontiguousarray(np.asarray(coef, np.float64).reshape(-1))
+    phi = np.zeros(1)
+    z = np.zeros(nf)
+    G = np.zeros((nf, ncv, 3))
+    _check(h, load().phi_frames_adjoint(h, int(trial), F.ctypes.data, nf, _ptr(Cf), phi.ctypes.data, z.ctypes.data,
+                                        G.ctypes.data))
+    return (None if coef is not None else float(phi[0])), z, G
+
+
+def phi_adjoint_coefficients(h, z, Q):
+    zz = np.ascontiguousarray(np.asarray(z, np.float64))
+    qq = np.ascontiguousarray(np.asarray(Q, np.float64))
+    coef = np.zeros((len(zz), 2))
+    phi = np.zeros(1)
+    _check(h, load().phi_adjoint_coefficients(h, zz.ctypes.data, qq.ctypes.data, len(zz), coef.ctypes.data,
+                                              phi.ctypes.data))
+    return coef, float(phi[0])
 
 
 def sim_pairlist(h, trial: int, cap: int = 0):

@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "../../include/vpath.h"
+#include "vp_adjoint.cuh"
 #include "vp_dev.cuh"
 
 #define VP_API extern "C" __attribute__((visibility("default")))
@@ -48,6 +49,9 @@ struct sim_handle {
   std::vector<void *> allocs;
   std::string err;
   int rec_cap = 0;
+  // CV-frame recorder (one trial)
+  int frame_trial = -1, frame_cap = 0;
+  float *frames = nullptr;
   // staging
   double *dbuf = nullptr;
   size_t dbuf_n = 0;
@@ -150,6 +154,8 @@ void forces(sim_handle *h, FinMode mode) {
   timed(h, "pair", [&] { launch_pair(h->d, h->c, false, -1, s); });
   timed(h, "cv", [&] { launch_cv(h->d, h->c, s); });
   timed(h, "cvfin", [&] { launch_cvfin(h->d, h->c, mode, s); });
+  if (h->frames)
+    launch_rec_frames(h->d, h->frame_trial, h->tinfo[h->frame_trial].n_cv, h->frame_cap, h->frames, s);
 }
 
 void one_step(sim_handle *h, bool with_rebuild) {
@@ -306,6 +312,18 @@ VP_API int sim_create(const sim_system *systems, int32_t n_systems, const int32_
   c.cv_rc_d = p.cv_r_cut;
   c.cv_min_sep = p.cv_min_sep;
   c.rec_cap = 0;
+  // one friction for every atom: the Langevin coefficients need no per-atom table
+  {
+    bool uni = true;
+    for (int s = 0; s < n_systems && uni; ++s)
+      if (systems[s].gamma)
+        for (int i = 0; i < systems[s].n_atoms; ++i)
+          if (systems[s].gamma[i] != p.gamma) { uni = false; break; }
+    const double c1u = std::exp(-p.gamma * p.dt);
+    c.uniform_gamma = uni ? 1 : 0;
+    c.c1_u = (float)c1u;
+    c.c2sqkT_u = (float)std::sqrt((1.0 - c1u * c1u) * kT);
+  }
   h->rl2_bbox = (float)((rl + 1e-3) * (rl + 1e-3));
   h->half_skin2 = (float)(0.25 * p.skin * p.skin);
 
@@ -780,7 +798,7 @@ VP_API int sim_record(sim_handle *h, int32_t capacity) {
     h->chunk = nullptr;
   }
   if (capacity > 0) {
-    size_t n = (size_t)h->n_trials * capacity * 4;
+    size_t n = (size_t)h->n_trials * capacity * 5;
     CK(cudaMalloc(&h->d.rec, n * sizeof(double)));
     CK(cudaMemset(h->d.rec, 0, n * sizeof(double)));
   }
@@ -791,9 +809,97 @@ VP_API int sim_get_record(sim_handle *h, int32_t trial, double *out) {
   int r = enter(h);
   if (r) return r;
   if (trial < 0 || trial >= h->n_trials || !out || h->rec_cap <= 0) return fail(h, SIM_EINVAL, "no record");
-  size_t n = (size_t)h->rec_cap * 4;
+  size_t n = (size_t)h->rec_cap * 5;
   CK(cudaMemcpyAsync(out, h->d.rec + (size_t)trial * n, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
+  return SIM_OK;
+}
+
+VP_API int sim_record_frames(sim_handle *h, int32_t trial, int32_t capacity) {
+  int r = enter(h);
+  if (r) return r;
+  if (capacity < 0 || (capacity > 0 && (trial < 0 || trial >= h->n_trials)))
+    return fail(h, SIM_EINVAL, "bad frame-record arguments");
+  if (h->frames) {
+    cudaFree(h->frames);
+    h->frames = nullptr;
+  }
+  if (h->chunk) {
+    cudaGraphExecDestroy(h->chunk);
+    h->chunk = nullptr;
+  }
+  h->frame_cap = capacity;
+  h->frame_trial = capacity > 0 ? trial : -1;
+  if (capacity > 0) {
+    size_t n = (size_t)capacity * 3 * (size_t)std::max(1, h->tinfo[trial].n_cv);
+    CK(cudaMalloc(&h->frames, n * sizeof(float)));
+    CK(cudaMemset(h->frames, 0, n * sizeof(float)));
+  }
+  return SIM_OK;
+}
+
+VP_API int sim_get_frames(sim_handle *h, double *out) {
+  int r = enter(h);
+  if (r) return r;
+  if (!h->frames || !out) return fail(h, SIM_EINVAL, "no frame record");
+  size_t n = (size_t)h->frame_cap * 3 * (size_t)h->tinfo[h->frame_trial].n_cv;
+  std::vector<float> tmp(n);
+  CK(cudaMemcpyAsync(tmp.data(), h->frames, n * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  for (size_t k = 0; k < n; ++k) out[k] = tmp[k];
+  return SIM_OK;
+}
+
+namespace {
+AdjInput adj_input(sim_handle *h, int trial) {
+  const TrialInfo &T = h->tinfo[trial];
+  AdjInput in{};
+  in.n_cv = T.n_cv;
+  in.min_sep = h->c.cv_min_sep;
+  in.n_tiles = T.n_work;
+  in.tiles = h->d.tiles + T.systile0;
+  in.cnat = h->d.cnat + (size_t)T.systile0 * CV_T * CV_T;
+  in.gm = h->d.gm + T.sysatom0;
+  in.L = T.box;
+  in.iL = T.inv_box;
+  const SimConst &c = h->c;
+  in.k = CvConst{ff{c.cv_inv_r0sq_hi, c.cv_inv_r0sq_lo}, ff{c.cv_rs_hi, c.cv_rs_lo}, ff{c.cv_inv_w_hi, c.cv_inv_w_lo},
+                 c.cv_rs2, c.cv_rc2_far};
+  in.c = h->c.dt_d * h->c.kR_half_d * h->c.kR_half_d;
+  return in;
+}
+}  // namespace
+
+VP_API int phi_frames_adjoint(sim_handle *h, int32_t trial, const double *frames, int32_t n_frames, const double *coef,
+                              double *phi, double *z, double *grad) {
+  int r = enter(h);
+  if (r) return r;
+  if (trial < 0 || trial >= h->n_trials || n_frames < 1 || !frames) return fail(h, SIM_EINVAL, "bad arguments");
+  TrialState S;
+  CK(cudaMemcpyAsync(&S, h->d.tstate + trial, sizeof(S), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  AdjInput in = adj_input(h, trial);
+  in.frames = frames;
+  in.n_frames = n_frames;
+  in.zconst = S.zconst;
+  in.coef = coef;
+  in.phi = phi;
+  in.z_out = z;
+  in.grad = grad;
+  std::string err;
+  r = adjoint_frames(in, h->stream, err);
+  if (r) return fail(h, r, "phi_frames_adjoint: " + err);
+  return SIM_OK;
+}
+
+VP_API int phi_adjoint_coefficients(sim_handle *h, const double *z, const double *Q, int32_t n, double *coef,
+                                    double *phi) {
+  int r = enter(h);
+  if (r) return r;
+  if (n < 1 || !z || !Q || !coef) return fail(h, SIM_EINVAL, "bad arguments");
+  std::string err;
+  r = adjoint_coefficients(z, Q, n, h->c.dt_d * h->c.kR_half_d * h->c.kR_half_d, coef, phi, h->stream, err);
+  if (r) return fail(h, r, "phi_adjoint_coefficients: " + err);
   return SIM_OK;
 }
 
@@ -891,6 +997,7 @@ VP_API void sim_destroy(sim_handle *h) {
   if (h->chunk) cudaGraphExecDestroy(h->chunk);
   for (void *p : h->allocs) cudaFree(p);
   if (h->d.rec) cudaFree(h->d.rec);
+  if (h->frames) cudaFree(h->frames);
   if (h->dbuf) cudaFree(h->dbuf);
   for (auto &t : h->timers)
     for (auto &pr : t.ev) { cudaEventDestroy(pr.first); cudaEventDestroy(pr.second); }

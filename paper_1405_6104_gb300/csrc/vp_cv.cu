@@ -14,28 +14,10 @@
 // Lane l owns i = bi*32 + l; at step k it takes column (l + k) mod 32, and the
 // column accumulators travel one lane per step around the warp so that every
 // column sum is built in a fixed order without atomics inside the tile.
+#include "vp_cvpair.cuh"
 #include "vp_dev.cuh"
 
 namespace vp {
-
-// C(s) with s = (r/r0)^2: (1 + s + s^2) / (1 + s + s^2 + s^3 + s^4), the printed
-// (1 - rho^6)/(1 - rho^10) with the common factor (1 - s) cancelled
-__device__ __forceinline__ ff contact_ff(ff s) {
-  ff s2 = ff_sqr(s);
-  ff s3 = ff_mul(s2, s);
-  ff s4 = ff_sqr(s2);
-  ff N = ff_add(ff_add_f(s, 1.0f), s2);
-  ff D = ff_add(ff_add(N, s3), s4);
-  return ff_div(N, D);
-}
-
-__device__ __forceinline__ float dcontact_ds(float s) {
-  float N = 1.0f + s + s * s;
-  float D = N + s * s * s + s * s * s * s;
-  float dN = 1.0f + 2.0f * s;
-  float dD = dN + 3.0f * s * s + 4.0f * s * s * s;
-  return (dN * D - N * dD) / (D * D);
-}
 
 // one warp per (system tile); C~ of the native structure in FP64
 __global__ void k_cnat(Dev d, SimConst c, const double *native, const int32_t *sys_nat0, const int32_t *tile_sys,
@@ -89,8 +71,20 @@ __global__ void k_zconst(Dev d, const int32_t *sys_tile0, const int32_t *sys_nti
   if (threadIdx.x == 0) d.tstate[t].zconst = red[0];
 }
 
-__global__ void __launch_bounds__(128) k_cv(Dev d, SimConst c) {
-  const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+// Two phases per (trial, tile) warp: (1) a cheap FP32 distance test of the
+// 1024 pairs of the tile lists the pairs closer than the contact cut-off in
+// shared memory; (2) the warp evaluates only those, 32 at a time, in
+// float-float, accumulating the gradient of the tile's 64 atoms with int64
+// shared-memory atomics (order-independent, so deterministic) and flushing it
+// once per tile.  Far pairs (C~ = 0) contribute only to the constant Z0.
+constexpr int CV_WARPS = 4;
+
+__global__ void __launch_bounds__(CV_WARPS * 32) k_cv(Dev d, SimConst c) {
+  __shared__ unsigned short s_near[CV_WARPS][CV_T * CV_T];
+  __shared__ float s_x[CV_WARPS][2 * CV_T][3];
+  __shared__ unsigned long long s_g[CV_WARPS][2 * CV_T][3];
+  const int wib = threadIdx.x >> 5;
+  const int w = blockIdx.x * CV_WARPS + wib;
   const int lane = threadIdx.x & 31;
   if (w >= d.total_work) return;
   const int2 wk = d.work[w];
@@ -101,70 +95,76 @@ __global__ void __launch_bounds__(128) k_cv(Dev d, SimConst c) {
   const int i = bij.x * CV_T + lane;
   const int jl = bij.y * CV_T + lane;
   float3 xi = make_float3(0.f, 0.f, 0.f), xj = make_float3(0.f, 0.f, 0.f);
-  if (i < ncv) { float4 p = d.pos[d.slot_of[T.atom0 + i]]; xi = make_float3(p.x, p.y, p.z); }
-  if (jl < ncv) { float4 p = d.pos[d.slot_of[T.atom0 + jl]]; xj = make_float3(p.x, p.y, p.z); }
-  const ff inv_r0sq = {c.cv_inv_r0sq_hi, c.cv_inv_r0sq_lo};
-  const double *cn = d.cnat + (size_t)wk.y * CV_T * CV_T;
-  long long gix = 0, giy = 0, giz = 0, gjx = 0, gjy = 0, gjz = 0;
-  ff zacc = {0.f, 0.f};
+  if (i < ncv) { float4 q = d.pos[d.slot_of[T.atom0 + i]]; xi = make_float3(q.x, q.y, q.z); }
+  if (jl < ncv) { float4 q = d.pos[d.slot_of[T.atom0 + jl]]; xj = make_float3(q.x, q.y, q.z); }
+  s_x[wib][lane][0] = xi.x; s_x[wib][lane][1] = xi.y; s_x[wib][lane][2] = xi.z;
+  s_x[wib][CV_T + lane][0] = xj.x; s_x[wib][CV_T + lane][1] = xj.y; s_x[wib][CV_T + lane][2] = xj.z;
+#pragma unroll
+  for (int q = 0; q < 3; ++q) { s_g[wib][lane][q] = 0ull; s_g[wib][CV_T + lane][q] = 0ull; }
+  // ---- phase 1: near pairs of the tile ----
+  int n_near = 0;
   for (int k = 0; k < CV_T; ++k) {
     const int jc = (lane + k) & (CV_T - 1);
     const int j = bij.y * CV_T + jc;
     const float xjx = __shfl_sync(0xffffffffu, xj.x, jc);
     const float xjy = __shfl_sync(0xffffffffu, xj.y, jc);
     const float xjz = __shfl_sync(0xffffffffu, xj.z, jc);
+    bool near = false;
     if (i < ncv && j < ncv && j - i > msep) {
-      ff dx = ff_diff(xjx, xi.x), dy = ff_diff(xjy, xi.y), dz = ff_diff(xjz, xi.z);
-      float nx = rintf(dx.hi * iL), ny = rintf(dy.hi * iL), nz = rintf(dz.hi * iL);
-      if (nx != 0.f) dx = ff_add_f(dx, -L * nx);
-      if (ny != 0.f) dy = ff_add_f(dy, -L * ny);
-      if (nz != 0.f) dz = ff_add_f(dz, -L * nz);
-      const float r2f = dx.hi * dx.hi + dy.hi * dy.hi + dz.hi * dz.hi;
-      if (r2f < c.cv_rc2_far) {
-        const ff cnat = ff_from_d(cn[k * CV_T + lane]);
-        const ff r2 = ff_add(ff_add(ff_sqr(dx), ff_sqr(dy)), ff_sqr(dz));
-        const ff s = ff_mul(r2, inv_r0sq);
-        ff Ct = contact_ff(s);
-        const float rf = sqrtf(r2.hi);
-        float dCt = dcontact_ds(s.hi) * 2.0f * rf * inv_r0sq.hi;  // dC/dr
-        if (r2.hi > c.cv_rs2) {
-          const ff r = ff_sqrt(r2);
-          const ff x = ff_mul(ff_add(r, ff{-c.cv_rs_hi, -c.cv_rs_lo}), ff{c.cv_inv_w_hi, c.cv_inv_w_lo});
-          if (x.hi >= 1.0f) {
-            Ct = {0.f, 0.f};
-            dCt = 0.f;
-          } else {
-            // S = 1 - x^3 (10 - 15 x + 6 x^2)
-            ff p = ff_add_f(ff_mul_f(x, 6.0f), -15.0f);
-            p = ff_add_f(ff_mul(p, x), 10.0f);
-            const ff x3 = ff_mul(ff_sqr(x), x);
-            const ff S = ff_add_f(ff_neg(ff_mul(x3, p)), 1.0f);
-            const float xf = x.hi;
-            const float dS = -30.0f * xf * xf * (1.0f - xf) * (1.0f - xf) * c.cv_inv_w_hi;
-            dCt = dCt * S.hi + Ct.hi * dS;
-            Ct = ff_mul(Ct, S);
-          }
-        }
-        const ff h = ff_add(Ct, ff_neg(cnat));
-        // z term: C~ (C~ - 2 C~_nat) = (C~ - C~_nat)^2 - C~_nat^2
-        zacc = ff_add(zacc, ff_mul(Ct, ff_add(Ct, ff_neg(ff_mul_f(cnat, 2.0f)))));
-        // dz/dx_i = -w d, dz/dx_j = +w d with d = x_j - x_i, w = 2 h C~'(r)/r
-        const float wgt = 2.0f * h.hi * dCt / rf;
+      float dx = xjx - xi.x, dy = xjy - xi.y, dz = xjz - xi.z;
+      dx -= L * rintf(dx * iL);
+      dy -= L * rintf(dy * iL);
+      dz -= L * rintf(dz * iL);
+      near = dx * dx + dy * dy + dz * dz < c.cv_rc2_far;
+    }
+    const unsigned bal = __ballot_sync(0xffffffffu, near);
+    if (near) s_near[wib][n_near + __popc(bal & ((1u << lane) - 1u))] = (unsigned short)(lane | (jc << 5));
+    n_near += __popc(bal);
+  }
+  __syncwarp();
+  // ---- phase 2: the near pairs, densely ----
+  const CvConst k = cv_const(c);
+  const double *cn = d.cnat + (size_t)wk.y * CV_T * CV_T;
+  ff zacc = {0.f, 0.f};
+  for (int base = 0; base < n_near; base += 32) {
+    const int idx = base + lane;
+    if (idx < n_near) {
+      const unsigned e = s_near[wib][idx];
+      const int il = e & 31, jc = e >> 5;
+      const float3 pi = make_float3(s_x[wib][il][0], s_x[wib][il][1], s_x[wib][il][2]);
+      ff dx, dy, dz;
+      cv_delta(pi, s_x[wib][CV_T + jc][0], s_x[wib][CV_T + jc][1], s_x[wib][CV_T + jc][2], L, iL, dx, dy, dz);
+      const ff cnat = ff_from_d(cn[((jc - il) & (CV_T - 1)) * CV_T + il]);
+      const ff r2 = ff_add(ff_add(ff_sqr(dx), ff_sqr(dy)), ff_sqr(dz));
+      const CvPair cp = cv_contact<false>(r2, k);
+      const ff h = ff_add(cp.Ct, ff_neg(cnat));
+      // z term: C~ (C~ - 2 C~_nat) = (C~ - C~_nat)^2 - C~_nat^2
+      zacc = ff_add(zacc, ff_mul(cp.Ct, ff_add(cp.Ct, ff_neg(ff_mul_f(cnat, 2.0f)))));
+      // dz/dx_i = -w d, dz/dx_j = +w d with d = x_j - x_i, w = 2 h C~'(r)/r
+      const float wgt = 2.0f * h.hi * cp.dCt / cp.r;
+      if (wgt != 0.0f) {
         const long long gx = fx_from(wgt * dx.hi), gy = fx_from(wgt * dy.hi), gz = fx_from(wgt * dz.hi);
-        gix -= gx; giy -= gy; giz -= gz;
-        gjx += gx; gjy += gy; gjz += gz;
+        atomicAdd(&s_g[wib][il][0], (unsigned long long)(-gx));
+        atomicAdd(&s_g[wib][il][1], (unsigned long long)(-gy));
+        atomicAdd(&s_g[wib][il][2], (unsigned long long)(-gz));
+        atomicAdd(&s_g[wib][CV_T + jc][0], (unsigned long long)gx);
+        atomicAdd(&s_g[wib][CV_T + jc][1], (unsigned long long)gy);
+        atomicAdd(&s_g[wib][CV_T + jc][2], (unsigned long long)gz);
       }
     }
-    const int src = (lane + 1) & 31;
-    gjx = __shfl_sync(0xffffffffu, gjx, src);
-    gjy = __shfl_sync(0xffffffffu, gjy, src);
-    gjz = __shfl_sync(0xffffffffu, gjz, src);
   }
-  if (i < ncv && (gix | giy | giz)) {
-    red_add(d.gx + T.cv0 + i, gix); red_add(d.gy + T.cv0 + i, giy); red_add(d.gz + T.cv0 + i, giz);
-  }
-  if (jl < ncv && (gjx | gjy | gjz)) {
-    red_add(d.gx + T.cv0 + jl, gjx); red_add(d.gy + T.cv0 + jl, gjy); red_add(d.gz + T.cv0 + jl, gjz);
+  __syncwarp();
+  if (n_near > 0) {
+    if (i < ncv) {
+      const long long a0 = (long long)s_g[wib][lane][0], a1 = (long long)s_g[wib][lane][1],
+                      a2 = (long long)s_g[wib][lane][2];
+      if (a0 | a1 | a2) { red_add(d.gx + T.cv0 + i, a0); red_add(d.gy + T.cv0 + i, a1); red_add(d.gz + T.cv0 + i, a2); }
+    }
+    if (jl < ncv) {
+      const long long a0 = (long long)s_g[wib][CV_T + lane][0], a1 = (long long)s_g[wib][CV_T + lane][1],
+                      a2 = (long long)s_g[wib][CV_T + lane][2];
+      if (a0 | a1 | a2) { red_add(d.gx + T.cv0 + jl, a0); red_add(d.gy + T.cv0 + jl, a1); red_add(d.gz + T.cv0 + jl, a2); }
+    }
   }
   double zl = ff_to_d(zacc);
 #pragma unroll
@@ -216,8 +216,8 @@ __global__ void __launch_bounds__(256) k_cvfin(Dev d, SimConst c) {
     if (!isfinite(z)) atomicOr(d.err, ERR_NONFINITE);
     if (c.rec_cap > 0) {
       long long n = MODE == FIN_STEP ? step_now + 1 : step_now;
-      double *r = d.rec + ((size_t)t * c.rec_cap + (size_t)(n % c.rec_cap)) * 4;
-      r[0] = z; r[1] = S.zm; r[2] = a; r[3] = phi;
+      double *r = d.rec + ((size_t)t * c.rec_cap + (size_t)(n % c.rec_cap)) * 5;
+      r[0] = z; r[1] = S.zm; r[2] = a; r[3] = phi; r[4] = Q;
     }
     if (MODE == FIN_STEP) {
       __threadfence();
@@ -235,6 +235,22 @@ __global__ void __launch_bounds__(256) k_cvfin(Dev d, SimConst c) {
   }
 }
 
+// CV-atom positions of one trial after every force evaluation (the step
+// counter has already advanced for a step; frame index = step % capacity)
+__global__ void k_rec_frames(Dev d, int trial, int cap, float *frames) {
+  const TrialInfo &T = d.tinfo[trial];
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= T.n_cv) return;
+  const long long n = *d.step;
+  const float4 p = d.pos[d.slot_of[T.atom0 + i]];
+  float *f = frames + ((size_t)(n % cap) * T.n_cv + i) * 3;
+  f[0] = p.x; f[1] = p.y; f[2] = p.z;
+}
+
+void launch_rec_frames(const Dev &d, int trial, int n_cv, int cap, float *frames, cudaStream_t s) {
+  if (n_cv > 0 && cap > 0) k_rec_frames<<<(n_cv + 127) / 128, 128, 0, s>>>(d, trial, cap, frames);
+}
+
 void launch_cnat(const Dev &d, const SimConst &c, const double *native, const int32_t *sys_nat0, int32_t n_tiles,
                  const int32_t *tile_sys, cudaStream_t s) {
   if (n_tiles <= 0) return;
@@ -246,8 +262,7 @@ void launch_zconst(const Dev &d, const int32_t *sys_tile0, const int32_t *sys_nt
 }
 void launch_cv(const Dev &d, const SimConst &c, cudaStream_t s) {
   if (d.total_work <= 0) return;
-  long long threads = (long long)d.total_work * 32;
-  k_cv<<<(unsigned)((threads + 127) / 128), 128, 0, s>>>(d, c);
+  k_cv<<<(unsigned)((d.total_work + CV_WARPS - 1) / CV_WARPS), CV_WARPS * 32, 0, s>>>(d, c);
 }
 void launch_cvfin(const Dev &d, const SimConst &c, FinMode mode, cudaStream_t s) {
   if (mode == FIN_STEP) k_cvfin<FIN_STEP><<<d.n_trials, 256, 0, s>>>(d, c);

@@ -51,7 +51,7 @@ struct Dev {
   unsigned int *done;                  // block ticket of the per-trial finaliser
   long long *energy;                   // [n_trials * 5] fixed point (2^24): LJ, RF, bond, angle, kin
   long long *skin_count;
-  double *rec;                         // [n_trials * rec_cap * 4]
+  double *rec;                         // [n_trials * rec_cap * 5]: z, z_m, a, phi, Q
 };
 
 enum UpdateMode { UPD_DRIFT = 0, UPD_FINAL = 1 };
@@ -71,6 +71,7 @@ void launch_cnat(const Dev &d, const SimConst &c, const double *native, const in
 void launch_zconst(const Dev &d, const int32_t *sys_tile0, const int32_t *sys_ntiles, cudaStream_t s);
 void launch_cv(const Dev &d, const SimConst &c, cudaStream_t s);
 void launch_cvfin(const Dev &d, const SimConst &c, FinMode mode, cudaStream_t s);
+void launch_rec_frames(const Dev &d, int trial, int n_cv, int cap, float *frames, cudaStream_t s);
 // integrator and state (vp_update.cu)
 void launch_update(const Dev &d, const SimConst &c, UpdateMode mode, cudaStream_t s);
 void launch_init_vel(const Dev &d, float kT, const int32_t *need, cudaStream_t s);

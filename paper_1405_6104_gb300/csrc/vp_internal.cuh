@@ -105,6 +105,8 @@ struct SimConst {
   double cv_r0_d, cv_rs_d, cv_rc_d;
   int32_t cv_min_sep;
   int32_t rec_cap;
+  int32_t uniform_gamma;      // every atom of every system has the same friction
+  float c1_u, c2sqkT_u;       // then exp(-gamma dt) and sqrt((1 - c1^2) kT)
 };
 
 // ---------------------------------------------------------------------------

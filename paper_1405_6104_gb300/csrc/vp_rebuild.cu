@@ -93,13 +93,19 @@ __global__ void k_colscan(Dev d) {
     pc += (n + CL - 1) / CL;
   }
   if (bad) atomicOr(d.err, ERR_COL);
-  if (threadIdx.x == NT - 1) {
-    int total = s_c[NT - 1];
-    if (total > T.max_clus) {
-      atomicOr(d.err, ERR_CAPACITY);
-      total = T.max_clus;
-    }
-    d.tstate[t].n_clus = total;
+  int total = s_c[NT - 1];
+  if (total > T.max_clus) {
+    if (threadIdx.x == 0) atomicOr(d.err, ERR_CAPACITY);
+    total = T.max_clus;
+  }
+  if (threadIdx.x == NT - 1) d.tstate[t].n_clus = total;
+  // slots past the new clusters become empty (the re-sorted layout is copied
+  // over the current one after k_colsort)
+  for (int sl = T.slot0 + total * CL + threadIdx.x; sl < T.slot0 + T.max_clus * CL; sl += NT) {
+    d.orig_b[sl] = -1;
+    d.pos_b[sl] = pad_pos(sl);
+    d.vel_b[sl] = make_float4(0.f, 0.f, 0.f, 0.f);
+    d.type_b[sl] = 0;
   }
 }
 

@@ -16,13 +16,15 @@ __global__ void __launch_bounds__(256) k_update(Dev d, SimConst c) {
   const int slot = blockIdx.x * blockDim.x + threadIdx.x;
   if (slot >= d.total_slots) return;
   if (MODE == UPD_FINAL && slot == 0) *d.kick = 0.5f;
-  const int t = d.slot_trial[slot];
-  const TrialInfo &T = d.tinfo[t];
-  if (slot - T.slot0 >= d.tstate[t].n_clus * CL) return;
+  // every slot-indexed load is issued before any of them is needed; slots
+  // past a trial's clusters and padding slots carry orig = -1
   const int o = d.orig[slot];
-  if (o < 0) return;
+  const int t = d.slot_trial[slot];
   float4 p = d.pos[slot], v = d.vel[slot];
-  float Fx = fx_to(d.fx[slot]), Fy = fx_to(d.fy[slot]), Fz = fx_to(d.fz[slot]);
+  const long long fxi = d.fx[slot], fyi = d.fy[slot], fzi = d.fz[slot];
+  if (o < 0) return;
+  const TrialInfo &T = d.tinfo[t];
+  float Fx = fx_to(fxi), Fy = fx_to(fyi), Fz = fx_to(fzi);
   if (MODE == UPD_DRIFT) { d.fx[slot] = 0; d.fy[slot] = 0; d.fz[slot] = 0; }
   if (o < T.n_cv) {
     // ratchet force F_i = -(k_R/2) a grad_i z (Eq. VR); a = 0 when z <= z_m
@@ -37,13 +39,21 @@ __global__ void __launch_bounds__(256) k_update(Dev d, SimConst c) {
   const float kdt = kick * c.dt * v.w;
   v.x += kdt * Fx; v.y += kdt * Fy; v.z += kdt * Fz;
   if (MODE == UPD_DRIFT) {
-    const AtomSys as = d.asys[T.sysatom0 + o];
+    float c1, c2sd;
+    if (c.uniform_gamma) {  // c2 sqrt(kT/m) = c2 sqrt(kT) sqrt(1/m)
+      c1 = c.c1_u;
+      c2sd = c.c2sqkT_u * sqrtf(v.w);
+    } else {
+      const AtomSys as = d.asys[T.sysatom0 + o];
+      c1 = as.c1;
+      c2sd = as.c2sd;
+    }
     const unsigned long long step = (unsigned long long)(*d.step) + 1ull;
     p.x += c.half_dt * v.x; p.y += c.half_dt * v.y; p.z += c.half_dt * v.z;
     const float3 xi = normal3(T.key0, T.key1, (uint32_t)o, step, 0u);
-    v.x = as.c1 * v.x + as.c2sd * xi.x;
-    v.y = as.c1 * v.y + as.c2sd * xi.y;
-    v.z = as.c1 * v.z + as.c2sd * xi.z;
+    v.x = c1 * v.x + c2sd * xi.x;
+    v.y = c1 * v.y + c2sd * xi.y;
+    v.z = c1 * v.z + c2sd * xi.z;
     p.x += c.half_dt * v.x; p.y += c.half_dt * v.y; p.z += c.half_dt * v.z;
     if (!(isfinite(p.x) && isfinite(p.y) && isfinite(p.z) && isfinite(v.x) && isfinite(v.y) && isfinite(v.z)))
       atomicOr(d.err, ERR_NONFINITE);

@@ -122,6 +122,9 @@ def test_functional_parity_on_shared_states(name):
     assert np.allclose(rec[1:, 0], z[1:], rtol=1e-11, atol=1e-11)
     assert np.allclose(rec[1:, 2], a[1:], rtol=1e-6, atol=1e-9 * max(1.0, z.max()))
     assert np.allclose(rec[1:, 3], phi[1:], rtol=1e-5, atol=1e-12 * max(1.0, phi.max()))
+    biased = rec[1:, 2] > 0
+    assert np.allclose(rec[1:, 3][biased], (0.5 * p.k_ratchet) ** 2 * rec[1:, 2][biased] ** 2 * rec[1:, 4][biased],
+                       rtol=1e-12)
 
 
 def test_batch_invariance_and_determinism():
