@@ -83,6 +83,7 @@ _SIGS = {
     "phi_adjoint_coefficients": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p], C.c_int),
     "sim_pairlist": ([C.c_void_p, C.c_int32, C.c_void_p, C.c_int64, C.c_void_p], C.c_int),
     "sim_diagnostics": ([C.c_void_p, C.c_void_p], C.c_int),
+    "sim_autotune": ([C.c_void_p, C.c_int32, C.c_char_p, C.c_void_p], C.c_int),
     "sim_set_timing": ([C.c_void_p, C.c_int32], C.c_int),
     "sim_kernel_times": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32], C.c_int),
     "sim_philox_normals": ([C.c_uint64, C.c_int64, C.c_uint32, C.c_int32, C.c_void_p, C.c_void_p], C.c_int),
@@ -282,6 +283,13 @@ def sim_diagnostics(h):
     _check(h, load().sim_diagnostics(h, out.ctypes.data))
     return dict(skin_violations=int(out[0]), max_list_entries=int(out[1]), list_capacity=int(out[2]),
                 clusters=int(out[3]))
+
+
+def sim_autotune(h, reps: int = 5, cache_path: Optional[str] = None):
+    """Picks the fastest launch shapes for this batch; returns (pair, cv) variants."""
+    ch = np.zeros(2, np.int32)
+    _check(h, load().sim_autotune(h, int(reps), None if cache_path is None else cache_path.encode(), ch.ctypes.data))
+    return int(ch[0]), int(ch[1])
 
 
 def sim_set_timing(h, on: bool):

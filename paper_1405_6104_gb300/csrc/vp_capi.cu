@@ -49,6 +49,7 @@ struct sim_handle {
   std::vector<void *> allocs;
   std::string err;
   int rec_cap = 0;
+  int pair_variant = 0, cv_variant = 0;  // launch shapes picked by the autotuner
   // CV-frame recorder (one trial)
   int frame_trial = -1, frame_cap = 0;
   float *frames = nullptr;
@@ -151,8 +152,8 @@ void rebuild(sim_handle *h) {
 
 void forces(sim_handle *h, FinMode mode) {
   cudaStream_t s = h->stream;
-  timed(h, "pair", [&] { launch_pair(h->d, h->c, false, -1, s); });
-  timed(h, "cv", [&] { launch_cv(h->d, h->c, s); });
+  timed(h, "pair", [&] { launch_pair(h->d, h->c, false, -1, s, h->pair_variant); });
+  timed(h, "cv", [&] { launch_cv(h->d, h->c, s, h->cv_variant); });
   timed(h, "cvfin", [&] { launch_cvfin(h->d, h->c, mode, s); });
   if (h->frames)
     launch_rec_frames(h->d, h->frame_trial, h->tinfo[h->frame_trial].n_cv, h->frame_cap, h->frames, s);
@@ -900,6 +901,110 @@ VP_API int phi_adjoint_coefficients(sim_handle *h, const double *z, const double
   std::string err;
   r = adjoint_coefficients(z, Q, n, h->c.dt_d * h->c.kR_half_d * h->c.kR_half_d, coef, phi, h->stream, err);
   if (r) return fail(h, r, "phi_adjoint_coefficients: " + err);
+  return SIM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// autotuner: times the launch-shape variants of the pair and reaction-
+// coordinate kernels on this batch (into scratch accumulators, so the state
+// is untouched) and keeps the fastest; results are cached per size class
+// (atoms per trial, trials, atom density) in a small text file.
+// ---------------------------------------------------------------------------
+namespace {
+
+std::string tune_key(const sim_handle *h) {
+  long long atoms = 0;
+  double vol = 0.0;
+  for (const auto &T : h->tinfo) {
+    atoms += T.n_atoms;
+    vol += (double)T.box * T.box * T.box;
+  }
+  const int lg_atoms = (int)std::lround(std::log2((double)std::max(1LL, atoms)));
+  const int lg_trials = (int)std::lround(std::log2((double)std::max(1, h->n_trials)));
+  const int dens = (int)std::lround(atoms / std::max(vol, 1e-9) / 10.0);
+  char buf[96];
+  std::snprintf(buf, sizeof(buf), "a%d_t%d_d%d_nt%d", lg_atoms, lg_trials, dens, h->c.n_types);
+  return buf;
+}
+
+bool tune_lookup(const char *path, const std::string &key, int &pv, int &cv) {
+  FILE *f = path ? std::fopen(path, "r") : nullptr;
+  if (!f) return false;
+  char k[128];
+  int a, b;
+  bool found = false;
+  while (std::fscanf(f, "%127s %d %d", k, &a, &b) == 3)
+    if (key == k) { pv = a; cv = b; found = true; }
+  std::fclose(f);
+  return found && pv >= 0 && pv < PAIR_VARIANTS && cv >= 0 && cv < CV_VARIANTS;
+}
+
+void tune_store(const char *path, const std::string &key, int pv, int cv) {
+  if (!path) return;
+  FILE *f = std::fopen(path, "a");
+  if (!f) return;
+  std::fprintf(f, "%s %d %d\n", key.c_str(), pv, cv);
+  std::fclose(f);
+}
+
+}  // namespace
+
+VP_API int sim_autotune(sim_handle *h, int32_t reps, const char *cache_path, int32_t *choice) {
+  int r = enter(h);
+  if (r) return r;
+  if (reps < 1) reps = 5;
+  const std::string key = tune_key(h);
+  int pv = 0, cv = 0;
+  if (!tune_lookup(cache_path, key, pv, cv)) {
+    // scratch accumulators: the timed launches must not touch the state
+    Dev scratch = h->d;
+    const size_t ns = (size_t)h->d.total_slots;
+    size_t ncv = 0;
+    for (auto &T : h->tinfo) ncv += T.n_cv;
+    long long *buf = nullptr;
+    double *zp = nullptr;
+    CK(cudaMalloc(&buf, sizeof(long long) * (3 * ns + 3 * std::max<size_t>(ncv, 1))));
+    CK(cudaMalloc(&zp, sizeof(double) * std::max(1, h->d.total_work)));
+    scratch.fx = buf; scratch.fy = buf + ns; scratch.fz = buf + 2 * ns;
+    scratch.gx = buf + 3 * ns; scratch.gy = scratch.gx + ncv; scratch.gz = scratch.gy + ncv;
+    scratch.z_part = zp;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    auto time_it = [&](auto &&launch) {
+      launch();  // warm
+      cudaEventRecord(e0, h->stream);
+      for (int k = 0; k < reps; ++k) launch();
+      cudaEventRecord(e1, h->stream);
+      cudaEventSynchronize(e1);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      return ms;
+    };
+    float best = 3e38f;
+    for (int v = 0; v < PAIR_VARIANTS; ++v) {
+      float ms = time_it([&] { launch_pair(scratch, h->c, false, -1, h->stream, v); });
+      if (ms < best) { best = ms; pv = v; }
+    }
+    best = 3e38f;
+    for (int v = 0; v < CV_VARIANTS; ++v) {
+      float ms = time_it([&] { launch_cv(scratch, h->c, h->stream, v); });
+      if (ms < best) { best = ms; cv = v; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(buf);
+    cudaFree(zp);
+    CK(cudaGetLastError());
+    tune_store(cache_path, key, pv, cv);
+  }
+  h->pair_variant = pv;
+  h->cv_variant = cv;
+  if (h->chunk) {
+    cudaGraphExecDestroy(h->chunk);
+    h->chunk = nullptr;
+  }
+  if (choice) { choice[0] = pv; choice[1] = cv; }
   return SIM_OK;
 }
 

@@ -77,8 +77,7 @@ __global__ void k_zconst(Dev d, const int32_t *sys_tile0, const int32_t *sys_nti
 // float-float, accumulating the gradient of the tile's 64 atoms with int64
 // shared-memory atomics (order-independent, so deterministic) and flushing it
 // once per tile.  Far pairs (C~ = 0) contribute only to the constant Z0.
-constexpr int CV_WARPS = 4;
-
+template <int CV_WARPS>
 __global__ void __launch_bounds__(CV_WARPS * 32) k_cv(Dev d, SimConst c) {
   __shared__ unsigned short s_near[CV_WARPS][CV_T * CV_T];
   __shared__ float s_x[CV_WARPS][2 * CV_T][3];
@@ -260,9 +259,12 @@ void launch_cnat(const Dev &d, const SimConst &c, const double *native, const in
 void launch_zconst(const Dev &d, const int32_t *sys_tile0, const int32_t *sys_ntiles, cudaStream_t s) {
   k_zconst<<<d.n_trials, 256, 0, s>>>(d, sys_tile0, sys_ntiles);
 }
-void launch_cv(const Dev &d, const SimConst &c, cudaStream_t s) {
+// variants: 0: 4 warps per block, 1: 2 warps, 2: 8 warps
+void launch_cv(const Dev &d, const SimConst &c, cudaStream_t s, int variant) {
   if (d.total_work <= 0) return;
-  k_cv<<<(unsigned)((d.total_work + CV_WARPS - 1) / CV_WARPS), CV_WARPS * 32, 0, s>>>(d, c);
+  if (variant == 1) k_cv<2><<<(unsigned)((d.total_work + 1) / 2), 64, 0, s>>>(d, c);
+  else if (variant == 2) k_cv<8><<<(unsigned)((d.total_work + 7) / 8), 256, 0, s>>>(d, c);
+  else k_cv<4><<<(unsigned)((d.total_work + 3) / 4), 128, 0, s>>>(d, c);
 }
 void launch_cvfin(const Dev &d, const SimConst &c, FinMode mode, cudaStream_t s) {
   if (mode == FIN_STEP) k_cvfin<FIN_STEP><<<d.n_trials, 256, 0, s>>>(d, c);

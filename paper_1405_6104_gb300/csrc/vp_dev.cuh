@@ -64,12 +64,14 @@ void launch_colfill(const Dev &d, cudaStream_t s);
 void launch_colsort(const Dev &d, cudaStream_t s);
 void launch_list(const Dev &d, const SimConst &c, float rl2_bbox, cudaStream_t s);
 // forces (vp_pair.cu)
-void launch_pair(const Dev &d, const SimConst &c, bool energy, int32_t only_trial, cudaStream_t s);
+void launch_pair(const Dev &d, const SimConst &c, bool energy, int32_t only_trial, cudaStream_t s, int variant = 0);
+constexpr int PAIR_VARIANTS = 3;
 // reaction coordinate and functional (vp_cv.cu)
 void launch_cnat(const Dev &d, const SimConst &c, const double *native, const int32_t *sys_nat0, int32_t n_tiles_total,
                  const int32_t *tile_sys, cudaStream_t s);
 void launch_zconst(const Dev &d, const int32_t *sys_tile0, const int32_t *sys_ntiles, cudaStream_t s);
-void launch_cv(const Dev &d, const SimConst &c, cudaStream_t s);
+void launch_cv(const Dev &d, const SimConst &c, cudaStream_t s, int variant = 0);
+constexpr int CV_VARIANTS = 3;
 void launch_cvfin(const Dev &d, const SimConst &c, FinMode mode, cudaStream_t s);
 void launch_rec_frames(const Dev &d, int trial, int n_cv, int cap, float *frames, cudaStream_t s);
 // integrator and state (vp_update.cu)

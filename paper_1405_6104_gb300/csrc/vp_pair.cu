@@ -121,8 +121,8 @@ __device__ __forceinline__ void pair_block(const float (&xi)[CL], const float (&
   }
 }
 
-template <bool ENERGY>
-__global__ void __launch_bounds__(128) k_pair(Dev d, SimConst c, int only_trial) {
+template <bool ENERGY, int MINB>
+__global__ void __launch_bounds__(128, MINB) k_pair(Dev d, SimConst c, int only_trial) {
   extern __shared__ float2 smem_tab[];
   __shared__ float s_red[ENERGY ? 1 : 4][ENERGY ? 1 : 3 * CL * 33];
   float2 *tab = smem_tab;
@@ -241,12 +241,187 @@ __global__ void __launch_bounds__(128) k_pair(Dev d, SimConst c, int only_trial)
   }
 }
 
-void launch_pair(const Dev &d, const SimConst &c, bool energy, int32_t only_trial, cudaStream_t s) {
+// Force-only kernel (the hot path).  Per warp, shared memory holds the LJ
+// coefficients of its 8 i-atoms against every type (row a at a fixed stride,
+// so the pair loop addresses them with immediate offsets) and the 27 image
+// shifts of its box; the list mask enters the squared distance as a penalty
+// (0 or 1e30), so a masked pair falls outside the cut-off without any
+// per-pair bit test.  Arithmetic per pair: 3 FADD, 6 FMUL, 12 FFMA, 1 RSQ,
+// 1 LDS, 1 FSETP + FSEL.
+constexpr int PF_WARPS = 4;
+constexpr float MASK_PEN = 1.0e30f;
+
+template <int MINB>
+__global__ void __launch_bounds__(PF_WARPS * 32, MINB) k_pair_f(Dev d, SimConst c) {
+  __shared__ float2 s_cij[PF_WARPS][CL][MAX_TYPES];
+  __shared__ float4 s_sh[PF_WARPS][64];
+  __shared__ float s_red[PF_WARPS][3 * CL * 33];
+  const int wib = threadIdx.x >> 5;
+  const int I = blockIdx.x * PF_WARPS + wib;
+  const int lane = threadIdx.x & 31;
+  if (I >= d.total_clus) return;
+  const int t = d.clus_trial[I];
+  const TrialInfo T = d.tinfo[t];
+  if (I - T.clus0 >= d.tstate[t].n_clus) return;
+  const float L = T.box, iL = T.inv_box;
+  const int g = lane >> 2, b = lane & 3;
+  const int NT = c.n_types;
+
+  float xi[CL], yi[CL], zi[CL], qi[CL];
+  int ti[CL];
+#pragma unroll
+  for (int a = 0; a < CL; ++a) {
+    const float4 p = d.pos[I * CL + a];
+    xi[a] = p.x; yi[a] = p.y; zi[a] = p.z; qi[a] = p.w;
+    ti[a] = d.type[I * CL + a];
+  }
+  // per-warp tables: LJ rows of the i-atoms, image shifts (code = (nx+1) | (ny+1)<<2 | (nz+1)<<4)
+  for (int k = lane; k < CL * NT; k += 32) {
+    const int a = k / NT, tj = k - a * NT;
+    int tia = ti[0];
+#pragma unroll
+    for (int q = 1; q < CL; ++q)
+      if (q == a) tia = ti[q];
+    s_cij[wib][a][tj] = d.ljtab[tia * NT + tj];
+  }
+  for (int k = lane; k < 64; k += 32) {
+    const int nx = (k & 3) - 1, ny = ((k >> 2) & 3) - 1, nz = ((k >> 4) & 3) - 1;
+    s_sh[wib][k] = make_float4(L * nx, L * ny, L * nz, 0.f);
+  }
+  __syncwarp();
+  float fi[CL][3];
+#pragma unroll
+  for (int a = 0; a < CL; ++a) fi[a][0] = fi[a][1] = fi[a][2] = 0.0f;
+
+  const int n = d.list_n[I];
+  const uint2 *seg = d.list + (size_t)I * c.list_cap;
+  uint2 ent = g < n ? seg[g] : make_uint2(0u, 0u);
+  uint2 ent_n = 8 + g < n ? seg[8 + g] : make_uint2(0u, 0u);
+  float4 pj = d.pos[(int)(ent.x & J_MASK) * CJ + b];
+  int tj = d.type[(int)(ent.x & J_MASK) * CJ + b];
+  for (int e0 = 0; e0 < n; e0 += 8) {
+    const uint2 ent_nn = e0 + 16 + g < n ? seg[e0 + 16 + g] : make_uint2(0u, 0u);
+    const int sj_n = (int)(ent_n.x & J_MASK) * CJ + b;
+    const float4 pj_n = d.pos[sj_n];
+    const int tj_n = d.type[sj_n];
+    const int sj = (int)(ent.x & J_MASK) * CJ + b;
+    const float4 shv = s_sh[wib][(ent.x >> J_BITS) & 63u];
+    const float xj = pj.x - shv.x, yj = pj.y - shv.y, zj = pj.z - shv.z, qj = pj.w;
+    const unsigned mb = ent.y >> b;
+    const bool exact = (ent.x & E_EXACT) != 0u;
+    const float2 *row = &s_cij[wib][0][tj];
+    float fjx = 0.f, fjy = 0.f, fjz = 0.f;
+    if (!__any_sync(0xffffffffu, exact)) {
+#pragma unroll
+      for (int a = 0; a < CL; ++a) {
+        const float pen = (mb & (1u << (4 * a))) ? 0.0f : MASK_PEN;
+        const float dx = __fsub_rn(xj, xi[a]), dy = __fsub_rn(yj, yi[a]), dz = __fsub_rn(zj, zi[a]);
+        const float r2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmaf_rn(dx, dx, pen)));
+        const float rinv = rsqrtf(r2);
+        const float rinv2 = __fmul_rn(rinv, rinv);
+        const float rinv6 = __fmul_rn(__fmul_rn(rinv2, rinv2), rinv2);
+        const float2 cc = row[a * MAX_TYPES];
+        const float qq = __fmul_rn(qi[a], qj);
+        float tt = __fmaf_rn(cc.y, rinv6, -cc.x);
+        tt = __fmul_rn(tt, rinv6);
+        tt = __fmaf_rn(qq, rinv, tt);
+        tt = __fmul_rn(tt, rinv2);
+        float f = __fmaf_rn(-qq, c.two_krf, tt);
+        f = r2 < c.rc2 ? f : 0.0f;
+        fi[a][0] = __fmaf_rn(-f, dx, fi[a][0]);
+        fi[a][1] = __fmaf_rn(-f, dy, fi[a][1]);
+        fi[a][2] = __fmaf_rn(-f, dz, fi[a][2]);
+        fjx = __fmaf_rn(f, dx, fjx);
+        fjy = __fmaf_rn(f, dy, fjy);
+        fjz = __fmaf_rn(f, dz, fjz);
+      }
+    } else {
+      // some entry of this group needs pair-by-pair minimum images
+#pragma unroll
+      for (int a = 0; a < CL; ++a) {
+        const float pen = (mb & (1u << (4 * a))) ? 0.0f : MASK_PEN;
+        float dx = __fsub_rn(xj, xi[a]), dy = __fsub_rn(yj, yi[a]), dz = __fsub_rn(zj, zi[a]);
+        if (exact) {
+          dx = __fmaf_rn(-L, rintf(__fmul_rn(dx, iL)), dx);
+          dy = __fmaf_rn(-L, rintf(__fmul_rn(dy, iL)), dy);
+          dz = __fmaf_rn(-L, rintf(__fmul_rn(dz, iL)), dz);
+        }
+        const float r2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmaf_rn(dx, dx, pen)));
+        const float rinv = rsqrtf(r2);
+        const float rinv2 = __fmul_rn(rinv, rinv);
+        const float rinv6 = __fmul_rn(__fmul_rn(rinv2, rinv2), rinv2);
+        const float2 cc = row[a * MAX_TYPES];
+        const float qq = __fmul_rn(qi[a], qj);
+        float tt = __fmaf_rn(cc.y, rinv6, -cc.x);
+        tt = __fmul_rn(tt, rinv6);
+        tt = __fmaf_rn(qq, rinv, tt);
+        tt = __fmul_rn(tt, rinv2);
+        float f = __fmaf_rn(-qq, c.two_krf, tt);
+        f = r2 < c.rc2 ? f : 0.0f;
+        fi[a][0] = __fmaf_rn(-f, dx, fi[a][0]);
+        fi[a][1] = __fmaf_rn(-f, dy, fi[a][1]);
+        fi[a][2] = __fmaf_rn(-f, dz, fi[a][2]);
+        fjx = __fmaf_rn(f, dx, fjx);
+        fjy = __fmaf_rn(f, dy, fjy);
+        fjz = __fmaf_rn(f, dz, fjz);
+      }
+    }
+    if (fjx != 0.f || fjy != 0.f || fjz != 0.f) {
+      red_add(d.fx + sj, fx_from(fjx));
+      red_add(d.fy + sj, fx_from(fjy));
+      red_add(d.fz + sj, fx_from(fjz));
+    }
+    ent = ent_n;
+    ent_n = ent_nn;
+    pj = pj_n;
+    tj = tj_n;
+  }
+
+  // bonded terms of the 8 i-atoms (lanes 0..7)
+  if (lane < CL) {
+    const int o = d.orig[I * CL + lane];
+    if (o >= 0) {
+      float4 self = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+      for (int a = 0; a < CL; ++a)
+        if (a == lane) self = make_float4(xi[a], yi[a], zi[a], 0.f);
+      float eb = 0.f, ea = 0.f;
+      const float3 fb = bonded_force(d, T, o, self, eb, ea);
+#pragma unroll
+      for (int a = 0; a < CL; ++a)
+        if (a == lane) { fi[a][0] += fb.x; fi[a][1] += fb.y; fi[a][2] += fb.z; }
+    }
+  }
+  // i-forces: column sums of the 32 lanes' partials in a fixed order
+  float *r = s_red[wib];
+#pragma unroll
+  for (int a = 0; a < CL; ++a)
+#pragma unroll
+    for (int k = 0; k < 3; ++k) r[(3 * a + k) * 33 + lane] = fi[a][k];
+  __syncwarp();
+  if (lane < 3 * CL) {
+    float sum = 0.f;
+    for (int l = 0; l < 32; ++l) sum += r[lane * 33 + l];
+    const int a = lane / 3, comp = lane - 3 * a;
+    const long long val = fx_from(sum);
+    if (val != 0) red_add((comp == 0 ? d.fx : comp == 1 ? d.fy : d.fz) + I * CL + a, val);
+  }
+}
+
+// variants differ in the register cap (blocks per SM the compiler must fit):
+// 0: 4 blocks, 1: 5 blocks, 2: 6 blocks
+void launch_pair(const Dev &d, const SimConst &c, bool energy, int32_t only_trial, cudaStream_t s, int variant) {
   long long threads = (long long)d.total_clus * 32;
   unsigned blocks = (unsigned)((threads + 127) / 128);
   const size_t nt2 = (size_t)c.n_types * c.n_types;
-  if (energy) k_pair<true><<<blocks, 128, nt2 * (sizeof(float2) + sizeof(float)), s>>>(d, c, only_trial);
-  else k_pair<false><<<blocks, 128, nt2 * sizeof(float2), s>>>(d, c, only_trial);
+  if (energy || only_trial >= 0) {
+    k_pair<true, 4><<<blocks, 128, nt2 * (sizeof(float2) + sizeof(float)), s>>>(d, c, only_trial);
+    return;
+  }
+  const unsigned fb = (unsigned)((d.total_clus + PF_WARPS - 1) / PF_WARPS);
+  if (variant == 1) k_pair_f<5><<<fb, PF_WARPS * 32, 0, s>>>(d, c);
+  else if (variant == 2) k_pair_f<6><<<fb, PF_WARPS * 32, 0, s>>>(d, c);
+  else k_pair_f<4><<<fb, PF_WARPS * 32, 0, s>>>(d, c);
 }
 
 }  // namespace vp

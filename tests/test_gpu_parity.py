@@ -259,3 +259,23 @@ def test_potential_autograd_backward_is_minus_force():
         assert rel_rms(y.grad.numpy(), -Fr2) < 1e-5
     finally:
         ev.close()
+
+
+def test_autotuner_variants_are_bit_identical(tmp_path):
+    """Every launch shape the autotuner can pick computes the same result."""
+    s, p = S.small_solvated()
+    results = []
+    for pv in range(3):
+        for cv in (0, 2):
+            cache = tmp_path / f"tune_{pv}_{cv}.txt"
+            with B.TrialBatch(s, p, [2], trial_seeds=[4, 5]) as b:
+                key_probe = tmp_path / "probe.txt"
+                B.sim_autotune(b.h, 1, str(key_probe))  # learn the size-class key
+                key = key_probe.read_text().split()[0]
+                cache.write_text(f"{key} {pv} {cv}\n")
+                assert B.sim_autotune(b.h, 1, str(cache)) == (pv, cv)
+                b.step(30)
+                results.append([b.get_state(t) for t in range(2)])
+    for r in results[1:]:
+        for x, y in zip(results[0], r):
+            assert np.array_equal(x[0], y[0]) and np.array_equal(x[1], y[1]) and x[2][3] == y[2][3]
