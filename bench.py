@@ -234,6 +234,28 @@ def run_gpu(args):
     diag = B.sim_diagnostics(batch.h)
     batch.close()
 
+    # plain: one trial of the same system on the same kernels (graph replay),
+    # the single-trial GPU baseline that batching is compared with
+    plain = None
+    if rank == 0:
+        with B.TrialBatch(s, p, [1], trial_seeds=seeds[:1]) as one:
+            B.sim_autotune(one.h, 5, None)
+            ostream = torch.cuda.ExternalStream(one.stream)
+            for _ in range(args.warmup):
+                one.step(nst)
+            torch.cuda.synchronize()
+            n_plain = max(10, args.steps)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(ostream)
+            for _ in range(n_plain):
+                one.step(nst)
+            e1.record(ostream)
+            torch.cuda.synchronize()
+            pv = s.n_atoms * nst * n_plain / (e0.elapsed_time(e1) * 1e-3)
+            plain = {"value": pv, "unit": "atom-steps/s",
+                     "workload": f"1 trial x {s.n_atoms} atoms, same kernels and graph replay, {n_plain} x {nst} MD steps",
+                     "batching_speedup": value / world / pv}
+
     if rank == 0:
         pk, src = peaks()
         pair_ms, pair_n = kt.get("pair", (float("nan"), 1))
@@ -266,6 +288,7 @@ def run_gpu(args):
                           "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": hbm_achieved / pk["hbm_gbs"],
                           "peak_source": src},
             "kernel_ms": {k: v[0] / max(v[1], 1) for k, v in kt.items()},
+            "plain": plain,
             "cpu_baseline": cb,
             "e2e": e2e,
             "gpu_launches": args.steps * (4 * nst + 5 + 1),

@@ -233,6 +233,39 @@ __device__ __forceinline__ bool list_rule(float4 pi, float4 pj, float L, float i
   return r2 < rl2;
 }
 
+__device__ __forceinline__ bool excluded(const int *ex, int n, int o) {
+  for (int q = 0; q < n; ++q)
+    if (ex[q] == o) return true;
+  return false;
+}
+
+// A candidate whose atom pairs do not all share the image counts (it spans
+// half a box length in some dimension): the per-pair rule for all 8 x 4
+// pairs, with validity, self-pair and exclusion tests; kmin/kmax collect the
+// image keys of the passing pairs.
+__device__ __noinline__ unsigned list_mixed_images(const Dev &d, int I, int Il, int J8, int sj0, float L, float iL,
+                                                   float rl2, const int (*ex)[MAX_EXCL], const int *nex, float &kmin,
+                                                   float &kmax) {
+  unsigned mask = 0u;
+  for (int b = 0; b < CJ; ++b) {
+    const float4 pj = d.pos[sj0 + b];
+    const int oj = d.orig[sj0 + b];
+    for (int a = 0; a < CL; ++a) {
+      const float4 pi = d.pos[I * CL + a];
+      const int oi = d.orig[I * CL + a];
+      float key;
+      bool v = list_rule(pi, pj, L, iL, rl2, key) && oi >= 0 && oj >= 0 && (J8 != Il || sj0 + b > I * CL + a);
+      if (v && excluded(ex[a], nex[a], oj)) v = false;
+      if (v) {
+        kmin = fminf(kmin, key);
+        kmax = fmaxf(kmax, key);
+        mask |= 1u << (a * CJ + b);
+      }
+    }
+  }
+  return mask;
+}
+
 constexpr int LIST_WARPS = 4;
 constexpr int CAND_MAX = 512;  // candidate 8-atom clusters per i-cluster (bounding-box pass)
 
@@ -327,12 +360,10 @@ __global__ void __launch_bounds__(LIST_WARPS * 32) k_list(Dev d, SimConst c, flo
   }
   // i-atoms and their exclusions
   float xi[CL], yi[CL], zi[CL];
-  int oi[CL];
 #pragma unroll
   for (int a = 0; a < CL; ++a) {
     const float4 p = d.pos[I * CL + a];
     xi[a] = p.x; yi[a] = p.y; zi[a] = p.z;
-    oi[a] = d.orig[I * CL + a];
   }
   if (lane < CL) {
     const int o = d.orig[I * CL + lane];
@@ -351,6 +382,20 @@ __global__ void __launch_bounds__(LIST_WARPS * 32) k_list(Dev d, SimConst c, flo
   }
   __syncwarp();
   // ---- phase 2: one candidate 4-atom j-cluster per lane ----
+  // Image counts: q = rint(fl(d * invL)) is monotone in d = fl(xj - xi), so
+  // when the two bounding-box extremes of d give the same q in a dimension,
+  // every atom pair of the candidate has that q there and the rule reduces to
+  // d - fl(L q) with the same rounding as the per-pair form.  Padding atoms
+  // sit far outside every box and fail the distance test on that path.
+  // Exclusions: an i-atom's excluded indices span [exlo, exlo + exspan]; only
+  // a j index inside that range is looked up.
+  int exlo[CL];
+  unsigned exspan[CL];
+#pragma unroll
+  for (int a = 0; a < CL; ++a) {
+    exlo[a] = s_exlo[wib][a];
+    exspan[a] = s_exhi[wib][a] >= exlo[a] ? (unsigned)(s_exhi[wib][a] - exlo[a]) : 0u;
+  }
   uint2 *seg = d.list + (size_t)I * c.list_cap;
   const float rl2 = c.rl2;
   int cnt = 0;
@@ -362,27 +407,40 @@ __global__ void __launch_bounds__(LIST_WARPS * 32) k_list(Dev d, SimConst c, flo
       const int JG = T.clus0 + J8;
       const int sj0 = JG * CL + h * CJ;
       float kmin = 3e38f, kmax = -3e38f;
+      const float4 jlo4 = d.bb_lo[JG], jhi4 = d.bb_hi[JG];
+      const float qlx = rintf(__fmul_rn(__fsub_rn(jlo4.x, hi.x), iL)), qhx = rintf(__fmul_rn(__fsub_rn(jhi4.x, lo.x), iL));
+      const float qly = rintf(__fmul_rn(__fsub_rn(jlo4.y, hi.y), iL)), qhy = rintf(__fmul_rn(__fsub_rn(jhi4.y, lo.y), iL));
+      const float qlz = rintf(__fmul_rn(__fsub_rn(jlo4.z, hi.z), iL)), qhz = rintf(__fmul_rn(__fsub_rn(jhi4.z, lo.z), iL));
+      if (qlx == qhx && qly == qhy && qlz == qhz) {
+        const float sx = __fmul_rn(L, qlx), sy = __fmul_rn(L, qly), sz = __fmul_rn(L, qlz);
+        const int4 oj4 = *reinterpret_cast<const int4 *>(d.orig + sj0);
+        const int oj[CJ] = {oj4.x, oj4.y, oj4.z, oj4.w};
 #pragma unroll
-      for (int b = 0; b < CJ; ++b) {
-        const float4 pj = d.pos[sj0 + b];
-        const int oj = d.orig[sj0 + b];
+        for (int b = 0; b < CJ; ++b) {
+          const float4 pj = d.pos[sj0 + b];
 #pragma unroll
-        for (int a = 0; a < CL; ++a) {
-          float key;
-          const float4 pi = make_float4(xi[a], yi[a], zi[a], 0.f);
-          bool v = list_rule(pi, pj, L, iL, rl2, key) && oi[a] >= 0 && oj >= 0 &&
-                   (J8 != Il || sj0 + b > I * CL + a);
-          if (v && oj >= s_exlo[wib][a] && oj <= s_exhi[wib][a]) {
-            const int ne = s_nex[wib][a];
-            for (int q = 0; q < ne; ++q)
-              if (s_excl[wib][a][q] == oj) { v = false; break; }
-          }
-          if (v) {
-            kmin = fminf(kmin, key);
-            kmax = fmaxf(kmax, key);
-            mask |= 1u << (a * CJ + b);
+          for (int a = 0; a < CL; ++a) {
+            const float dx = __fsub_rn(__fsub_rn(pj.x, xi[a]), sx);
+            const float dy = __fsub_rn(__fsub_rn(pj.y, yi[a]), sy);
+            const float dz = __fsub_rn(__fsub_rn(pj.z, zi[a]), sz);
+            const float r2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+            bool v = r2 < rl2;
+            if (v && (unsigned)(oj[b] - exlo[a]) <= exspan[a]) v = !excluded(s_excl[wib][a], s_nex[wib][a], oj[b]);
+            if (v) mask |= 1u << (a * CJ + b);
           }
         }
+        if (J8 == Il) {  // inside the i-cluster itself: pairs with the j slot above the i slot
+          unsigned tri = 0u;
+#pragma unroll
+          for (int a = 0; a < CL; ++a)
+#pragma unroll
+            for (int b = 0; b < CJ; ++b)
+              if (h * CJ + b > a) tri |= 1u << (a * CJ + b);
+          mask &= tri;
+        }
+        if (mask) kmin = kmax = __fmaf_rn(9.0f, qlx, __fmaf_rn(3.0f, qly, qlz));
+      } else {
+        mask = list_mixed_images(d, I, Il, J8, sj0, L, iL, rl2, s_excl[wib], s_nex[wib], kmin, kmax);
       }
       // image counts of the entry from the key 9 nx + 3 ny + nz (each in -1..1)
       const int key = mask ? (int)kmin : 0;

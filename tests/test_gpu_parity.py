@@ -248,7 +248,7 @@ def test_potential_autograd_backward_is_minus_force():
         L = 3.0 * U + 0.5 * (x ** 2).sum()
         L.backward()
         Fr, er = O.forces(s, p, s.pos)
-        assert float(U) == pytest.approx(er.sum(), rel=1e-5, abs=1e-5 * np.abs(er).sum())
+        assert float(U.detach()) == pytest.approx(er.sum(), rel=1e-5, abs=1e-5 * np.abs(er).sum())
         g = x.grad.numpy()
         assert rel_rms(g, -3.0 * Fr + s.pos) < 1e-5
         assert rel_rms((g - s.pos) / 3.0, -Fr) < 1e-5
