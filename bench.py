@@ -50,20 +50,37 @@ def peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    """nvidia-smi clocks and throttle reasons, sampled every 100 ms from before
+    the warm-up to after the kernel-timing pass; summarised over the samples
+    whose timestamps fall inside the timed region (or, when that region is
+    shorter than three sampling periods, over the whole loaded window)."""
+
+    NAMES = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
 
     def __init__(self, index: int):
         self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
-        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+        q = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
         try:
             self.p = subprocess.Popen(["nvidia-smi", f"--id={index}", f"--query-gpu={q}", "--format=csv,noheader,nounits",
-                                       "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+                                       "-lms", "100"], stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.p = None
+        # wait (bounded) for the first sample so that the window is covered
+        t0 = time.time()
+        while self.p is not None and time.time() - t0 < 5.0 and os.path.getsize(self.f.name) == 0:
+            time.sleep(0.05)
 
-    def stop(self):
+    @staticmethod
+    def _stamp(text: str):
+        import datetime
+        try:
+            return datetime.datetime.strptime(text.strip(), "%Y/%m/%d %H:%M:%S.%f").timestamp()
+        except ValueError:
+            return None
+
+    def stop(self, t_begin: float, t_end: float):
         if self.p is None:
             return None
         self.p.terminate()
@@ -73,24 +90,26 @@ class ClockSampler:
             self.p.kill()
         self.f.flush()
         self.f.seek(0)
-        sm, mx, reasons = [], None, set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        rows = []
         for line in self.f.read().splitlines():
             parts = [x.strip() for x in line.split(",")]
             if len(parts) < 9:
                 continue
             try:
-                sm.append(float(parts[1]))
-                mx = float(parts[2])
+                rows.append((self._stamp(parts[0]), float(parts[1]), float(parts[2]),
+                             {nm for nm, v in zip(self.NAMES, parts[5:9]) if v.lower().startswith("active")}))
             except ValueError:
                 continue
-            for nm, v in zip(names, parts[5:9]):
-                if v.lower().startswith("active"):
-                    reasons.add(nm)
         os.unlink(self.f.name)
-        if not sm:
+        inside = [r for r in rows if r[0] is not None and t_begin <= r[0] <= t_end]
+        window = "timed region"
+        if len(inside) < 3:
+            inside, window = rows, "warm-up + timed region + kernel-timing pass (timed region < 3 samples)"
+        if not inside:
             return None
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+        reasons = set().union(*[r[3] for r in inside])
+        return {"sm_mhz": statistics.median([r[1] for r in inside]), "sm_max_mhz": inside[-1][2],
+                "reasons": sorted(reasons), "samples": len(inside), "window": window}
 
 
 def equilibrate(B, S, s, p, steps: int = 3000, gamma: float = 20.0):
@@ -180,19 +199,20 @@ def run_gpu(args):
 
     # launch shapes picked by the project's autotuner on this batch (untimed)
     tuned = B.sim_autotune(batch.h, 5, None)
+    clocks = ClockSampler(local) if rank == 0 else None
     # warm-up (also captures the CUDA graph)
     for _ in range(args.warmup):
         batch.step(nst)
     barrier()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    clocks = ClockSampler(local) if rank == 0 else None
+    t_begin = time.time()
     ev0.record(stream)
     for _ in range(args.steps):
         batch.step(nst)
     ev1.record(stream)
     barrier()
+    t_end = time.time()
     ms = ev0.elapsed_time(ev1)
-    clk = clocks.stop() if clocks else None
     if world > 1:
         t = torch.tensor([ms], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -208,6 +228,7 @@ def run_gpu(args):
         batch.step(nst)
     kt = B.sim_kernel_times(batch.h)
     B.sim_set_timing(batch.h, False)
+    clk = clocks.stop(t_begin, t_end) if clocks else None
 
     # end to end through the C ABI with host buffers: per step the state of
     # every trial is uploaded from pinned memory, nstlist steps are taken and

@@ -192,9 +192,11 @@ int phi_adjoint_coefficients(sim_handle *h, const double *z, const double *Q, in
 int sim_pairlist(sim_handle *h, int32_t trial, int32_t *pairs, int64_t cap, int64_t *n_pairs);
 int sim_diagnostics(sim_handle *h, int64_t *out);
 
-/* Autotuner: times the launch-shape variants of the pair kernel (register
- * caps of 4, 5 or 6 blocks per SM) and of the reaction-coordinate kernel (2,
- * 4 or 8 warps per block) on this batch, reps launches each, into scratch
+/* Autotuner: times the launch-shape variants of the pair kernel (0-2: the
+ * i-atoms in registers with register caps of 4, 5 or 6 blocks per SM; 3-5:
+ * the i-atoms in shared memory with caps of 6, 7 or 8 blocks per SM, for at
+ * most 16 LJ types, else as variant 0) and of the reaction-coordinate kernel
+ * (2, 4 or 8 warps per block) on this batch, reps launches each, into scratch
  * accumulators (the state is untouched), and uses the fastest from then on.
  * cache_path (may be NULL): a text file of "size-class variant variant" lines
  * consulted first and appended to.  choice[2] (may be NULL) receives the

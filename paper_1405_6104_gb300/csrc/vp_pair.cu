@@ -249,12 +249,17 @@ __global__ void __launch_bounds__(128, MINB) k_pair(Dev d, SimConst c, int only_
 // per-pair bit test.  Arithmetic per pair: 3 FADD, 6 FMUL, 12 FFMA, 1 RSQ,
 // 1 LDS, 1 FSETP + FSEL.
 constexpr int PF_WARPS = 4;
+constexpr int SMALL_TYPES = 16;
 constexpr float MASK_PEN = 1.0e30f;
 
-template <int MINB>
+// SHI: the i-atoms are read from shared memory (one broadcast LDS.128 per
+// pair) instead of being held in 32 registers, which lets more warps reside.
+// TS is the row stride of the per-warp LJ table (at least the number of types).
+template <int MINB, bool SHI, int TS>
 __global__ void __launch_bounds__(PF_WARPS * 32, MINB) k_pair_f(Dev d, SimConst c) {
-  __shared__ float2 s_cij[PF_WARPS][CL][MAX_TYPES];
+  __shared__ float2 s_cij[PF_WARPS][CL][TS];
   __shared__ float4 s_sh[PF_WARPS][64];
+  __shared__ float4 s_i[PF_WARPS][CL];
   __shared__ float s_red[PF_WARPS][3 * CL * 33];
   const int wib = threadIdx.x >> 5;
   const int I = blockIdx.x * PF_WARPS + wib;
@@ -275,6 +280,7 @@ __global__ void __launch_bounds__(PF_WARPS * 32, MINB) k_pair_f(Dev d, SimConst 
     xi[a] = p.x; yi[a] = p.y; zi[a] = p.z; qi[a] = p.w;
     ti[a] = d.type[I * CL + a];
   }
+  if (SHI && lane < CL) s_i[wib][lane] = d.pos[I * CL + lane];
   // per-warp tables: LJ rows of the i-atoms, image shifts (code = (nx+1) | (ny+1)<<2 | (nz+1)<<4)
   for (int k = lane; k < CL * NT; k += 32) {
     const int a = k / NT, tj = k - a * NT;
@@ -314,14 +320,15 @@ __global__ void __launch_bounds__(PF_WARPS * 32, MINB) k_pair_f(Dev d, SimConst 
     if (!__any_sync(0xffffffffu, exact)) {
 #pragma unroll
       for (int a = 0; a < CL; ++a) {
+        const float4 ia = SHI ? s_i[wib][a] : make_float4(xi[a], yi[a], zi[a], qi[a]);
         const float pen = (mb & (1u << (4 * a))) ? 0.0f : MASK_PEN;
-        const float dx = __fsub_rn(xj, xi[a]), dy = __fsub_rn(yj, yi[a]), dz = __fsub_rn(zj, zi[a]);
+        const float dx = __fsub_rn(xj, ia.x), dy = __fsub_rn(yj, ia.y), dz = __fsub_rn(zj, ia.z);
         const float r2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmaf_rn(dx, dx, pen)));
         const float rinv = rsqrtf(r2);
         const float rinv2 = __fmul_rn(rinv, rinv);
         const float rinv6 = __fmul_rn(__fmul_rn(rinv2, rinv2), rinv2);
-        const float2 cc = row[a * MAX_TYPES];
-        const float qq = __fmul_rn(qi[a], qj);
+        const float2 cc = row[a * TS];
+        const float qq = __fmul_rn(ia.w, qj);
         float tt = __fmaf_rn(cc.y, rinv6, -cc.x);
         tt = __fmul_rn(tt, rinv6);
         tt = __fmaf_rn(qq, rinv, tt);
@@ -339,8 +346,9 @@ __global__ void __launch_bounds__(PF_WARPS * 32, MINB) k_pair_f(Dev d, SimConst 
       // some entry of this group needs pair-by-pair minimum images
 #pragma unroll
       for (int a = 0; a < CL; ++a) {
+        const float4 ia = SHI ? s_i[wib][a] : make_float4(xi[a], yi[a], zi[a], qi[a]);
         const float pen = (mb & (1u << (4 * a))) ? 0.0f : MASK_PEN;
-        float dx = __fsub_rn(xj, xi[a]), dy = __fsub_rn(yj, yi[a]), dz = __fsub_rn(zj, zi[a]);
+        float dx = __fsub_rn(xj, ia.x), dy = __fsub_rn(yj, ia.y), dz = __fsub_rn(zj, ia.z);
         if (exact) {
           dx = __fmaf_rn(-L, rintf(__fmul_rn(dx, iL)), dx);
           dy = __fmaf_rn(-L, rintf(__fmul_rn(dy, iL)), dy);
@@ -350,8 +358,8 @@ __global__ void __launch_bounds__(PF_WARPS * 32, MINB) k_pair_f(Dev d, SimConst 
         const float rinv = rsqrtf(r2);
         const float rinv2 = __fmul_rn(rinv, rinv);
         const float rinv6 = __fmul_rn(__fmul_rn(rinv2, rinv2), rinv2);
-        const float2 cc = row[a * MAX_TYPES];
-        const float qq = __fmul_rn(qi[a], qj);
+        const float2 cc = row[a * TS];
+        const float qq = __fmul_rn(ia.w, qj);
         float tt = __fmaf_rn(cc.y, rinv6, -cc.x);
         tt = __fmul_rn(tt, rinv6);
         tt = __fmaf_rn(qq, rinv, tt);
@@ -385,6 +393,7 @@ __global__ void __launch_bounds__(PF_WARPS * 32, MINB) k_pair_f(Dev d, SimConst 
 #pragma unroll
       for (int a = 0; a < CL; ++a)
         if (a == lane) self = make_float4(xi[a], yi[a], zi[a], 0.f);
+      if (SHI) self = make_float4(s_i[wib][lane].x, s_i[wib][lane].y, s_i[wib][lane].z, 0.f);
       float eb = 0.f, ea = 0.f;
       const float3 fb = bonded_force(d, T, o, self, eb, ea);
 #pragma unroll
@@ -408,8 +417,11 @@ __global__ void __launch_bounds__(PF_WARPS * 32, MINB) k_pair_f(Dev d, SimConst 
   }
 }
 
-// variants differ in the register cap (blocks per SM the compiler must fit):
-// 0: 4 blocks, 1: 5 blocks, 2: 6 blocks
+// variants differ in the register cap (blocks per SM the compiler must fit)
+// and in where the i-atoms live: 0/1/2: registers, 4/5/6 blocks; 3/4/5:
+// shared memory and an LJ table for at most SMALL_TYPES types (less shared
+// memory per block), 6/7/8 blocks (larger type sets fall back to variant 0).
+// All variants do the same arithmetic in the same order (bit-identical forces).
 void launch_pair(const Dev &d, const SimConst &c, bool energy, int32_t only_trial, cudaStream_t s, int variant) {
   long long threads = (long long)d.total_clus * 32;
   unsigned blocks = (unsigned)((threads + 127) / 128);
@@ -419,9 +431,15 @@ void launch_pair(const Dev &d, const SimConst &c, bool energy, int32_t only_tria
     return;
   }
   const unsigned fb = (unsigned)((d.total_clus + PF_WARPS - 1) / PF_WARPS);
-  if (variant == 1) k_pair_f<5><<<fb, PF_WARPS * 32, 0, s>>>(d, c);
-  else if (variant == 2) k_pair_f<6><<<fb, PF_WARPS * 32, 0, s>>>(d, c);
-  else k_pair_f<4><<<fb, PF_WARPS * 32, 0, s>>>(d, c);
+  if (variant >= 3 && c.n_types > SMALL_TYPES) variant = 0;
+  switch (variant) {
+    case 1: k_pair_f<5, false, MAX_TYPES><<<fb, PF_WARPS * 32, 0, s>>>(d, c); break;
+    case 2: k_pair_f<6, false, MAX_TYPES><<<fb, PF_WARPS * 32, 0, s>>>(d, c); break;
+    case 3: k_pair_f<6, true, SMALL_TYPES><<<fb, PF_WARPS * 32, 0, s>>>(d, c); break;
+    case 4: k_pair_f<7, true, SMALL_TYPES><<<fb, PF_WARPS * 32, 0, s>>>(d, c); break;
+    case 5: k_pair_f<8, true, SMALL_TYPES><<<fb, PF_WARPS * 32, 0, s>>>(d, c); break;
+    default: k_pair_f<4, false, MAX_TYPES><<<fb, PF_WARPS * 32, 0, s>>>(d, c); break;
+  }
 }
 
 }  // namespace vp

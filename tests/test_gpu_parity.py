@@ -265,7 +265,7 @@ def test_autotuner_variants_are_bit_identical(tmp_path):
     """Every launch shape the autotuner can pick computes the same result."""
     s, p = S.small_solvated()
     results = []
-    for pv in range(3):
+    for pv in range(6):  # every pair-kernel variant
         for cv in (0, 2):
             cache = tmp_path / f"tune_{pv}_{cv}.txt"
             with B.TrialBatch(s, p, [2], trial_seeds=[4, 5]) as b:
