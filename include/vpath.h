@@ -194,8 +194,10 @@ int sim_diagnostics(sim_handle *h, int64_t *out);
 
 /* Autotuner: times the launch-shape variants of the pair kernel (0-2: the
  * i-atoms in registers with register caps of 4, 5 or 6 blocks per SM; 3-5:
- * the i-atoms in shared memory with caps of 6, 7 or 8 blocks per SM, for at
- * most 16 LJ types, else as variant 0) and of the reaction-coordinate kernel
+ * the i-atoms in shared memory with caps of 6, 7 or 8 blocks per SM; 6-8:
+ * packed FP32x2 arithmetic, i-atoms in shared memory, caps of 5, 6 or 7;
+ * 3-8 need at most 16 LJ types, else run as variant 0; all give bit-identical
+ * forces) and of the reaction-coordinate kernel
  * (2, 4 or 8 warps per block) on this batch, reps launches each, into scratch
  * accumulators (the state is untouched), and uses the fastest from then on.
  * cache_path (may be NULL): a text file of "size-class variant variant" lines
@@ -203,11 +205,16 @@ int sim_diagnostics(sim_handle *h, int64_t *out);
  * picked variants. */
 int sim_autotune(sim_handle *h, int32_t reps, const char *cache_path, int32_t *choice);
 
-/* Kernel timing: with on != 0 the next sim_step_batch calls launch kernels
+/* Kernel timing.  on = 1: the next sim_step_batch calls launch kernels
  * directly and time each launch with CUDA events on the library stream.
- * sim_kernel_times fills up to cap entries of names (static strings), total
- * milliseconds and launch counts, returns the number of kernels, and resets
- * the accumulators. */
+ * on = 2: the steps still run as CUDA-graph replays, and the chunk graph is
+ * captured with external event-record nodes around each pair-kernel launch;
+ * their durations are read after every replay (a call of several chunks
+ * synchronises between them) and reported as "pair_in_graph".  on = 0: off
+ * (the graph is captured again without the event nodes).  SIM_EINVAL for
+ * other values.  sim_kernel_times fills up to cap entries of names (static
+ * strings), total milliseconds and launch counts, returns the number of
+ * kernels, and resets the accumulators. */
 int sim_set_timing(sim_handle *h, int32_t on);
 int sim_kernel_times(sim_handle *h, const char **names, double *ms, int64_t *counts, int32_t cap);
 

@@ -292,8 +292,9 @@ def sim_autotune(h, reps: int = 5, cache_path: Optional[str] = None):
     return int(ch[0]), int(ch[1])
 
 
-def sim_set_timing(h, on: bool):
-    _check(h, load().sim_set_timing(h, int(bool(on))))
+def sim_set_timing(h, on):
+    """0: off, 1 (or True): direct launches timed per kernel, 2: in-graph timing of the pair kernel."""
+    _check(h, load().sim_set_timing(h, int(on)))
 
 
 def sim_kernel_times(h):

@@ -44,6 +44,11 @@ struct sim_handle {
   bool use_graph = true;
   cudaGraphExec_t chunk = nullptr;
   bool timing = false;
+  // in-graph timing: external event-record nodes around each pair-kernel
+  // launch of the captured chunk, read after every graph replay
+  bool gtiming = false;
+  int cap_k = -1;  // step index inside the chunk being captured (-1: not capturing)
+  std::vector<cudaEvent_t> gev;
   std::vector<Timer> timers;
   std::map<std::string, int> timer_idx;
   std::vector<void *> allocs;
@@ -141,6 +146,27 @@ void harvest_timers(sim_handle *h) {
   }
 }
 
+Timer &timer(sim_handle *h, const char *name) {
+  auto it = h->timer_idx.find(name);
+  if (it != h->timer_idx.end()) return h->timers[it->second];
+  h->timer_idx[name] = (int)h->timers.size();
+  h->timers.push_back(Timer{name, {}, 0.0, 0});
+  return h->timers.back();
+}
+
+// durations of the pair-kernel launches of the last chunk replay
+int harvest_graph_timers(sim_handle *h) {
+  Timer &t = timer(h, "pair_in_graph");
+  for (int k = 0; k + 1 < (int)h->gev.size(); k += 2) {
+    float ms = 0.f;
+    cudaError_t e = cudaEventElapsedTime(&ms, h->gev[k], h->gev[k + 1]);
+    if (e != cudaSuccess) return fail(h, SIM_ECUDA, std::string("in-graph timing: ") + cudaGetErrorString(e));
+    t.ms += ms;
+    t.count += 1;
+  }
+  return SIM_OK;
+}
+
 void rebuild(sim_handle *h) {
   cudaStream_t s = h->stream;
   timed(h, "bin", [&] { launch_bin(h->d, h->c, h->half_skin2, h->strict_skin, s); });
@@ -152,7 +178,13 @@ void rebuild(sim_handle *h) {
 
 void forces(sim_handle *h, FinMode mode) {
   cudaStream_t s = h->stream;
-  timed(h, "pair", [&] { launch_pair(h->d, h->c, false, -1, s, h->pair_variant); });
+  if (h->gtiming && h->cap_k >= 0) {
+    cudaEventRecordWithFlags(h->gev[2 * h->cap_k], s, cudaEventRecordExternal);  // a failure ends the capture
+    launch_pair(h->d, h->c, false, -1, s, h->pair_variant);
+    cudaEventRecordWithFlags(h->gev[2 * h->cap_k + 1], s, cudaEventRecordExternal);
+  } else {
+    timed(h, "pair", [&] { launch_pair(h->d, h->c, false, -1, s, h->pair_variant); });
+  }
   timed(h, "cv", [&] { launch_cv(h->d, h->c, s, h->cv_variant); });
   timed(h, "cvfin", [&] { launch_cvfin(h->d, h->c, mode, s); });
   if (h->frames)
@@ -199,8 +231,20 @@ int ensure_dbuf(sim_handle *h, size_t n) {
 int capture_chunk(sim_handle *h) {
   if (h->chunk) return SIM_OK;
   cudaGraph_t g;
+  if (h->gtiming && h->gev.empty()) {
+    h->gev.resize(2 * (size_t)h->params.nstlist);
+    for (auto &e : h->gev) CK(cudaEventCreate(&e));
+  }
+  // the chunk is steps n = m nst + 1 .. (m + 1) nst: nst - 1 plain steps and
+  // the step that rebuilds the lists, so that calls of nst steps from a
+  // list step replay it
+  const int nst = h->params.nstlist;
   CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
-  for (int k = 0; k < h->params.nstlist; ++k) one_step(h, k == 0);
+  for (int k = 0; k < nst; ++k) {
+    h->cap_k = k;
+    one_step(h, k == nst - 1);
+  }
+  h->cap_k = -1;
   CK(cudaStreamEndCapture(h->stream, &g));
   cudaError_t e = cudaGraphInstantiate(&h->chunk, g, 0);
   cudaGraphDestroy(g);
@@ -630,17 +674,23 @@ VP_API int sim_step_batch(sim_handle *h, int32_t n_steps) {
   CK(cudaMemsetAsync(h->d.err, 0, sizeof(int), h->stream));
   const int nst = h->params.nstlist;
   int left = n_steps;
+  bool pending = false;  // a replay whose in-graph timing events are not read yet
   while (left > 0) {
-    const long long next = h->step + 1;
-    const bool aligned = (next % nst) == 0;
-    if (h->use_graph && !h->timing && aligned && left >= nst) {
+    if (h->use_graph && !h->timing && h->step % nst == 0 && left >= nst) {
       r = capture_chunk(h);
       if (r) return r;
+      if (pending) {  // read the previous replay's events before this one records them again
+        CK(cudaStreamSynchronize(h->stream));
+        r = harvest_graph_timers(h);
+        if (r) return r;
+      }
       CK(cudaGraphLaunch(h->chunk, h->stream));
       h->step += nst;
       left -= nst;
+      pending = h->gtiming;
     } else {
-      one_step(h, aligned);
+      const long long next = h->step + 1;
+      one_step(h, next % nst == 0);
       h->step += 1;
       left -= 1;
     }
@@ -649,6 +699,10 @@ VP_API int sim_step_batch(sim_handle *h, int32_t n_steps) {
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(h->stream));
   if (h->timing) harvest_timers(h);
+  if (pending) {
+    r = harvest_graph_timers(h);
+    if (r) return r;
+  }
   return check_flags(h);
 }
 
@@ -1056,7 +1110,14 @@ VP_API int sim_diagnostics(sim_handle *h, int64_t *out) {
 
 VP_API int sim_set_timing(sim_handle *h, int32_t on) {
   if (!h) return SIM_EINVAL;
-  h->timing = on != 0;
+  if (on < 0 || on > 2) return fail(h, SIM_EINVAL, "timing mode must be 0, 1 or 2");
+  h->timing = on == 1;
+  const bool g = on == 2;
+  if (g != h->gtiming && h->chunk) {  // the chunk graph is captured again with or without the event nodes
+    cudaGraphExecDestroy(h->chunk);
+    h->chunk = nullptr;
+  }
+  h->gtiming = g;
   return SIM_OK;
 }
 
@@ -1100,6 +1161,7 @@ VP_API void sim_destroy(sim_handle *h) {
   cudaSetDevice(h->device);
   if (h->stream) cudaStreamSynchronize(h->stream);
   if (h->chunk) cudaGraphExecDestroy(h->chunk);
+  for (auto &e : h->gev) cudaEventDestroy(e);
   for (void *p : h->allocs) cudaFree(p);
   if (h->d.rec) cudaFree(h->d.rec);
   if (h->frames) cudaFree(h->frames);

@@ -65,7 +65,7 @@ void launch_colsort(const Dev &d, cudaStream_t s);
 void launch_list(const Dev &d, const SimConst &c, float rl2_bbox, cudaStream_t s);
 // forces (vp_pair.cu)
 void launch_pair(const Dev &d, const SimConst &c, bool energy, int32_t only_trial, cudaStream_t s, int variant = 0);
-constexpr int PAIR_VARIANTS = 6;
+constexpr int PAIR_VARIANTS = 9;
 // reaction coordinate and functional (vp_cv.cu)
 void launch_cnat(const Dev &d, const SimConst &c, const double *native, const int32_t *sys_nat0, int32_t n_tiles_total,
                  const int32_t *tile_sys, cudaStream_t s);

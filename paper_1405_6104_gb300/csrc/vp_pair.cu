@@ -316,7 +316,8 @@ __global__ void __launch_bounds__(PF_WARPS * 32, MINB) k_pair_f(Dev d, SimConst 
     const unsigned mb = ent.y >> b;
     const bool exact = (ent.x & E_EXACT) != 0u;
     const float2 *row = &s_cij[wib][0][tj];
-    float fjx = 0.f, fjy = 0.f, fjz = 0.f;
+    // j-force: even and odd i-atoms in two partial sums (the packed variant's order)
+    float fjx[2] = {0.f, 0.f}, fjy[2] = {0.f, 0.f}, fjz[2] = {0.f, 0.f};
     if (!__any_sync(0xffffffffu, exact)) {
 #pragma unroll
       for (int a = 0; a < CL; ++a) {
@@ -338,9 +339,9 @@ __global__ void __launch_bounds__(PF_WARPS * 32, MINB) k_pair_f(Dev d, SimConst 
         fi[a][0] = __fmaf_rn(-f, dx, fi[a][0]);
         fi[a][1] = __fmaf_rn(-f, dy, fi[a][1]);
         fi[a][2] = __fmaf_rn(-f, dz, fi[a][2]);
-        fjx = __fmaf_rn(f, dx, fjx);
-        fjy = __fmaf_rn(f, dy, fjy);
-        fjz = __fmaf_rn(f, dz, fjz);
+        fjx[a & 1] = __fmaf_rn(f, dx, fjx[a & 1]);
+        fjy[a & 1] = __fmaf_rn(f, dy, fjy[a & 1]);
+        fjz[a & 1] = __fmaf_rn(f, dz, fjz[a & 1]);
       }
     } else {
       // some entry of this group needs pair-by-pair minimum images
@@ -369,15 +370,16 @@ __global__ void __launch_bounds__(PF_WARPS * 32, MINB) k_pair_f(Dev d, SimConst 
         fi[a][0] = __fmaf_rn(-f, dx, fi[a][0]);
         fi[a][1] = __fmaf_rn(-f, dy, fi[a][1]);
         fi[a][2] = __fmaf_rn(-f, dz, fi[a][2]);
-        fjx = __fmaf_rn(f, dx, fjx);
-        fjy = __fmaf_rn(f, dy, fjy);
-        fjz = __fmaf_rn(f, dz, fjz);
+        fjx[a & 1] = __fmaf_rn(f, dx, fjx[a & 1]);
+        fjy[a & 1] = __fmaf_rn(f, dy, fjy[a & 1]);
+        fjz[a & 1] = __fmaf_rn(f, dz, fjz[a & 1]);
       }
     }
-    if (fjx != 0.f || fjy != 0.f || fjz != 0.f) {
-      red_add(d.fx + sj, fx_from(fjx));
-      red_add(d.fy + sj, fx_from(fjy));
-      red_add(d.fz + sj, fx_from(fjz));
+    const float sx = fjx[0] + fjx[1], sy = fjy[0] + fjy[1], sz = fjz[0] + fjz[1];
+    if (sx != 0.f || sy != 0.f || sz != 0.f) {
+      red_add(d.fx + sj, fx_from(sx));
+      red_add(d.fy + sj, fx_from(sy));
+      red_add(d.fz + sj, fx_from(sz));
     }
     ent = ent_n;
     ent_n = ent_nn;
@@ -417,6 +419,194 @@ __global__ void __launch_bounds__(PF_WARPS * 32, MINB) k_pair_f(Dev d, SimConst 
   }
 }
 
+// Packed variant: the same pair loop on FP32x2 arithmetic (FADD2, FMUL2,
+// FFMA2: one instruction for two pairs) over the i-atom pairs (2p, 2p+1).
+// The i-atoms sit in shared memory as {x, x', y, y'} {z, z', q, q'} and the
+// LJ row of an i-atom pair is {c12, c12', -c6, -c6'}; per two pairs the loop
+// issues 3 FADD2, 5 FMUL2, 8 FFMA2, 2 RSQ, 3 LDS.128, 2 FSETP + FSEL and the
+// two mask tests.  The i-force partials accumulate +f*d and are negated once
+// (exactly the sum of -f*d: round-to-nearest is sign-symmetric); the j-force
+// sums even and odd i-atoms in two partials, as the scalar variants do, so
+// all variants give bit-identical forces.
+template <int MINB>
+__global__ void __launch_bounds__(PF_WARPS * 32, MINB) k_pair_f2(Dev d, SimConst c) {
+  constexpr int TS = SMALL_TYPES;
+  __shared__ float4 s_c4[PF_WARPS][CL / 2][TS];
+  __shared__ float4 s_sh[PF_WARPS][64];
+  __shared__ float4 s_ip[PF_WARPS][CL / 2][2];
+  __shared__ float s_red[PF_WARPS][3 * CL * 33];
+  const int wib = threadIdx.x >> 5;
+  const int I = blockIdx.x * PF_WARPS + wib;
+  const int lane = threadIdx.x & 31;
+  if (I >= d.total_clus) return;
+  const int t = d.clus_trial[I];
+  const TrialInfo T = d.tinfo[t];
+  if (I - T.clus0 >= d.tstate[t].n_clus) return;
+  const float L = T.box, iL = T.inv_box;
+  const int g = lane >> 2, b = lane & 3;
+  const int NT = c.n_types;
+
+  if (lane < CL / 2) {
+    const float4 a0 = d.pos[I * CL + 2 * lane], a1 = d.pos[I * CL + 2 * lane + 1];
+    s_ip[wib][lane][0] = make_float4(a0.x, a1.x, a0.y, a1.y);
+    s_ip[wib][lane][1] = make_float4(a0.z, a1.z, a0.w, a1.w);
+  }
+  for (int k = lane; k < (CL / 2) * NT; k += 32) {
+    const int p = k / NT, tj = k - p * NT;
+    const int t0 = d.type[I * CL + 2 * p], t1 = d.type[I * CL + 2 * p + 1];
+    const float2 c0 = d.ljtab[t0 * NT + tj], c1 = d.ljtab[t1 * NT + tj];
+    s_c4[wib][p][tj] = make_float4(c0.y, c1.y, -c0.x, -c1.x);
+  }
+  for (int k = lane; k < 64; k += 32) {
+    const int ix = (k & 3) - 1, iy = ((k >> 2) & 3) - 1, iz = ((k >> 4) & 3) - 1;
+    s_sh[wib][k] = make_float4(L * ix, L * iy, L * iz, 0.f);
+  }
+  __syncwarp();
+  float2 fx[CL / 2], fy[CL / 2], fz[CL / 2];
+#pragma unroll
+  for (int p = 0; p < CL / 2; ++p) fx[p] = fy[p] = fz[p] = make_float2(0.f, 0.f);
+  const float2 m2krf = make_float2(-c.two_krf, -c.two_krf);
+  const float rc2 = c.rc2;
+
+  const int n = d.list_n[I];
+  const uint2 *seg = d.list + (size_t)I * c.list_cap;
+  uint2 ent = g < n ? seg[g] : make_uint2(0u, 0u);
+  uint2 ent_n = 8 + g < n ? seg[8 + g] : make_uint2(0u, 0u);
+  float4 pj = d.pos[(int)(ent.x & J_MASK) * CJ + b];
+  int tj = d.type[(int)(ent.x & J_MASK) * CJ + b];
+  for (int e0 = 0; e0 < n; e0 += 8) {
+    const uint2 ent_nn = e0 + 16 + g < n ? seg[e0 + 16 + g] : make_uint2(0u, 0u);
+    const int sj_n = (int)(ent_n.x & J_MASK) * CJ + b;
+    const float4 pj_n = d.pos[sj_n];
+    const int tj_n = d.type[sj_n];
+    const int sj = (int)(ent.x & J_MASK) * CJ + b;
+    const float4 shv = s_sh[wib][(ent.x >> J_BITS) & 63u];
+    const float xj = pj.x - shv.x, yj = pj.y - shv.y, zj = pj.z - shv.z, qj = pj.w;
+    const unsigned mb = ent.y >> b;
+    const bool exact = (ent.x & E_EXACT) != 0u;
+    const float4 *row = &s_c4[wib][0][tj];
+    float fjx, fjy, fjz;
+    if (!__any_sync(0xffffffffu, exact)) {
+      const float2 xj2 = make_float2(xj, xj), yj2 = make_float2(yj, yj), zj2 = make_float2(zj, zj);
+      const float2 qj2 = make_float2(qj, qj);
+      float2 gx = make_float2(0.f, 0.f), gy = gx, gz = gx;
+#pragma unroll
+      for (int p = 0; p < CL / 2; ++p) {
+        const float4 i0 = s_ip[wib][p][0], i1 = s_ip[wib][p][1];
+        const float2 pen = make_float2((mb & (1u << (8 * p))) ? 0.0f : MASK_PEN,
+                                       (mb & (1u << (8 * p + 4))) ? 0.0f : MASK_PEN);
+        const float2 dx = __fadd2_rn(xj2, make_float2(-i0.x, -i0.y));
+        const float2 dy = __fadd2_rn(yj2, make_float2(-i0.z, -i0.w));
+        const float2 dz = __fadd2_rn(zj2, make_float2(-i1.x, -i1.y));
+        const float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __ffma2_rn(dx, dx, pen)));
+        const float2 rinv = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
+        const float2 rinv2 = __fmul2_rn(rinv, rinv);
+        const float2 rinv6 = __fmul2_rn(__fmul2_rn(rinv2, rinv2), rinv2);
+        const float4 cc = row[p * TS];
+        const float2 qq = __fmul2_rn(make_float2(i1.z, i1.w), qj2);
+        float2 tt = __ffma2_rn(make_float2(cc.x, cc.y), rinv6, make_float2(cc.z, cc.w));
+        tt = __fmul2_rn(tt, rinv6);
+        tt = __ffma2_rn(qq, rinv, tt);
+        tt = __fmul2_rn(tt, rinv2);
+        float2 f = __ffma2_rn(qq, m2krf, tt);
+        f.x = r2.x < rc2 ? f.x : 0.0f;
+        f.y = r2.y < rc2 ? f.y : 0.0f;
+        fx[p] = __ffma2_rn(f, dx, fx[p]);
+        fy[p] = __ffma2_rn(f, dy, fy[p]);
+        fz[p] = __ffma2_rn(f, dz, fz[p]);
+        gx = __ffma2_rn(f, dx, gx);
+        gy = __ffma2_rn(f, dy, gy);
+        gz = __ffma2_rn(f, dz, gz);
+      }
+      fjx = gx.x + gx.y;
+      fjy = gy.x + gy.y;
+      fjz = gz.x + gz.y;
+    } else {
+      // some entry of this group needs pair-by-pair minimum images
+      float2 gx = make_float2(0.f, 0.f), gy = gx, gz = gx;
+#pragma unroll
+      for (int p = 0; p < CL / 2; ++p) {
+        const float4 i0 = s_ip[wib][p][0], i1 = s_ip[wib][p][1];
+        const float4 cc = row[p * TS];
+        float2 f2v, dx2, dy2, dz2;
+#pragma unroll
+        for (int hh = 0; hh < 2; ++hh) {
+          const float pen = (mb & (1u << (8 * p + 4 * hh))) ? 0.0f : MASK_PEN;
+          float dx = __fsub_rn(xj, hh ? i0.y : i0.x), dy = __fsub_rn(yj, hh ? i0.w : i0.z),
+                dz = __fsub_rn(zj, hh ? i1.y : i1.x);
+          if (exact) {
+            dx = __fmaf_rn(-L, rintf(__fmul_rn(dx, iL)), dx);
+            dy = __fmaf_rn(-L, rintf(__fmul_rn(dy, iL)), dy);
+            dz = __fmaf_rn(-L, rintf(__fmul_rn(dz, iL)), dz);
+          }
+          const float r2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmaf_rn(dx, dx, pen)));
+          const float rinv = rsqrtf(r2);
+          const float rinv2 = __fmul_rn(rinv, rinv);
+          const float rinv6 = __fmul_rn(__fmul_rn(rinv2, rinv2), rinv2);
+          const float qq = __fmul_rn(hh ? i1.w : i1.z, qj);
+          float tt = __fmaf_rn(hh ? cc.y : cc.x, rinv6, hh ? cc.w : cc.z);
+          tt = __fmul_rn(tt, rinv6);
+          tt = __fmaf_rn(qq, rinv, tt);
+          tt = __fmul_rn(tt, rinv2);
+          float f = __fmaf_rn(qq, -c.two_krf, tt);
+          f = r2 < rc2 ? f : 0.0f;
+          if (hh) { f2v.y = f; dx2.y = dx; dy2.y = dy; dz2.y = dz; }
+          else { f2v.x = f; dx2.x = dx; dy2.x = dy; dz2.x = dz; }
+        }
+        fx[p] = __ffma2_rn(f2v, dx2, fx[p]);
+        fy[p] = __ffma2_rn(f2v, dy2, fy[p]);
+        fz[p] = __ffma2_rn(f2v, dz2, fz[p]);
+        gx = __ffma2_rn(f2v, dx2, gx);
+        gy = __ffma2_rn(f2v, dy2, gy);
+        gz = __ffma2_rn(f2v, dz2, gz);
+      }
+      fjx = gx.x + gx.y;
+      fjy = gy.x + gy.y;
+      fjz = gz.x + gz.y;
+    }
+    if (fjx != 0.f || fjy != 0.f || fjz != 0.f) {
+      red_add(d.fx + sj, fx_from(fjx));
+      red_add(d.fy + sj, fx_from(fjy));
+      red_add(d.fz + sj, fx_from(fjz));
+    }
+    ent = ent_n;
+    ent_n = ent_nn;
+    pj = pj_n;
+    tj = tj_n;
+  }
+
+  float fi[CL][3];
+#pragma unroll
+  for (int p = 0; p < CL / 2; ++p) {
+    fi[2 * p][0] = -fx[p].x; fi[2 * p][1] = -fy[p].x; fi[2 * p][2] = -fz[p].x;
+    fi[2 * p + 1][0] = -fx[p].y; fi[2 * p + 1][1] = -fy[p].y; fi[2 * p + 1][2] = -fz[p].y;
+  }
+  if (lane < CL) {
+    const int o = d.orig[I * CL + lane];
+    if (o >= 0) {
+      const float4 sp = d.pos[I * CL + lane];
+      float eb = 0.f, ea = 0.f;
+      const float3 fb = bonded_force(d, T, o, make_float4(sp.x, sp.y, sp.z, 0.f), eb, ea);
+#pragma unroll
+      for (int a = 0; a < CL; ++a)
+        if (a == lane) { fi[a][0] += fb.x; fi[a][1] += fb.y; fi[a][2] += fb.z; }
+    }
+  }
+  float *r = s_red[wib];
+#pragma unroll
+  for (int a = 0; a < CL; ++a)
+#pragma unroll
+    for (int k = 0; k < 3; ++k) r[(3 * a + k) * 33 + lane] = fi[a][k];
+  __syncwarp();
+  if (lane < 3 * CL) {
+    float sum = 0.f;
+    for (int l = 0; l < 32; ++l) sum += r[lane * 33 + l];
+    const int a = lane / 3, comp = lane - 3 * a;
+    const long long val = fx_from(sum);
+    if (val != 0) red_add((comp == 0 ? d.fx : comp == 1 ? d.fy : d.fz) + I * CL + a, val);
+  }
+}
+
 // variants differ in the register cap (blocks per SM the compiler must fit)
 // and in where the i-atoms live: 0/1/2: registers, 4/5/6 blocks; 3/4/5:
 // shared memory and an LJ table for at most SMALL_TYPES types (less shared
@@ -438,6 +628,9 @@ void launch_pair(const Dev &d, const SimConst &c, bool energy, int32_t only_tria
     case 3: k_pair_f<6, true, SMALL_TYPES><<<fb, PF_WARPS * 32, 0, s>>>(d, c); break;
     case 4: k_pair_f<7, true, SMALL_TYPES><<<fb, PF_WARPS * 32, 0, s>>>(d, c); break;
     case 5: k_pair_f<8, true, SMALL_TYPES><<<fb, PF_WARPS * 32, 0, s>>>(d, c); break;
+    case 6: k_pair_f2<5><<<fb, PF_WARPS * 32, 0, s>>>(d, c); break;
+    case 7: k_pair_f2<6><<<fb, PF_WARPS * 32, 0, s>>>(d, c); break;
+    case 8: k_pair_f2<7><<<fb, PF_WARPS * 32, 0, s>>>(d, c); break;
     default: k_pair_f<4, false, MAX_TYPES><<<fb, PF_WARPS * 32, 0, s>>>(d, c); break;
   }
 }

@@ -265,7 +265,7 @@ def test_autotuner_variants_are_bit_identical(tmp_path):
     """Every launch shape the autotuner can pick computes the same result."""
     s, p = S.small_solvated()
     results = []
-    for pv in range(6):  # every pair-kernel variant
+    for pv in range(9):  # every pair-kernel variant
         for cv in (0, 2):
             cache = tmp_path / f"tune_{pv}_{cv}.txt"
             with B.TrialBatch(s, p, [2], trial_seeds=[4, 5]) as b:
@@ -279,3 +279,25 @@ def test_autotuner_variants_are_bit_identical(tmp_path):
     for r in results[1:]:
         for x, y in zip(results[0], r):
             assert np.array_equal(x[0], y[0]) and np.array_equal(x[1], y[1]) and x[2][3] == y[2][3]
+
+
+def test_in_graph_pair_timing():
+    """Event-record nodes around the pair kernel inside the chunk graph time
+    every replayed launch and leave the trajectory bit-identical."""
+    s, p = S.small_solvated()
+    results = []
+    for mode in (0, 2):
+        with B.TrialBatch(s, p, [2], trial_seeds=[4, 5]) as b:
+            B.sim_set_timing(b.h, mode)
+            b.step(3 * p.nstlist)  # three chunk replays in one call
+            b.step(3)  # direct steps
+            b.step(p.nstlist - 3 + p.nstlist)  # direct steps to the list step, one replay
+            kt = B.sim_kernel_times(b.h)
+            if mode == 2:
+                ms, n = kt["pair_in_graph"]
+                assert n == 4 * p.nstlist and ms > 0.0
+            else:
+                assert "pair_in_graph" not in kt
+            results.append([b.get_state(t) for t in range(2)])
+    for x, y in zip(*results):
+        assert np.array_equal(x[0], y[0]) and np.array_equal(x[1], y[1])
