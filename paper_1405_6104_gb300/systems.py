@@ -157,19 +157,25 @@ def _rand_unit(rng):
 def _chain_walk(rng, n, bond, angle, centre, radius, min_dist, max_tries=200):
     """Self-avoiding chain with fixed bond length and bond angle, random
     dihedrals, kept inside a sphere of the given radius."""
-    pts = [np.asarray(centre, dtype=np.float64)]
+    pts = np.zeros((n, 3))
+    pts[0] = np.asarray(centre, dtype=np.float64)
     if n == 1:
-        return np.array(pts)
+        return pts
     d = _rand_unit(rng)
-    pts.append(pts[0] + bond * d)
+    pts[1] = pts[0] + bond * d
     for i in range(2, n):
         best, best_score = None, -np.inf
-        a, b = pts[-2], pts[-1]
+        a, b = pts[i - 2], pts[i - 1]
         u = (b - a) / np.linalg.norm(b - a)
         perp = np.cross(u, _rand_unit(rng))
         perp /= np.linalg.norm(perp)
         w = np.cross(u, perp)
-        prev = np.array(pts[:-2]) if len(pts) > 2 else np.zeros((0, 3))
+        # only points within bond + min_dist of b can come within min_dist of a
+        # candidate; the minimum over them equals the minimum over all points
+        # whenever it is below min_dist, the only case in which its value matters
+        prev = pts[:i - 2]
+        reach = (bond + min_dist) * (1.0 + 1e-9)
+        prev = prev[((prev - b) ** 2).sum(1) < reach * reach]
         for _ in range(max_tries):
             phi = rng.uniform(0, 2 * np.pi)
             dirn = -math.cos(angle) * u + math.sin(angle) * (math.cos(phi) * perp + math.sin(phi) * w)
@@ -182,8 +188,8 @@ def _chain_walk(rng, n, bond, angle, centre, radius, min_dist, max_tries=200):
                 break
             if score > best_score:
                 best, best_score = c, score
-        pts.append(best)
-    return np.array(pts)
+        pts[i] = best
+    return pts
 
 
 def _lattice_hamiltonian_path(rng, dims, spacing):
