@@ -16,26 +16,32 @@ __global__ void __launch_bounds__(256) k_update(Dev d, SimConst c) {
   const int slot = blockIdx.x * blockDim.x + threadIdx.x;
   if (slot >= d.total_slots) return;
   if (MODE == UPD_FINAL && slot == 0) *d.kick = 0.5f;
-  // every slot-indexed load is issued before any of them is needed; slots
-  // past a trial's clusters and padding slots carry orig = -1
-  const int o = d.orig[slot];
-  const int t = d.slot_trial[slot];
+  // every load that does not depend on another is issued before any store
+  // (the stores could alias them as far as the compiler knows), so a thread
+  // waits for two memory round trips (three for reaction-coordinate atoms);
+  // slots past a trial's clusters and padding slots carry orig = -1
+  const int o = __ldg(d.orig + slot);
+  const int t = __ldg(d.slot_trial + slot);
   float4 p = d.pos[slot], v = d.vel[slot];
   const long long fxi = d.fx[slot], fyi = d.fy[slot], fzi = d.fz[slot];
+  const float kick = MODE == UPD_DRIFT ? *d.kick : 0.5f;
+  const unsigned long long step = MODE == UPD_DRIFT ? (unsigned long long)(*d.step) + 1ull : 0ull;
   if (o < 0) return;
-  const TrialInfo &T = d.tinfo[t];
+  const int n_cv = __ldg(&d.tinfo[t].n_cv), cv0 = __ldg(&d.tinfo[t].cv0);
+  const uint32_t key0 = __ldg(&d.tinfo[t].key0), key1 = __ldg(&d.tinfo[t].key1);
   float Fx = fx_to(fxi), Fy = fx_to(fyi), Fz = fx_to(fzi);
-  if (MODE == UPD_DRIFT) { d.fx[slot] = 0; d.fy[slot] = 0; d.fz[slot] = 0; }
-  if (o < T.n_cv) {
+  if (o < n_cv) {
     // ratchet force F_i = -(k_R/2) a grad_i z (Eq. VR); a = 0 when z <= z_m
-    const float s = -c.kR_half * (float)d.tstate[t].a;
-    const int gi = T.cv0 + o;
-    Fx += s * fx_to(d.gx[gi]);
-    Fy += s * fx_to(d.gy[gi]);
-    Fz += s * fx_to(d.gz[gi]);
+    const double a = d.tstate[t].a;
+    const int gi = cv0 + o;
+    const long long gx = d.gx[gi], gy = d.gy[gi], gz = d.gz[gi];
+    const float s = -c.kR_half * (float)a;
+    Fx += s * fx_to(gx);
+    Fy += s * fx_to(gy);
+    Fz += s * fx_to(gz);
     if (MODE == UPD_DRIFT) { d.gx[gi] = 0; d.gy[gi] = 0; d.gz[gi] = 0; }
   }
-  const float kick = MODE == UPD_DRIFT ? *d.kick : 0.5f;
+  if (MODE == UPD_DRIFT) { d.fx[slot] = 0; d.fy[slot] = 0; d.fz[slot] = 0; }
   const float kdt = kick * c.dt * v.w;
   v.x += kdt * Fx; v.y += kdt * Fy; v.z += kdt * Fz;
   if (MODE == UPD_DRIFT) {
@@ -44,13 +50,12 @@ __global__ void __launch_bounds__(256) k_update(Dev d, SimConst c) {
       c1 = c.c1_u;
       c2sd = c.c2sqkT_u * sqrtf(v.w);
     } else {
-      const AtomSys as = d.asys[T.sysatom0 + o];
+      const AtomSys as = d.asys[__ldg(&d.tinfo[t].sysatom0) + o];
       c1 = as.c1;
       c2sd = as.c2sd;
     }
-    const unsigned long long step = (unsigned long long)(*d.step) + 1ull;
     p.x += c.half_dt * v.x; p.y += c.half_dt * v.y; p.z += c.half_dt * v.z;
-    const float3 xi = normal3(T.key0, T.key1, (uint32_t)o, step, 0u);
+    const float3 xi = normal3(key0, key1, (uint32_t)o, step, 0u);
     v.x = c1 * v.x + c2sd * xi.x;
     v.y = c1 * v.y + c2sd * xi.y;
     v.z = c1 * v.z + c2sd * xi.z;
