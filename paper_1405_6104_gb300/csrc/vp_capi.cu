@@ -599,8 +599,8 @@ VP_API int sim_create(const sim_system *systems, int32_t n_systems, const int32_
   r |= dalloc(h, &d.fy, slot0);
   r |= dalloc(h, &d.fz, slot0);
   r |= upload(h, &d.clus_trial, clus_trial);
-  r |= dalloc(h, &d.bb_lo, d.total_clus);
-  r |= dalloc(h, &d.bb_hi, d.total_clus);
+  r |= dalloc(h, &d.bb_lo, 2 * (size_t)d.total_clus);  // per 4-atom half cluster
+  r |= dalloc(h, &d.bb_hi, 2 * (size_t)d.total_clus);
   r |= dalloc(h, &d.list, (size_t)d.total_clus * c.list_cap);
   r |= dalloc(h, &d.list_n, d.total_clus);
   r |= upload(h, &d.col_trial, col_trial);

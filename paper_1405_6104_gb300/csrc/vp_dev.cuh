@@ -18,7 +18,7 @@ struct Dev {
   long long *fx, *fy, *fz;             // fixed-point force accumulators per slot
   // clusters
   int32_t *clus_trial;                 // static: trial of every i-cluster
-  float4 *bb_lo, *bb_hi;               // bounding boxes (wrapped positions at rebuild)
+  float4 *bb_lo, *bb_hi;               // bounding boxes of the 4-atom half clusters (wrapped positions at rebuild)
   uint2 *list;                         // [total_clus * list_cap] entries (see vp_internal.cuh)
   int32_t *list_n;
   // grid columns

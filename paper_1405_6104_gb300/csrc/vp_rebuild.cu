@@ -188,19 +188,20 @@ __global__ void __launch_bounds__(256) k_colsort(Dev d) {
       d.type_b[ns] = 0;
     }
   }
-  // bounding boxes (from the sorted keys' slots)
-  for (int k = threadIdx.x; k < ncl; k += blockDim.x) {
+  // bounding boxes of the 4-atom halves of each cluster (real atoms only; an
+  // all-padding half gets an empty box, lo > hi)
+  for (int k = threadIdx.x; k < 2 * ncl; k += blockDim.x) {
     float3 lo = make_float3(3e38f, 3e38f, 3e38f), hi = make_float3(-3e38f, -3e38f, -3e38f);
-    for (int a = 0; a < CL; ++a) {
-      int r = k * CL + a;
+    for (int a = 0; a < CJ; ++a) {
+      int r = k * CJ + a;
       if (r >= n) break;
       float4 p = d.pos[s_old[r]];
       lo.x = fminf(lo.x, p.x); lo.y = fminf(lo.y, p.y); lo.z = fminf(lo.z, p.z);
       hi.x = fmaxf(hi.x, p.x); hi.y = fmaxf(hi.y, p.y); hi.z = fmaxf(hi.z, p.z);
     }
-    int ci = T.clus0 + cstart + k;
-    d.bb_lo[ci] = make_float4(lo.x, lo.y, lo.z, 0.f);
-    d.bb_hi[ci] = make_float4(hi.x, hi.y, hi.z, 0.f);
+    int hj = 2 * (T.clus0 + cstart) + k;
+    d.bb_lo[hj] = make_float4(lo.x, lo.y, lo.z, 0.f);
+    d.bb_hi[hj] = make_float4(hi.x, hi.y, hi.z, 0.f);
   }
 }
 
@@ -233,19 +234,12 @@ __device__ __forceinline__ bool list_rule(float4 pi, float4 pj, float L, float i
   return r2 < rl2;
 }
 
-__device__ __forceinline__ bool excluded(const int *ex, int n, int o) {
-  for (int q = 0; q < n; ++q)
-    if (ex[q] == o) return true;
-  return false;
-}
-
 // A candidate whose atom pairs do not all share the image counts (it spans
 // half a box length in some dimension): the per-pair rule for all 8 x 4
-// pairs, with validity, self-pair and exclusion tests; kmin/kmax collect the
-// image keys of the passing pairs.
+// pairs, with validity and self-pair tests; kmin/kmax collect the image keys
+// of the passing pairs (exclusions are cleared afterwards).
 __device__ __noinline__ unsigned list_mixed_images(const Dev &d, int I, int Il, int J8, int sj0, float L, float iL,
-                                                   float rl2, const int (*ex)[MAX_EXCL], const int *nex, float &kmin,
-                                                   float &kmax) {
+                                                   float rl2, float &kmin, float &kmax) {
   unsigned mask = 0u;
   for (int b = 0; b < CJ; ++b) {
     const float4 pj = d.pos[sj0 + b];
@@ -254,8 +248,7 @@ __device__ __noinline__ unsigned list_mixed_images(const Dev &d, int I, int Il, 
       const float4 pi = d.pos[I * CL + a];
       const int oi = d.orig[I * CL + a];
       float key;
-      bool v = list_rule(pi, pj, L, iL, rl2, key) && oi >= 0 && oj >= 0 && (J8 != Il || sj0 + b > I * CL + a);
-      if (v && excluded(ex[a], nex[a], oj)) v = false;
+      const bool v = list_rule(pi, pj, L, iL, rl2, key) && oi >= 0 && oj >= 0 && (J8 != Il || sj0 + b > I * CL + a);
       if (v) {
         kmin = fminf(kmin, key);
         kmax = fmaxf(kmax, key);
@@ -267,19 +260,20 @@ __device__ __noinline__ unsigned list_mixed_images(const Dev &d, int I, int Il, 
 }
 
 constexpr int LIST_WARPS = 4;
-constexpr int CAND_MAX = 512;  // candidate 8-atom clusters per i-cluster (bounding-box pass)
+constexpr int CAND_MAX = 1024;  // candidate 4-atom j-clusters per i-cluster (bounding-box pass)
 
-// One warp per i-cluster.  Phase 1: lanes test columns, then the clusters of
-// each passing column, against the i-cluster's bounding box and collect the
-// candidates in order (column-major, then z).  Phase 2: each lane takes one
-// candidate 4-atom j-cluster and evaluates the FP32 list rule for all 8 x 4
-// atom pairs itself, giving the entry's mask, image code and exact flag;
-// entries are written in candidate order (deterministic).
-__global__ void __launch_bounds__(LIST_WARPS * 32) k_list(Dev d, SimConst c, float rl2_bbox) {
+// One warp per i-cluster.  Phase 1: lanes test columns, then the 4-atom
+// halves of the clusters of each passing column, against the i-cluster's
+// bounding box and collect the candidates in order (column-major, then z,
+// i.e. ascending j-cluster index).  Phase 2: each lane takes one candidate
+// and evaluates the FP32 list rule for all 8 x 4 atom pairs itself, giving
+// the entry's mask, image code and exact flag; entries are written in
+// candidate order (deterministic).  Phase 3: the i-atoms' exclusions clear
+// their bits in the written entries (found by binary search).
+__global__ void __launch_bounds__(LIST_WARPS * 32, 5) k_list(Dev d, SimConst c, float rl2_bbox) {
   __shared__ int s_cand[LIST_WARPS][CAND_MAX];
   __shared__ int s_excl[LIST_WARPS][CL][MAX_EXCL];
   __shared__ int s_nex[LIST_WARPS][CL];
-  __shared__ int s_exlo[LIST_WARPS][CL], s_exhi[LIST_WARPS][CL];
   const int wib = threadIdx.x >> 5;
   const int I = blockIdx.x * LIST_WARPS + wib;
   const int lane = threadIdx.x & 31;
@@ -291,16 +285,21 @@ __global__ void __launch_bounds__(LIST_WARPS * 32) k_list(Dev d, SimConst c, flo
     if (lane == 0) d.list_n[I] = 0;
     return;
   }
-  const float4 lo = d.bb_lo[I], hi = d.bb_hi[I];
+  float4 lo, hi;
+  {
+    const float4 l0 = d.bb_lo[2 * I], l1 = d.bb_lo[2 * I + 1], h0 = d.bb_hi[2 * I], h1 = d.bb_hi[2 * I + 1];
+    lo = make_float4(fminf(l0.x, l1.x), fminf(l0.y, l1.y), fminf(l0.z, l1.z), 0.f);
+    hi = make_float4(fmaxf(h0.x, h1.x), fmaxf(h0.y, h1.y), fmaxf(h0.z, h1.z), 0.f);
+  }
   const float L = T.box, iL = T.inv_box, w = T.col_w;
   const int nc2 = T.ncol * T.ncol;
   int *cand = s_cand[wib];
   int n_cand = 0;
   bool overflow = false;
-  // ---- phase 1: candidate clusters ----
-  // lanes test 32 columns; the clusters (index >= Il) of the passing columns
-  // are then enumerated as one flat range, 32 per step, so that the
-  // bounding-box loads of a whole step are in flight together
+  // ---- phase 1: candidate 4-atom j-clusters ----
+  // lanes test 32 columns; the halves (of clusters with index >= Il) of the
+  // passing columns are then enumerated as one flat range, 32 per step, so
+  // that the bounding-box loads of a whole step are in flight together
   for (int cb = 0; cb < nc2; cb += 32) {
     const int cc = cb + lane;
     int jlo = 0, cntc = 0;
@@ -313,7 +312,7 @@ __global__ void __launch_bounds__(LIST_WARPS * 32) k_list(Dev d, SimConst c, flo
         const int cx = cc / T.ncol, cy = cc - cx * T.ncol;
         const float gx = periodic_gap(lo.x, hi.x, cx * w, (cx + 1) * w, L);
         const float gy = periodic_gap(lo.y, hi.y, cy * w, (cy + 1) * w, L);
-        if (gx * gx + gy * gy < rl2_bbox) cntc = ccs + ncl - jlo;
+        if (gx * gx + gy * gy < rl2_bbox) cntc = 2 * (ccs + ncl - jlo);
       }
     }
     // inclusive scan of the per-column candidate counts
@@ -339,10 +338,10 @@ __global__ void __launch_bounds__(LIST_WARPS * 32) k_list(Dev d, SimConst c, flo
       const int own_cnt = __shfl_sync(0xffffffffu, cntc, lo_l);
       const int own_jlo = __shfl_sync(0xffffffffu, jlo, lo_l);
       bool ok = false;
-      int J8 = 0;
+      int J4 = 0;
       if (tt < total) {
-        J8 = own_jlo + (tt - (own_incl - own_cnt));
-        const float4 jlo4 = d.bb_lo[T.clus0 + J8], jhi4 = d.bb_hi[T.clus0 + J8];
+        J4 = 2 * own_jlo + (tt - (own_incl - own_cnt));
+        const float4 jlo4 = d.bb_lo[2 * T.clus0 + J4], jhi4 = d.bb_hi[2 * T.clus0 + J4];
         const float gx = periodic_gap(lo.x, hi.x, jlo4.x, jhi4.x, L);
         const float gy = periodic_gap(lo.y, hi.y, jlo4.y, jhi4.y, L);
         const float gz = periodic_gap(lo.z, hi.z, jlo4.z, jhi4.z, L);
@@ -350,7 +349,7 @@ __global__ void __launch_bounds__(LIST_WARPS * 32) k_list(Dev d, SimConst c, flo
       }
       const unsigned m = __ballot_sync(0xffffffffu, ok);
       const int pos = n_cand + __popc(m & ((1u << lane) - 1u));
-      if (ok && pos < CAND_MAX) cand[pos] = J8;
+      if (ok && pos < CAND_MAX) cand[pos] = J4;
       n_cand += __popc(m);
     }
   }
@@ -369,16 +368,8 @@ __global__ void __launch_bounds__(LIST_WARPS * 32) k_list(Dev d, SimConst c, flo
     const int o = d.orig[I * CL + lane];
     const int sa = T.sysatom0 + (o < 0 ? 0 : o);
     const int n = o < 0 ? 0 : d.excl_n[sa];
-    int lo_e = 0x7fffffff, hi_e = -1;
-    for (int k = 0; k < n; ++k) {
-      const int e = d.excl[(size_t)sa * MAX_EXCL + k];
-      s_excl[wib][lane][k] = e;
-      lo_e = min(lo_e, e);
-      hi_e = max(hi_e, e);
-    }
+    for (int k = 0; k < n; ++k) s_excl[wib][lane][k] = d.excl[(size_t)sa * MAX_EXCL + k];
     s_nex[wib][lane] = n;
-    s_exlo[wib][lane] = lo_e;
-    s_exhi[wib][lane] = hi_e;
   }
   __syncwarp();
   // ---- phase 2: one candidate 4-atom j-cluster per lane ----
@@ -387,34 +378,24 @@ __global__ void __launch_bounds__(LIST_WARPS * 32) k_list(Dev d, SimConst c, flo
   // every atom pair of the candidate has that q there and the rule reduces to
   // d - fl(L q) with the same rounding as the per-pair form.  Padding atoms
   // sit far outside every box and fail the distance test on that path.
-  // Exclusions: an i-atom's excluded indices span [exlo, exlo + exspan]; only
-  // a j index inside that range is looked up.
-  int exlo[CL];
-  unsigned exspan[CL];
-#pragma unroll
-  for (int a = 0; a < CL; ++a) {
-    exlo[a] = s_exlo[wib][a];
-    exspan[a] = s_exhi[wib][a] >= exlo[a] ? (unsigned)(s_exhi[wib][a] - exlo[a]) : 0u;
-  }
   uint2 *seg = d.list + (size_t)I * c.list_cap;
   const float rl2 = c.rl2;
   int cnt = 0;
-  for (int k0 = 0; k0 < 2 * n_cand; k0 += 32) {
+  for (int k0 = 0; k0 < n_cand; k0 += 32) {
     const int k = k0 + lane;
     unsigned mask = 0u, w0 = 0u;
-    if (k < 2 * n_cand) {
-      const int J8 = cand[k >> 1], h = k & 1;
+    if (k < n_cand) {
+      const int J4 = cand[k];
+      const int J8 = J4 >> 1, h = J4 & 1;
       const int JG = T.clus0 + J8;
       const int sj0 = JG * CL + h * CJ;
       float kmin = 3e38f, kmax = -3e38f;
-      const float4 jlo4 = d.bb_lo[JG], jhi4 = d.bb_hi[JG];
+      const float4 jlo4 = d.bb_lo[2 * T.clus0 + J4], jhi4 = d.bb_hi[2 * T.clus0 + J4];
       const float qlx = rintf(__fmul_rn(__fsub_rn(jlo4.x, hi.x), iL)), qhx = rintf(__fmul_rn(__fsub_rn(jhi4.x, lo.x), iL));
       const float qly = rintf(__fmul_rn(__fsub_rn(jlo4.y, hi.y), iL)), qhy = rintf(__fmul_rn(__fsub_rn(jhi4.y, lo.y), iL));
       const float qlz = rintf(__fmul_rn(__fsub_rn(jlo4.z, hi.z), iL)), qhz = rintf(__fmul_rn(__fsub_rn(jhi4.z, lo.z), iL));
       if (qlx == qhx && qly == qhy && qlz == qhz) {
         const float sx = __fmul_rn(L, qlx), sy = __fmul_rn(L, qly), sz = __fmul_rn(L, qlz);
-        const int4 oj4 = *reinterpret_cast<const int4 *>(d.orig + sj0);
-        const int oj[CJ] = {oj4.x, oj4.y, oj4.z, oj4.w};
 #pragma unroll
         for (int b = 0; b < CJ; ++b) {
           const float4 pj = d.pos[sj0 + b];
@@ -424,9 +405,7 @@ __global__ void __launch_bounds__(LIST_WARPS * 32) k_list(Dev d, SimConst c, flo
             const float dy = __fsub_rn(__fsub_rn(pj.y, yi[a]), sy);
             const float dz = __fsub_rn(__fsub_rn(pj.z, zi[a]), sz);
             const float r2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
-            bool v = r2 < rl2;
-            if (v && (unsigned)(oj[b] - exlo[a]) <= exspan[a]) v = !excluded(s_excl[wib][a], s_nex[wib][a], oj[b]);
-            if (v) mask |= 1u << (a * CJ + b);
+            if (r2 < rl2) mask |= 1u << (a * CJ + b);
           }
         }
         if (J8 == Il) {  // inside the i-cluster itself: pairs with the j slot above the i slot
@@ -440,7 +419,7 @@ __global__ void __launch_bounds__(LIST_WARPS * 32) k_list(Dev d, SimConst c, flo
         }
         if (mask) kmin = kmax = __fmaf_rn(9.0f, qlx, __fmaf_rn(3.0f, qly, qlz));
       } else {
-        mask = list_mixed_images(d, I, Il, J8, sj0, L, iL, rl2, s_excl[wib], s_nex[wib], kmin, kmax);
+        mask = list_mixed_images(d, I, Il, J8, sj0, L, iL, rl2, kmin, kmax);
       }
       // image counts of the entry from the key 9 nx + 3 ny + nz (each in -1..1)
       const int key = mask ? (int)kmin : 0;
@@ -456,8 +435,31 @@ __global__ void __launch_bounds__(LIST_WARPS * 32) k_list(Dev d, SimConst c, flo
     if (mask != 0u && pos < c.list_cap) seg[pos] = make_uint2(w0, mask);
     cnt += __popc(bal);
   }
+  const int n_ent = min(cnt, c.list_cap);
+  // ---- phase 3: exclusions ----
+  // lane a < 8 clears, for each atom excluded from i-atom a, the bit of that
+  // pair in the entry of its 4-atom j-cluster, if this list holds the pair
+  // (entries ascend in j-cluster index; a pair inside the i-cluster belongs
+  // to the entry with the higher slot as j)
+  __syncwarp();
+  if (lane < CL) {
+    const int si = I * CL + lane;
+    const int ne = s_nex[wib][lane];
+    for (int q = 0; q < ne; ++q) {
+      const int sj = d.slot_of[T.atom0 + s_excl[wib][lane][q]];
+      if ((sj >> 3) < I || ((sj >> 3) == I && sj <= si)) continue;  // listed from the other side, or not at all
+      const unsigned j4 = (unsigned)(sj >> 2);
+      int lo_e = 0, hi_e = n_ent;  // first entry with j-cluster >= j4
+      while (lo_e < hi_e) {
+        const int mid = (lo_e + hi_e) >> 1;
+        if ((seg[mid].x & J_MASK) < j4) lo_e = mid + 1; else hi_e = mid;
+      }
+      if (lo_e < n_ent && (seg[lo_e].x & J_MASK) == j4)
+        atomicAnd(&seg[lo_e].y, ~(1u << (lane * CJ + (sj & 3))));
+    }
+  }
   if (lane == 0) {
-    d.list_n[I] = min(cnt, c.list_cap);
+    d.list_n[I] = n_ent;
     if (cnt > c.list_cap || overflow) atomicOr(d.err, ERR_LIST);
   }
 }
