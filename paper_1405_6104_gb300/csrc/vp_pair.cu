@@ -421,10 +421,11 @@ __global__ void __launch_bounds__(PF_WARPS * 32, MINB) k_pair_f(Dev d, SimConst 
 
 // Packed variant: the same pair loop on FP32x2 arithmetic (FADD2, FMUL2,
 // FFMA2: one instruction for two pairs) over the i-atom pairs (2p, 2p+1).
-// The i-atoms sit in shared memory as {x, x', y, y'} {z, z', q, q'} and the
+// The i-atoms sit in shared memory as {-x, -x', -y, -y'} {-z, -z', q, q'} and the
 // LJ row of an i-atom pair is {c12, c12', -c6, -c6'}; per two pairs the loop
-// issues 3 FADD2, 5 FMUL2, 8 FFMA2, 2 RSQ, 3 LDS.128, 2 FSETP + FSEL and the
-// two mask tests.  The i-force partials accumulate +f*d and are negated once
+// issues 3 FADD2, 6 FMUL2, 7 FFMA2, 2 RSQ, 3 LDS.128 and, per pair, one mask
+// test joined with the cut-off test and a select (a masked pair may compute
+// inf or NaN on the way; the select discards it).  The i-force partials accumulate +f*d and are negated once
 // (exactly the sum of -f*d: round-to-nearest is sign-symmetric); the j-force
 // sums even and odd i-atoms in two partials, as the scalar variants do, so
 // all variants give bit-identical forces.
@@ -448,8 +449,9 @@ __global__ void __launch_bounds__(PF_WARPS * 32, MINB) k_pair_f2(Dev d, SimConst
 
   if (lane < CL / 2) {
     const float4 a0 = d.pos[I * CL + 2 * lane], a1 = d.pos[I * CL + 2 * lane + 1];
-    s_ip[wib][lane][0] = make_float4(a0.x, a1.x, a0.y, a1.y);
-    s_ip[wib][lane][1] = make_float4(a0.z, a1.z, a0.w, a1.w);
+    // negated coordinates: d = xj + (-xi) in one FADD2 (a packed operand has no negate modifier)
+    s_ip[wib][lane][0] = make_float4(-a0.x, -a1.x, -a0.y, -a1.y);
+    s_ip[wib][lane][1] = make_float4(-a0.z, -a1.z, a0.w, a1.w);
   }
   for (int k = lane; k < (CL / 2) * NT; k += 32) {
     const int p = k / NT, tj = k - p * NT;
@@ -493,12 +495,11 @@ __global__ void __launch_bounds__(PF_WARPS * 32, MINB) k_pair_f2(Dev d, SimConst
 #pragma unroll
       for (int p = 0; p < CL / 2; ++p) {
         const float4 i0 = s_ip[wib][p][0], i1 = s_ip[wib][p][1];
-        const float2 pen = make_float2((mb & (1u << (8 * p))) ? 0.0f : MASK_PEN,
-                                       (mb & (1u << (8 * p + 4))) ? 0.0f : MASK_PEN);
-        const float2 dx = __fadd2_rn(xj2, make_float2(-i0.x, -i0.y));
-        const float2 dy = __fadd2_rn(yj2, make_float2(-i0.z, -i0.w));
-        const float2 dz = __fadd2_rn(zj2, make_float2(-i1.x, -i1.y));
-        const float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __ffma2_rn(dx, dx, pen)));
+        const float2 dx = __fadd2_rn(xj2, make_float2(i0.x, i0.y));
+        const float2 dy = __fadd2_rn(yj2, make_float2(i0.z, i0.w));
+        const float2 dz = __fadd2_rn(zj2, make_float2(i1.x, i1.y));
+        // the mask bit joins the cut-off test (the same forces as the penalty form)
+        const float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
         const float2 rinv = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
         const float2 rinv2 = __fmul2_rn(rinv, rinv);
         const float2 rinv6 = __fmul2_rn(__fmul2_rn(rinv2, rinv2), rinv2);
@@ -509,8 +510,8 @@ __global__ void __launch_bounds__(PF_WARPS * 32, MINB) k_pair_f2(Dev d, SimConst
         tt = __ffma2_rn(qq, rinv, tt);
         tt = __fmul2_rn(tt, rinv2);
         float2 f = __ffma2_rn(qq, m2krf, tt);
-        f.x = r2.x < rc2 ? f.x : 0.0f;
-        f.y = r2.y < rc2 ? f.y : 0.0f;
+        f.x = ((mb & (1u << (8 * p))) && r2.x < rc2) ? f.x : 0.0f;
+        f.y = ((mb & (1u << (8 * p + 4))) && r2.y < rc2) ? f.y : 0.0f;
         fx[p] = __ffma2_rn(f, dx, fx[p]);
         fy[p] = __ffma2_rn(f, dy, fy[p]);
         fz[p] = __ffma2_rn(f, dz, fz[p]);
@@ -532,8 +533,8 @@ __global__ void __launch_bounds__(PF_WARPS * 32, MINB) k_pair_f2(Dev d, SimConst
 #pragma unroll
         for (int hh = 0; hh < 2; ++hh) {
           const float pen = (mb & (1u << (8 * p + 4 * hh))) ? 0.0f : MASK_PEN;
-          float dx = __fsub_rn(xj, hh ? i0.y : i0.x), dy = __fsub_rn(yj, hh ? i0.w : i0.z),
-                dz = __fsub_rn(zj, hh ? i1.y : i1.x);
+          float dx = __fadd_rn(xj, hh ? i0.y : i0.x), dy = __fadd_rn(yj, hh ? i0.w : i0.z),
+                dz = __fadd_rn(zj, hh ? i1.y : i1.x);
           if (exact) {
             dx = __fmaf_rn(-L, rintf(__fmul_rn(dx, iL)), dx);
             dy = __fmaf_rn(-L, rintf(__fmul_rn(dy, iL)), dy);
