@@ -16,6 +16,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "vpath_oracle.c")
+_SRCS = [_SRC, os.path.join(_HERE, "toy2d_oracle.c")]
 _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "libvpath_oracle.so")
 _lock = threading.Lock()
@@ -25,10 +26,11 @@ _lib = None
 def build(force: bool = False) -> str:
     """Compile the oracle (gcc, OpenMP, no FMA contraction)."""
     os.makedirs(_BUILD, exist_ok=True)
-    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+    newest = max(os.path.getmtime(f) for f in _SRCS)
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < newest:
         tmp = _LIB_PATH + f".tmp{os.getpid()}"
         cmd = ["gcc", "-O2", "-std=c11", "-fopenmp", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
-               _SRC, "-o", tmp, "-lm"]
+               *_SRCS, "-o", tmp, "-lm"]
         subprocess.run(cmd, check=True)
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
@@ -64,6 +66,11 @@ class OrRunOut(C.Structure):
     ]
 
 
+class OrToy2dParams(C.Structure):
+    _fields_ = [(n, C.c_double) for n in ("A1", "A2", "A3", "s1", "s2", "s3", "w", "xm", "ym", "mass", "gamma", "kT",
+                                          "dt", "x0", "y0", "z_product")] + [("bias", C.c_int32), ("s_power", C.c_int32)]
+
+
 def lib():
     global _lib
     with _lock:
@@ -88,6 +95,11 @@ def lib():
             L.or_phi_frames.restype = C.c_double
             L.or_phi_frames_grad.argtypes = [C.POINTER(OrSystem), C.POINTER(OrParams), vp, C.c_int32, vp]
             L.or_phi_frames_grad.restype = C.c_double
+            L.or_toy2d_force.argtypes = [C.POINTER(OrToy2dParams), C.c_double, C.c_double, vp, vp, vp]
+            L.or_toy2d_run.argtypes = [C.POINTER(OrToy2dParams), C.c_double, C.c_uint64, C.c_int64, vp, vp, vp]
+            L.or_toy2d_run.restype = C.c_int64
+            L.or_toy2d_phi_path.argtypes = [C.POINTER(OrToy2dParams), C.c_double, vp, C.c_int64, vp]
+            L.or_toy2d_phi_path.restype = C.c_double
             L.or_num_threads.restype = C.c_int32
             L.or_set_num_threads.argtypes = [C.c_int32]
             _lib = L
@@ -264,3 +276,43 @@ def num_threads():
 
 def set_num_threads(k):
     lib().or_set_num_threads(int(k))
+
+
+# ---------------------------------------------------------------------------
+# two-dimensional toy model (SM, "Illustrative Application in a Toy Model")
+# ---------------------------------------------------------------------------
+
+def _toy_params(tp):
+    return OrToy2dParams(**{f: float(getattr(tp, f)) for f, _ in OrToy2dParams._fields_ if f not in ("bias", "s_power")},
+                         bias=int(tp.bias), s_power=int(tp.s_power))
+
+
+def toy2d_force(tp, x, y):
+    """(U, Fx, Fy) at (x, y)."""
+    out = np.zeros(3)
+    pp = _toy_params(tp)
+    lib().or_toy2d_force(C.byref(pp), float(x), float(y), out[0:].ctypes.data, out[1:].ctypes.data,
+                         out[2:].ctypes.data)
+    return float(out[0]), float(out[1]), float(out[2])
+
+
+def toy2d_run(tp, k, seed, n_steps, want_path=False):
+    """One trial: (first passage step or -1, Phi, state (x, y, vx, vy), path (n, 2) or None)."""
+    pp = _toy_params(tp)
+    st = np.zeros(4)
+    phi = np.zeros(1)
+    path = np.zeros((n_steps + 1, 2)) if want_path else None
+    n = lib().or_toy2d_run(C.byref(pp), float(k), int(seed), int(n_steps), st.ctypes.data, phi.ctypes.data,
+                           None if path is None else path.ctypes.data)
+    if path is not None:
+        path = path[: (n + 1 if n >= 0 else n_steps + 1)]
+    return int(n), float(phi[0]), st, path
+
+
+def toy2d_phi_path(tp, k, path):
+    """(Phi, first passage index or -1) of Eq. VMDcondition along a given path (n, 2)."""
+    pp = _toy_params(tp)
+    P = np.ascontiguousarray(np.asarray(path, np.float64).reshape(-1, 2))
+    pas = np.zeros(1, np.int64)
+    Phi = lib().or_toy2d_phi_path(C.byref(pp), float(k), P.ctypes.data, len(P), pas.ctypes.data)
+    return float(Phi), int(pas[0])

@@ -436,3 +436,56 @@ def small_solvated(n_solute: int = 60, n_water: int = 420, seed: int = 5, cv_min
     p = protein_params(seed, k_ratchet=5.0, dt=0.001)
     p.cv_min_sep = cv_min_sep
     return s, p
+
+
+# ---------------------------------------------------------------------------
+# two-dimensional toy model (SM, "Illustrative Application in a Toy Model")
+# ---------------------------------------------------------------------------
+
+TOY_NONE, TOY_RATCHET, TOY_STEERED = 0, 1, 2
+
+
+@dataclasses.dataclass
+class Toy2dParams:
+    """The toy model's potential and Langevin parameters as the paper gives
+    them (A1 = 30, A2 = 20, A3 = 6, s1 = 1, s2 = 2, s3 = 2, w = 0.03, gate at
+    (1.5, 0); gamma = 1, dt = 0.02, k_B T = 0.2; start (0, 5)).  The mass is
+    not stated (m = 1); the product counts as reached when z = sqrt(x^2 + y^2)
+    <= z_product (0.3: well inside the funnel, whose thermal spread at the
+    bottom is about 0.04).  s_power is the exponent of s in the numerators of
+    the three well terms: the section prints 2, which leaves no ring barrier
+    (every plain trajectory reaches the funnel within about a thousand
+    steps); 4 (amplitude A at each centre) gives the barrier and the gate the
+    section describes and is the default."""
+    A1: float = 30.0
+    A2: float = 20.0
+    A3: float = 6.0
+    s1: float = 1.0
+    s2: float = 2.0
+    s3: float = 2.0
+    w: float = 0.03
+    xm: float = 1.5
+    ym: float = 0.0
+    mass: float = 1.0
+    gamma: float = 1.0
+    kT: float = 0.2
+    dt: float = 0.02
+    x0: float = 0.0
+    y0: float = 5.0
+    z_product: float = 0.3
+    bias: int = TOY_RATCHET
+    s_power: int = 4
+
+
+def toy2d_rmd_batch(n_trials: int = 2000, k_values: Sequence[float] = (1.0,), seed0: int = 5000):
+    """rMD trials of the toy model: n_trials per bias strength, trial seeds
+    seed0 + index (the paper: 2000 trials of 30 000 steps per K_R)."""
+    ks = np.repeat(np.asarray(k_values, np.float64), n_trials)
+    seeds = seed0 + np.arange(len(ks), dtype=np.uint64)
+    return Toy2dParams(bias=TOY_RATCHET), ks, seeds
+
+
+def toy2d_plain_batch(n_trials: int = 20000, seed0: int = 9000):
+    """Plain Langevin trials of the toy model (the paper: 20 000 trials of
+    90 000 steps)."""
+    return Toy2dParams(bias=TOY_NONE), np.zeros(n_trials), seed0 + np.arange(n_trials, dtype=np.uint64)
