@@ -248,6 +248,53 @@ int sim_philox_normals(uint64_t seed, int64_t step, uint32_t stream, int32_t n, 
 int cv_eval_noalloc(const float *d_pos, const double *d_native, int32_t n_cv, double box, const sim_params *params,
                     double *d_z, double *d_grad, void *cuda_stream, char *errbuf, int32_t errlen);
 
+/* ------------------------------------------------------------------------
+ * Two-dimensional toy model (SM, "Illustrative Application in a Toy Model").
+ * One particle of mass m on
+ *   U(x,y) = w^2 (x^2+y^2)^2 - A1 s1^p/(x^2+y^2+s1^2)^2 + A2 s2^p/(x^2+y^2+s2^2)^2
+ *            - A3 s3^p/((x-xm)^2+(y-ym)^2+s3^2)^2
+ * (the section prints p = 2; p = 4 gives each term the amplitude A at its
+ * centre and the ring barrier and gate the section describes), underdamped
+ * Langevin dynamics (Eq. Lang, BAOAB as on the atomistic path), started at
+ * (x0, y0) with a Maxwell-Boltzmann velocity (Philox stream 1, step 0), with
+ * one of three biases on z = sqrt(x^2 + y^2):
+ *   TOY2D_NONE     plain Langevin;
+ *   TOY2D_RATCHET  Eq. VR: F = -(k/2)(z - z_m) grad z when z > z_m, z_m the
+ *                  running minimum of z (z_m(0) = z(x0, y0));
+ *   TOY2D_STEERED  the section's steered-MD comparison: F = -k z grad z.
+ * A trial stops at its first step with z <= z_product; the functional of
+ * Eq. VMDcondition, Phi = sum dt |F_bias|^2 / (gamma m) over its force
+ * evaluations, is accumulated up to and including that step.
+ * ------------------------------------------------------------------------ */
+enum { TOY2D_NONE = 0, TOY2D_RATCHET = 1, TOY2D_STEERED = 2 };
+
+typedef struct {
+  double A1, A2, A3, s1, s2, s3, w, xm, ym; /* potential */
+  double mass, gamma, kT, dt;                /* Langevin (kT in the potential's units) */
+  double x0, y0;                             /* start */
+  double z_product;                          /* product reached when z <= z_product */
+  int32_t bias;                              /* TOY2D_* */
+  int32_t s_power;                           /* p: 2 or 4 */
+} toy2d_params;
+
+/* Runs n_trials independent trials of n_steps steps on the GPU (one thread
+ * per trial, FP64 without contraction).  All pointers are HOST pointers:
+ *   k[n_trials]      bias strength of each trial (ignored for TOY2D_NONE);
+ *   seeds[n_trials]  Philox key of each trial (noise counter (0, step, 0|1));
+ *   state[4*n_trials] (x, y, vx, vy) at each trial's end (may be NULL);
+ *   phi[n_trials]    the functional; passage[n_trials] first-passage step or -1;
+ *   path             may be NULL; else [n_trials][n_steps/path_every + 1][2]:
+ *                    (x, y) at steps 0, path_every, 2 path_every, ... up to
+ *                    the trial's end, NaN after it.
+ * cuda_stream: the stream used (NULL: legacy); the call returns when the
+ * results are on the host.  Device scratch is allocated and freed per call.
+ * Returns SIM_OK, SIM_EINVAL (null pointer, negative size, unknown bias,
+ * s_power not 2 or 4, m or dt <= 0, gamma or kT < 0, gamma = 0 with a bias)
+ * or SIM_ECUDA; errbuf/errlen (may be NULL/0) receive a message. */
+int toy2d_run(const toy2d_params *p, int32_t n_trials, const double *k, const uint64_t *seeds, int64_t n_steps,
+              double *state, double *phi, int64_t *passage, double *path, int32_t path_every, void *cuda_stream,
+              char *errbuf, int32_t errlen);
+
 /* The cudaStream_t the library launches on. */
 void *sim_stream(sim_handle *h);
 

@@ -60,6 +60,11 @@ class SimParams(C.Structure):
     ]
 
 
+class Toy2dParamsC(C.Structure):
+    _fields_ = [(n, C.c_double) for n in ("A1", "A2", "A3", "s1", "s2", "s3", "w", "xm", "ym", "mass", "gamma", "kT",
+                                          "dt", "x0", "y0", "z_product")] + [("bias", C.c_int32), ("s_power", C.c_int32)]
+
+
 _lib = None
 
 # every symbol the header declares, with its ctypes signature
@@ -89,6 +94,8 @@ _SIGS = {
     "sim_philox_normals": ([C.c_uint64, C.c_int64, C.c_uint32, C.c_int32, C.c_void_p, C.c_void_p], C.c_int),
     "cv_eval_noalloc": ([C.c_void_p, C.c_void_p, C.c_int32, C.c_double, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                          C.c_char_p, C.c_int32], C.c_int),
+    "toy2d_run": ([C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p,
+                   C.c_void_p, C.c_int32, C.c_void_p, C.c_char_p, C.c_int32], C.c_int),
     "sim_stream": ([C.c_void_p], C.c_void_p),
     "sim_destroy": ([C.c_void_p], None),
     "sim_last_error": ([C.c_void_p], C.c_char_p),
@@ -326,6 +333,31 @@ def cv_eval_noalloc(d_pos: int, d_native: int, n_cv: int, box: float, params, d_
                                 C.addressof(ps), C.c_void_p(d_z or None), C.c_void_p(d_grad or None),
                                 C.c_void_p(cuda_stream or None), buf, 256)
     return rc, buf.value.decode()
+
+
+def toy2d_run(tp, k, seeds, n_steps: int, path_every: int = 0, want_state: bool = True, cuda_stream: int = 0):
+    """Trials of the two-dimensional toy model on the GPU: k[i] and seeds[i]
+    per trial.  Returns (passage int64[n], phi[n], state (n, 4) or None,
+    path (n, n_steps // path_every + 1, 2) or None)."""
+    k = np.ascontiguousarray(k, np.float64).reshape(-1)
+    sd = np.ascontiguousarray(seeds, np.uint64).reshape(-1)
+    if len(k) != len(sd):
+        raise ValueError("k and seeds differ in length")
+    n = len(k)
+    pc = Toy2dParamsC(**{f: float(getattr(tp, f)) for f, _ in Toy2dParamsC._fields_ if f not in ("bias", "s_power")},
+                      bias=int(tp.bias), s_power=int(tp.s_power))
+    phi = np.zeros(n)
+    passage = np.zeros(n, np.int64)
+    state = np.zeros((n, 4)) if want_state else None
+    path = np.zeros((n, n_steps // path_every + 1, 2)) if path_every > 0 else None
+    buf = C.create_string_buffer(256)
+    rc = load().toy2d_run(C.addressof(pc), n, k.ctypes.data, sd.ctypes.data, int(n_steps),
+                          None if state is None else state.ctypes.data, phi.ctypes.data, passage.ctypes.data,
+                          None if path is None else path.ctypes.data, int(path_every), C.c_void_p(cuda_stream or None),
+                          buf, 256)
+    if rc != SIM_OK:
+        raise SimError(rc, buf.value.decode())
+    return passage, phi, state, path
 
 
 def sim_stream(h) -> int:

@@ -10,13 +10,16 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libvpath.so")
-SOURCES = ["vp_rebuild.cu", "vp_pair.cu", "vp_cv.cu", "vp_update.cu", "vp_capi.cu", "vp_noalloc.cu", "vp_adjoint.cu"]
+SOURCES = ["vp_rebuild.cu", "vp_pair.cu", "vp_cv.cu", "vp_update.cu", "vp_capi.cu", "vp_noalloc.cu", "vp_adjoint.cu",
+           "vp_toy2d.cu"]
 HEADERS = ["vp_internal.cuh", "vp_dev.cuh", "vp_cvpair.cuh", "vp_adjoint.cuh", os.path.join("..", "..", "include", "vpath.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-fvisibility=hidden"]
 # the pair kernel works far from the denormal range: flush-to-zero keeps its
 # reciprocal square root a single instruction
-EXTRA = {"vp_pair.cu": ["-ftz=true"]}
+EXTRA = {"vp_pair.cu": ["-ftz=true"],
+         # the toy model runs FP64 in the operation order of its equations
+         "vp_toy2d.cu": ["-fmad=false"]}
 
 
 def _nvcc():

@@ -78,3 +78,19 @@ def test_invalid_systems_are_rejected_on_the_host(lib):
     p2 = S.Params(**{**p.__dict__, "nstlist": 0})
     assert "params" in _expect_einval([s], p2)
     _expect_einval([s], p, trials=(0,))
+
+
+def test_toy2d_host_validation(lib):
+    import dataclasses
+    tp = S.Toy2dParams()
+    k, seeds = np.ones(3), np.arange(3, dtype=np.uint64)
+    for bad in (dict(bias=7), dict(s_power=3), dict(dt=0.0), dict(mass=-1.0), dict(gamma=0.0), dict(kT=-0.1)):
+        with pytest.raises(B.SimError) as e:
+            B.toy2d_run(dataclasses.replace(tp, **bad), k, seeds, 10)
+        assert e.value.code == B.SIM_EINVAL, bad
+    with pytest.raises(B.SimError) as e:
+        B.toy2d_run(tp, k, seeds, -1)
+    assert e.value.code == B.SIM_EINVAL
+    # no trials: nothing to do, no device touched
+    passage, phi, state, path = B.toy2d_run(tp, np.zeros(0), np.zeros(0, np.uint64), 10)
+    assert len(passage) == 0 and len(phi) == 0
