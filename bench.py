@@ -359,12 +359,98 @@ def run_gpu(args):
     return 0
 
 
+# the toy model: the section's rMD protocol (2000 trials of 30 000 steps per
+# K_R) over a scan of twelve K_R values spanning two and a half decades
+TOY_K = [0.25 * 2 ** (i / 1.5) for i in range(12)]  # 0.25 .. 40
+TOY_TRIALS, TOY_STEPS = 2000, 30000
+# FP64 operations of one trial-step as the equations state them (normals 12,
+# B-A-O-A-B 26, force 51, z 4, ratchet 9, functional 5, sum 2; a division,
+# square root, logarithm or sincos counts as one)
+TOY_FLOPS_PER_STEP = 109.0
+
+
+def toy_cpu_baseline(S, tp, ks, seeds, per_k: int = 2):
+    import oracle as O
+    idx = [i for k in TOY_K for i in np.where(ks == k)[0][:per_k]]
+    O.toy2d_run(tp, ks[idx[0]], int(seeds[idx[0]]), 100)
+    t0 = time.perf_counter()
+    steps = 0
+    for i in idx:
+        n, _, _, _ = O.toy2d_run(tp, ks[i], int(seeds[i]), TOY_STEPS)
+        steps += n if n >= 0 else TOY_STEPS
+    dt = time.perf_counter() - t0
+    return {"value": steps / dt, "unit": "trial-steps/s", "cores": 1, "kind": "oracle",
+            "sample": f"{len(idx)} trials ({per_k} per K_R) of up to {TOY_STEPS} steps, one core", "seconds": dt}
+
+
+def run_toy(args):
+    """The two-dimensional toy model: one bench step = one toy2d_run over the
+    whole K_R scan (12 x 2000 trials of up to 30 000 steps, each to first
+    passage)."""
+    import torch
+    rank, world, local = rank_info()
+    torch.cuda.set_device(local)
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1405_6104_gb300 import binding as B
+    from paper_1405_6104_gb300 import systems as S
+    tp, ks, seeds = S.toy2d_rmd_batch(TOY_TRIALS, TOY_K)
+    stream = torch.cuda.Stream()
+    sp = stream.cuda_stream
+    for _ in range(args.warmup):
+        passage, phi, _, _ = B.toy2d_run(tp, ks, seeds, TOY_STEPS, want_state=False, cuda_stream=sp)
+    executed = float(np.where(passage >= 0, passage, TOY_STEPS).sum())
+    clocks = ClockSampler(local) if rank == 0 else None
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t_begin = time.time()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        B.toy2d_run(tp, ks, seeds, TOY_STEPS, want_state=False, cuda_stream=sp)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    t_end = time.time()
+    ms = ev0.elapsed_time(ev1)
+    clk = clocks.stop(t_begin, t_end) if clocks else None
+    value = executed * args.steps / (ms * 1e-3)
+    pk, src = peaks()
+    sm_mhz = pk.get("sm_max_mhz", 2070.0)
+    fp64_peak = 152 * 2 * 2 * sm_mhz * 1e6  # 2 FP64 FMA per SM per clock
+    achieved = TOY_FLOPS_PER_STEP * executed / (ms * 1e-3 / args.steps)
+    best = {}
+    for k in TOY_K:
+        sel = np.where((ks == k) & (passage >= 0))[0]
+        best[f"{k:.3g}"] = {"reached": float(len(sel) / TOY_TRIALS),
+                            "best_phi": float(phi[sel].min()) if len(sel) else None}
+    line = {
+        "metric": "trial-steps/s (2-D toy model: rMD trials + functional, K_R scan)", "value": value,
+        "unit": "trial-steps/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"2-D toy model, {len(TOY_K)} K_R values x {TOY_TRIALS} rMD trials x up to "
+                               f"{TOY_STEPS} steps (each to first passage)", "trial_steps_executed": executed,
+                   "l2": "state in registers; no inputs beyond 32 B per trial"},
+        "roofline": {"bound": "alu", "kernel": "k_toy2d", "achieved": achieved / 1e12, "peak": fp64_peak / 1e12,
+                     "unit": "TFLOP/s (FP64)", "frac": achieved / fp64_peak, "traffic": None,
+                     "peak_source": f"152 SMs x 2 FP64 FMA x 2 x {sm_mhz:.0f} MHz",
+                     "work": f"{TOY_FLOPS_PER_STEP:.0f} FP64 operations per trial-step"},
+        "cpu_baseline": toy_cpu_baseline(S, tp, ks, seeds),
+        "gpu_launches": args.steps,
+        "clocks": clk,
+        "per_k": best,
+    }
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--workload", default="batched64", choices=["batched64", "toy2d"],
+                    help="batched64: the 64 x 11 040-atom trial batch (default); toy2d: the 2-D toy model's K_R scan")
     ap.add_argument("--pair-variant", type=int, default=None, help="fix the pair-kernel variant (skip autotuning)")
     ap.add_argument("--cv-variant", type=int, default=None, help="fix the reaction-coordinate kernel variant")
     ap.add_argument("--prep-steps", type=int, default=3000,
@@ -374,6 +460,8 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "toy2d":
+        return run_toy(args)
     return run_gpu(args)
 
 
