@@ -16,7 +16,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "vpath_oracle.c")
-_SRCS = [_SRC, os.path.join(_HERE, "toy2d_oracle.c")]
+_SRCS = [_SRC, os.path.join(_HERE, "toy2d_oracle.c"), os.path.join(_HERE, "contacts_oracle.c")]
 _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "libvpath_oracle.so")
 _lock = threading.Lock()
@@ -100,6 +100,11 @@ def lib():
             L.or_toy2d_run.restype = C.c_int64
             L.or_toy2d_phi_path.argtypes = [C.POINTER(OrToy2dParams), C.c_double, vp, C.c_int64, vp]
             L.or_toy2d_phi_path.restype = C.c_double
+            L.or_native_contacts.argtypes = [vp, C.c_int32, C.c_double, C.c_int32, vp, C.c_int64]
+            L.or_native_contacts.restype = C.c_int64
+            L.or_contact_times.argtypes = [vp, vp, C.c_int32, C.c_int32, C.c_double, C.c_double, vp, C.c_int64, vp]
+            L.or_path_similarity.argtypes = [vp, vp, C.c_int64]
+            L.or_path_similarity.restype = C.c_double
             L.or_num_threads.restype = C.c_int32
             L.or_set_num_threads.argtypes = [C.c_int32]
             _lib = L
@@ -316,3 +321,33 @@ def toy2d_phi_path(tp, k, path):
     pas = np.zeros(1, np.int64)
     Phi = lib().or_toy2d_phi_path(C.byref(pp), float(k), P.ctypes.data, len(P), pas.ctypes.data)
     return float(Phi), int(pas[0])
+
+
+# ---------------------------------------------------------------------------
+# order of native-contact formation and path similarity (Sec. "Results")
+# ---------------------------------------------------------------------------
+
+def native_contacts(native, n_cv, r0, min_sep):
+    """(Nc, 2) int32 pairs (i < j, j - i > min_sep) formed in the native structure."""
+    nat = np.ascontiguousarray(np.asarray(native, np.float64)[:n_cv].reshape(-1))
+    n = lib().or_native_contacts(nat.ctypes.data, int(n_cv), float(r0), int(min_sep), None, 0)
+    pairs = np.zeros((max(n, 1), 2), np.int32)
+    lib().or_native_contacts(nat.ctypes.data, int(n_cv), float(r0), int(min_sep), pairs.ctypes.data, n)
+    return pairs[:n]
+
+
+def contact_times(frames, steps, box, r0, pairs):
+    """Formation time of each contact along frames (n_frames, n_cv, 3) at the given steps (-1: not formed at the end)."""
+    F = np.ascontiguousarray(np.asarray(frames, np.float64))
+    st = np.ascontiguousarray(steps, np.int64)
+    pr = np.ascontiguousarray(pairs, np.int32)
+    t = np.zeros(len(pr), np.int64)
+    lib().or_contact_times(F.ctypes.data, st.ctypes.data, F.shape[0], F.shape[1], float(box), float(r0),
+                           pr.ctypes.data, len(pr), t.ctypes.data)
+    return t
+
+
+def path_similarity(ta, tb):
+    a = np.ascontiguousarray(ta, np.int64)
+    b = np.ascontiguousarray(tb, np.int64)
+    return float(lib().or_path_similarity(a.ctypes.data, b.ctypes.data, len(a)))
