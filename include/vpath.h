@@ -249,6 +249,41 @@ int cv_eval_noalloc(const float *d_pos, const double *d_native, int32_t n_cv, do
                     double *d_z, double *d_grad, void *cuda_stream, char *errbuf, int32_t errlen);
 
 /* ------------------------------------------------------------------------
+ * Order of native-contact formation and path similarity (Sec. "Results":
+ * the matrix M of the order in which native contacts form along a path, and
+ * s(k, k') = (1/(Nc (Nc - 1))) sum_{i != j} [M_ij(k) = M_ij(k')]).
+ * A contact (i, j) of reaction-coordinate atoms (j - i > cv_min_sep) is
+ * formed when C(r) = (1 - (r/r0)^6)/(1 - (r/r0)^10) > 1/2 (r0 = cv_r0, minimum
+ * image; decided in FP64 on the FP32 positions); native contacts are those
+ * formed in the native structure (Euclidean distances), listed by i then j.
+ * The formation time of a native contact is the step from which it has
+ * stayed formed, -1 when it is not formed at the last check; M_ij = 1, 0 or
+ * 1/2 as t_i <, > or = t_j, with -1 ordered after every step.
+ * ------------------------------------------------------------------------ */
+
+/* Tracks formation times in every trial, checking after each step whose
+ * number is a multiple of every (>= 1); 0 stops tracking.  Each call restarts
+ * all times at -1.  The first call builds the native contact lists.
+ * SIM_EINVAL for every < 0. */
+int sim_contact_tracking(sim_handle *h, int32_t every);
+
+/* Native contacts of a trial's system: *n_contacts receives their number and
+ * pairs[2*cap] the first cap of them (i, j).  Builds the lists if needed. */
+int sim_native_contacts(sim_handle *h, int32_t trial, int32_t *pairs, int64_t cap, int64_t *n_contacts);
+
+/* Formation times (steps, -1: not formed) of a trial's native contacts, in
+ * the order of sim_native_contacts; the first cap are written.  SIM_EINVAL if
+ * tracking was never enabled. */
+int sim_contact_times(sim_handle *h, int32_t trial, int64_t *times, int64_t cap);
+
+/* Path similarity on the GPU: times [n_paths][n_c] formation times (HOST,
+ * read), pairs [2*n_pairs] path indices (HOST), s [n_pairs] (HOST, written):
+ * s(pairs[2q], pairs[2q+1]).  n_c < 2 gives 1 (no ordered pair).  At most
+ * 65535 pairs per call.  Returns SIM_OK, SIM_EINVAL or SIM_ECUDA. */
+int path_similarity(const int64_t *times, int32_t n_paths, int64_t n_c, const int32_t *pairs, int32_t n_pairs,
+                    double *s, void *cuda_stream, char *errbuf, int32_t errlen);
+
+/* ------------------------------------------------------------------------
  * Two-dimensional toy model (SM, "Illustrative Application in a Toy Model").
  * One particle of mass m on
  *   U(x,y) = w^2 (x^2+y^2)^2 - A1 s1^p/(x^2+y^2+s1^2)^2 + A2 s2^p/(x^2+y^2+s2^2)^2

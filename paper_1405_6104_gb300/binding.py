@@ -94,6 +94,11 @@ _SIGS = {
     "sim_philox_normals": ([C.c_uint64, C.c_int64, C.c_uint32, C.c_int32, C.c_void_p, C.c_void_p], C.c_int),
     "cv_eval_noalloc": ([C.c_void_p, C.c_void_p, C.c_int32, C.c_double, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                          C.c_char_p, C.c_int32], C.c_int),
+    "sim_contact_tracking": ([C.c_void_p, C.c_int32], C.c_int),
+    "sim_native_contacts": ([C.c_void_p, C.c_int32, C.c_void_p, C.c_int64, C.c_void_p], C.c_int),
+    "sim_contact_times": ([C.c_void_p, C.c_int32, C.c_void_p, C.c_int64], C.c_int),
+    "path_similarity": ([C.c_void_p, C.c_int32, C.c_int64, C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p,
+                         C.c_char_p, C.c_int32], C.c_int),
     "toy2d_run": ([C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p,
                    C.c_void_p, C.c_int32, C.c_void_p, C.c_char_p, C.c_int32], C.c_int),
     "sim_stream": ([C.c_void_p], C.c_void_p),
@@ -333,6 +338,39 @@ def cv_eval_noalloc(d_pos: int, d_native: int, n_cv: int, box: float, params, d_
                                 C.addressof(ps), C.c_void_p(d_z or None), C.c_void_p(d_grad or None),
                                 C.c_void_p(cuda_stream or None), buf, 256)
     return rc, buf.value.decode()
+
+
+def sim_contact_tracking(h, every: int):
+    _check(h, load().sim_contact_tracking(h, int(every)))
+
+
+def sim_native_contacts(h, trial: int):
+    n = C.c_int64(0)
+    _check(h, load().sim_native_contacts(h, int(trial), None, 0, C.byref(n)))
+    pairs = np.zeros((max(n.value, 1), 2), np.int32)
+    _check(h, load().sim_native_contacts(h, int(trial), pairs.ctypes.data, n.value, C.byref(n)))
+    return pairs[: n.value]
+
+
+def sim_contact_times(h, trial: int, n_contacts: int):
+    t = np.zeros(max(n_contacts, 1), np.int64)
+    _check(h, load().sim_contact_times(h, int(trial), t.ctypes.data, int(n_contacts)))
+    return t[:n_contacts]
+
+
+def path_similarity(times, pairs, cuda_stream: int = 0):
+    """s(k, k') on the GPU for each (k, k') in pairs; times (n_paths, n_c)."""
+    T = np.ascontiguousarray(times, np.int64)
+    if T.ndim != 2:
+        raise ValueError("times must be (n_paths, n_contacts)")
+    P = np.ascontiguousarray(pairs, np.int32).reshape(-1, 2)
+    out = np.zeros(len(P))
+    buf = C.create_string_buffer(256)
+    rc = load().path_similarity(T.ctypes.data, T.shape[0], T.shape[1], P.ctypes.data, len(P), out.ctypes.data,
+                                C.c_void_p(cuda_stream or None), buf, 256)
+    if rc != SIM_OK:
+        raise SimError(rc, buf.value.decode())
+    return out
 
 
 def toy2d_run(tp, k, seeds, n_steps: int, path_every: int = 0, want_state: bool = True, cuda_stream: int = 0):

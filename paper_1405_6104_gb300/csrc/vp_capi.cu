@@ -10,6 +10,7 @@
 
 #include "../../include/vpath.h"
 #include "vp_adjoint.cuh"
+#include "vp_contacts.cuh"
 #include "vp_dev.cuh"
 
 #define VP_API extern "C" __attribute__((visibility("default")))
@@ -64,6 +65,16 @@ struct sim_handle {
   int32_t *d_argmin = nullptr;
   unsigned long long *d_count = nullptr;
   int max_atoms = 0;
+  // native structures (host copy, per system: first CV atom in native_all, CV atoms, min separation)
+  std::vector<double> native_all;
+  std::vector<int32_t> sys_nat0, sys_ncv, sys_minsep;
+  // native-contact formation tracker (built on first use)
+  ContactDev cdev{};
+  bool contacts_built = false;
+  bool contacts_tracked = false;     // sim_contact_tracking was called
+  std::vector<int32_t> csys_n;       // native contacts per system
+  std::vector<long long> ct_off;     // per trial: first entry of its formation times
+  std::vector<void *> callocs;
 };
 
 namespace {
@@ -187,6 +198,7 @@ void forces(sim_handle *h, FinMode mode) {
   }
   timed(h, "cv", [&] { launch_cv(h->d, h->c, s, h->cv_variant); });
   timed(h, "cvfin", [&] { launch_cvfin(h->d, h->c, mode, s); });
+  if (mode == FIN_STEP && h->cdev.every > 0) launch_contacts(h->d, h->cdev, s);
   if (h->frames)
     launch_rec_frames(h->d, h->frame_trial, h->tinfo[h->frame_trial].n_cv, h->frame_cap, h->frames, s);
 }
@@ -646,6 +658,10 @@ VP_API int sim_create(const sim_system *systems, int32_t n_systems, const int32_
   double *d_native = nullptr;
   r |= upload(h, &d_need, need_vel);
   r |= upload(h, &d_native, native_all);
+  h->native_all = native_all;
+  h->sys_nat0 = sys_nat0;
+  h->sys_ncv = sys_ncv;
+  h->sys_minsep = sys_minsep;
   r |= upload(h, &d_nat0, sys_nat0);
   r |= upload(h, &d_tsys, tile_sys);
   r |= upload(h, &d_st0, sys_tile0);
@@ -1133,6 +1149,135 @@ VP_API int sim_kernel_times(sim_handle *h, const char **names, double *ms, int64
   return n;
 }
 
+namespace {
+// C(r) > 1/2 with s = (r/r0)^2  <=>  s^4 + s^3 - s^2 - s - 1 < 0
+bool contact_above_half(double r2, double r0) {
+  const double s = r2 / (r0 * r0);
+  return (((s + 1.0) * s - 1.0) * s - 1.0) * s - 1.0 < 0.0;
+}
+
+// native contact lists of every system, per-trial formation times (all -1)
+int build_contacts(sim_handle *h) {
+  if (h->contacts_built) return SIM_OK;
+  const double r0 = h->params.cv_r0;
+  std::vector<int2> pairs;
+  std::vector<int32_t> off(h->n_sys), cnt(h->n_sys);
+  int max_nc = 0;
+  for (int sy = 0; sy < h->n_sys; ++sy) {
+    off[sy] = (int32_t)pairs.size();
+    const double *X = h->native_all.data() + 3 * (size_t)h->sys_nat0[sy];
+    const int n = h->sys_ncv[sy], ms = h->sys_minsep[sy];
+    for (int i = 0; i < n; ++i)
+      for (int j = i + ms + 1; j < n; ++j) {
+        const double dx = X[3 * j] - X[3 * i], dy = X[3 * j + 1] - X[3 * i + 1], dz = X[3 * j + 2] - X[3 * i + 2];
+        if (contact_above_half(dx * dx + dy * dy + dz * dz, r0)) pairs.push_back(make_int2(i, j));
+      }
+    cnt[sy] = (int32_t)pairs.size() - off[sy];
+    max_nc = std::max(max_nc, cnt[sy]);
+  }
+  std::vector<long long> toff(h->n_trials);
+  long long total = 0;
+  for (int t = 0; t < h->n_trials; ++t) {
+    toff[t] = total;
+    total += cnt[h->trial_sys[t]];
+  }
+  // threshold: the positive root s_h of s^4 + s^3 - s^2 - s - 1 (bisection on [1, 2])
+  double lo = 1.0, hi = 2.0;
+  for (int it = 0; it < 200; ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if ((((mid + 1.0) * mid - 1.0) * mid - 1.0) * mid - 1.0 < 0.0) lo = mid; else hi = mid;
+  }
+  const double rh2 = 0.5 * (lo + hi) * r0 * r0;
+  auto alloc = [&](void **p, size_t bytes) {
+    if (bytes == 0) bytes = 8;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e == cudaSuccess) h->callocs.push_back(*p);
+    return e;
+  };
+  int2 *dp = nullptr;
+  int32_t *doff = nullptr, *dcnt = nullptr, *dts = nullptr;
+  long long *dt = nullptr, *dtoff = nullptr;
+  CK(alloc((void **)&dp, pairs.size() * sizeof(int2)));
+  CK(alloc((void **)&doff, off.size() * sizeof(int32_t)));
+  CK(alloc((void **)&dcnt, cnt.size() * sizeof(int32_t)));
+  CK(alloc((void **)&dts, h->trial_sys.size() * sizeof(int32_t)));
+  CK(alloc((void **)&dt, (size_t)total * sizeof(long long)));
+  CK(alloc((void **)&dtoff, toff.size() * sizeof(long long)));
+  if (!pairs.empty()) CK(cudaMemcpy(dp, pairs.data(), pairs.size() * sizeof(int2), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(doff, off.data(), off.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(dcnt, cnt.data(), cnt.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+  std::vector<int32_t> ts(h->trial_sys.begin(), h->trial_sys.end());
+  CK(cudaMemcpy(dts, ts.data(), ts.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(dtoff, toff.data(), toff.size() * sizeof(long long), cudaMemcpyHostToDevice));
+  ContactDev &c = h->cdev;
+  c.every = 0;
+  c.max_nc = max_nc;
+  c.pairs = dp;
+  c.sys_off = doff;
+  c.sys_n = dcnt;
+  c.trial_sys = dts;
+  c.t = dt;
+  c.t_off = dtoff;
+  c.r2_lo = (float)(rh2 * (1.0 - 1e-4));
+  c.r2_hi = (float)(rh2 * (1.0 + 1e-4));
+  c.r0 = r0;
+  h->csys_n = cnt;
+  h->ct_off = toff;
+  h->contacts_built = true;
+  return SIM_OK;
+}
+}  // namespace
+
+VP_API int sim_contact_tracking(sim_handle *h, int32_t every) {
+  int r = enter(h);
+  if (r) return r;
+  if (every < 0) return fail(h, SIM_EINVAL, "every must be >= 0");
+  r = build_contacts(h);
+  if (r) return r;
+  long long total = h->ct_off.empty() ? 0 : h->ct_off.back() + h->csys_n[h->trial_sys.back()];
+  if (total > 0) CK(cudaMemsetAsync(h->cdev.t, 0xff, (size_t)total * sizeof(long long), h->stream));  // all -1
+  if (h->chunk) {  // the chunk graph is captured again with or without the tracker
+    cudaGraphExecDestroy(h->chunk);
+    h->chunk = nullptr;
+  }
+  h->cdev.every = every;
+  h->contacts_tracked = true;
+  CK(cudaStreamSynchronize(h->stream));
+  return SIM_OK;
+}
+
+VP_API int sim_native_contacts(sim_handle *h, int32_t trial, int32_t *pairs, int64_t cap, int64_t *n_contacts) {
+  int r = enter(h);
+  if (r) return r;
+  if (trial < 0 || trial >= h->n_trials || cap < 0 || (cap > 0 && !pairs))
+    return fail(h, SIM_EINVAL, "bad native-contact arguments");
+  r = build_contacts(h);
+  if (r) return r;
+  const int sy = h->trial_sys[trial];
+  const int64_t n = h->csys_n[sy];
+  if (n_contacts) *n_contacts = n;
+  const int64_t m = std::min(n, cap);
+  if (m > 0) {
+    int32_t off = 0;
+    for (int q = 0; q < sy; ++q) off += h->csys_n[q];
+    CK(cudaMemcpy(pairs, h->cdev.pairs + off, (size_t)m * sizeof(int2), cudaMemcpyDeviceToHost));
+  }
+  return SIM_OK;
+}
+
+VP_API int sim_contact_times(sim_handle *h, int32_t trial, int64_t *times, int64_t cap) {
+  int r = enter(h);
+  if (r) return r;
+  if (trial < 0 || trial >= h->n_trials || cap < 0 || (cap > 0 && !times))
+    return fail(h, SIM_EINVAL, "bad contact-time arguments");
+  if (!h->contacts_tracked) return fail(h, SIM_EINVAL, "contact tracking was never enabled");
+  const int64_t m = std::min<int64_t>(h->csys_n[h->trial_sys[trial]], cap);
+  CK(cudaStreamSynchronize(h->stream));
+  if (m > 0)
+    CK(cudaMemcpy(times, h->cdev.t + h->ct_off[trial], (size_t)m * sizeof(long long), cudaMemcpyDeviceToHost));
+  return SIM_OK;
+}
+
 VP_API int sim_philox_normals(uint64_t seed, int64_t step, uint32_t stream, int32_t n, uint32_t *raw,
                               double *normals) {
   if (n < 0 || step < 0) return SIM_EINVAL;
@@ -1162,6 +1307,7 @@ VP_API void sim_destroy(sim_handle *h) {
   if (h->stream) cudaStreamSynchronize(h->stream);
   if (h->chunk) cudaGraphExecDestroy(h->chunk);
   for (auto &e : h->gev) cudaEventDestroy(e);
+  for (void *p : h->callocs) cudaFree(p);
   for (void *p : h->allocs) cudaFree(p);
   if (h->d.rec) cudaFree(h->d.rec);
   if (h->frames) cudaFree(h->frames);
