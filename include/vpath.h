@@ -183,6 +183,22 @@ int phi_frames_adjoint(sim_handle *h, int32_t trial, const double *frames, int32
  * phi_frames_adjoint can process a long path segment by segment. */
 int phi_adjoint_coefficients(sim_handle *h, const double *z, const double *Q, int32_t n, double *coef, double *phi);
 
+/* Refinement of a path by descent on the functional (the variational
+ * condition of Eq. VMDcondition read as a minimisation over the path, with
+ * the frames X_1 .. X_{n_frames-2} as the variables and the end frames held
+ * fixed): starting from frames [n_frames][n_cv][3] (host, read and
+ * overwritten with the refined path), each iteration takes the gradient of
+ * phi_frames_adjoint and the first step eta, 2 eta_prev at first, halved until
+ * Phi(X - eta g) <= Phi(X) - 1e-4 eta |g|^2 (Armijo; g over the free frames);
+ * moved coordinates are rounded to FP32, the precision Phi is evaluated at.
+ * phi_history [n_iter + 1] (may be NULL) receives Phi before and after each
+ * iteration; *n_accepted (may be NULL) the iterations that moved the path.
+ * It stops early, repeating the last value, when no step lowers Phi.  The
+ * trial selects the system (and its native map).  SIM_EINVAL for n_frames < 2,
+ * n_iter < 0 or step <= 0. */
+int phi_frames_refine(sim_handle *h, int32_t trial, double *frames, int32_t n_frames, int32_t n_iter, double step,
+                      double *phi_history, int32_t *n_accepted);
+
 /* Test and diagnostics hooks.
  * sim_pairlist: the atom pairs (i < j, caller's indices) that the current
  *   cluster lists hold for one trial (list rule at the last rebuild);

@@ -351,3 +351,40 @@ def path_similarity(ta, tb):
     a = np.ascontiguousarray(ta, np.int64)
     b = np.ascontiguousarray(tb, np.int64)
     return float(lib().or_path_similarity(a.ctypes.data, b.ctypes.data, len(a)))
+
+
+def refine_frames(s, p, frames, n_iter, step):
+    """Descent on Phi over the inner frames of a path, end frames fixed, with
+    Armijo backtracking (first trial step 2x the last accepted one, halved
+    until Phi drops by 1e-4 eta |g|^2): FP64 restatement of the refinement.
+    Returns (frames, Phi history [n_iter + 1], accepted iterations)."""
+    X = np.array(frames, dtype=np.float64)[:, : s.n_cv, :].copy()
+    phi, G = phi_frames_grad(s, p, X)
+    G[0] = 0.0
+    G[-1] = 0.0
+    gg = float((G * G).sum())
+    hist = [phi]
+    eta, acc = step, 0
+    for it in range(n_iter):
+        ok = False
+        for _ in range(40):
+            if gg <= 0.0:
+                break
+            Y = X - eta * G
+            phi_y = phi_frames(s, p, Y)[0]
+            if phi_y <= phi - 1e-4 * eta * gg:
+                X, phi, ok = Y, phi_y, True
+                break
+            eta *= 0.5
+        if ok:
+            phi, G = phi_frames_grad(s, p, X)
+            G[0] = 0.0
+            G[-1] = 0.0
+            gg = float((G * G).sum())
+            acc += 1
+            eta *= 2.0
+        hist.append(phi)
+        if not ok:
+            hist += [phi] * (n_iter - it - 1)
+            break
+    return X, np.array(hist), acc

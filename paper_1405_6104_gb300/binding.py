@@ -94,6 +94,8 @@ _SIGS = {
     "sim_philox_normals": ([C.c_uint64, C.c_int64, C.c_uint32, C.c_int32, C.c_void_p, C.c_void_p], C.c_int),
     "cv_eval_noalloc": ([C.c_void_p, C.c_void_p, C.c_int32, C.c_double, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                          C.c_char_p, C.c_int32], C.c_int),
+    "phi_frames_refine": ([C.c_void_p, C.c_int32, C.c_void_p, C.c_int32, C.c_int32, C.c_double, C.c_void_p,
+                           C.c_void_p], C.c_int),
     "sim_contact_tracking": ([C.c_void_p, C.c_int32], C.c_int),
     "sim_native_contacts": ([C.c_void_p, C.c_int32, C.c_void_p, C.c_int64, C.c_void_p], C.c_int),
     "sim_contact_times": ([C.c_void_p, C.c_int32, C.c_void_p, C.c_int64], C.c_int),
@@ -338,6 +340,17 @@ def cv_eval_noalloc(d_pos: int, d_native: int, n_cv: int, box: float, params, d_
                                 C.addressof(ps), C.c_void_p(d_z or None), C.c_void_p(d_grad or None),
                                 C.c_void_p(cuda_stream or None), buf, 256)
     return rc, buf.value.decode()
+
+
+def phi_frames_refine(h, trial: int, frames, n_iter: int, step: float):
+    """Descent on Phi over the inner frames of a path (n_frames, n_cv, 3);
+    returns (refined frames, Phi history [n_iter + 1], accepted iterations)."""
+    F = np.array(frames, dtype=np.float64, order="C", copy=True)
+    hist = np.zeros(n_iter + 1)
+    acc = C.c_int32(0)
+    _check(h, load().phi_frames_refine(h, int(trial), F.ctypes.data, F.shape[0], int(n_iter), float(step),
+                                       hist.ctypes.data, C.byref(acc)))
+    return F, hist, int(acc.value)
 
 
 def sim_contact_tracking(h, every: int):

@@ -272,6 +272,145 @@ int adjoint_frames(const AdjInput &in, cudaStream_t st, std::string &err) {
   return SIM_OK;
 }
 
+// ---------------------------------------------------------------------------
+// refinement of a path by descent on the functional (frames as variables)
+// ---------------------------------------------------------------------------
+__global__ void k_to_f32(const double *x, float *y, size_t n) {
+  const size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < n) y[k] = (float)x[k];
+}
+
+// y = x - eta g on frames 1 .. nf-2, rounded to FP32 (the precision the
+// functional is evaluated at, so that the returned path is exactly the one
+// scored); y = x on the end frames, which stay put
+__global__ void k_descend(const double *x, const double *g, double eta, double *y, size_t per_frame, int nf) {
+  const size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= per_frame * (size_t)nf) return;
+  const int f = (int)(k / per_frame);
+  y[k] = (f == 0 || f == nf - 1) ? x[k] : (double)(float)(x[k] - eta * g[k]);
+}
+
+// |g|^2 over frames 1 .. nf-2: fixed-order block sums, then one block
+__global__ void k_sq_interior(const double *g, size_t per_frame, int nf, double *part) {
+  __shared__ double red[256];
+  double acc = 0.0;
+  const size_t lo = per_frame, hi = per_frame * (size_t)(nf > 1 ? nf - 1 : 0);
+  for (size_t k = lo + (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < hi; k += (size_t)gridDim.x * blockDim.x)
+    acc += g[k] * g[k];
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int off = blockDim.x / 2; off > 0; off >>= 1) {
+    if (threadIdx.x < off) red[threadIdx.x] += red[threadIdx.x + off];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = red[0];
+}
+
+int refine_frames(const AdjInput &in, double *frames, int n_iter, double step, double *phi_hist, int *n_accepted,
+                  cudaStream_t st, std::string &err) {
+  const int nf = in.n_frames, ncv = in.n_cv, nt = in.n_tiles;
+  const size_t na = (size_t)nf * ncv, nx = 3 * na;
+  AdjDev a{};
+  a.nf = nf; a.n_cv = ncv; a.min_sep = in.min_sep; a.n_tiles = nt;
+  a.tiles = in.tiles; a.cnat = in.cnat; a.gm = in.gm; a.L = in.L; a.iL = in.iL; a.zconst = in.zconst;
+  std::vector<void *> bufs;
+  auto alloc = [&](size_t bytes) -> void * {
+    void *p = nullptr;
+    if (cudaMalloc(&p, bytes ? bytes : 8) != cudaSuccess) return nullptr;
+    bufs.push_back(p);
+    return p;
+  };
+  auto freeall = [&]() { for (void *p : bufs) cudaFree(p); };
+  constexpr int SQ_BLOCKS = 64;
+  float *f32 = (float *)alloc(sizeof(float) * nx);
+  double *X = (double *)alloc(sizeof(double) * nx), *Y = (double *)alloc(sizeof(double) * nx);
+  double *G = (double *)alloc(sizeof(double) * nx);
+  a.gx = (long long *)alloc(sizeof(long long) * 3 * na);
+  a.hx = (long long *)alloc(sizeof(long long) * 3 * na);
+  a.w = (float *)alloc(sizeof(float) * nx);
+  a.zpart = (double *)alloc(sizeof(double) * (size_t)nf * (nt > 0 ? nt : 1));
+  a.z = (double *)alloc(sizeof(double) * nf);
+  a.Q = (double *)alloc(sizeof(double) * nf);
+  a.coef = (double *)alloc(sizeof(double) * 2 * nf);
+  double *route = (double *)alloc(sizeof(double) * nf);
+  double *dphi = (double *)alloc(sizeof(double));
+  double *part = (double *)alloc(sizeof(double) * SQ_BLOCKS);
+  for (void *p : bufs)
+    if (!p) { freeall(); err = "cudaMalloc failed"; return SIM_ECUDA; }
+  a.frames = f32;
+  a.gy = a.gx + na; a.gz = a.gy + na;
+  a.hy = a.hx + na; a.hz = a.hy + na;
+  const long long warps = (long long)nf * nt;
+  const unsigned gx_blocks = (unsigned)((nx + 255) / 256);
+  // Phi (and, when want_grad, dPhi/dX into G) at the frames in src
+  auto eval = [&](const double *src, bool want_grad, double &phi) -> cudaError_t {
+    k_to_f32<<<gx_blocks, 256, 0, st>>>(src, f32, nx);
+    cudaMemsetAsync(a.gx, 0, sizeof(long long) * 3 * na, st);
+    cudaMemsetAsync(a.hx, 0, sizeof(long long) * 3 * na, st);
+    if (warps > 0) k_adj_cv<<<(unsigned)((warps * 32 + 127) / 128), 128, 0, st>>>(a, in.k);
+    k_adj_fin<<<nf, 256, 0, st>>>(a);
+    k_adj_scan<<<1, 32, 0, st>>>(a.z, a.Q, nf, in.c, a.coef, route, dphi);
+    if (want_grad) {
+      if (warps > 0) k_adj_hw<<<(unsigned)((warps * 32 + 127) / 128), 128, 0, st>>>(a, in.k);
+      if (na > 0) k_adj_out<<<(unsigned)((na + 255) / 256), 256, 0, st>>>(a, G);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&phi, dphi, sizeof(double), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    return e;
+  };
+  auto sq = [&](double &v) -> cudaError_t {
+    k_sq_interior<<<SQ_BLOCKS, 256, 0, st>>>(G, 3 * (size_t)ncv, nf, part);
+    double h[SQ_BLOCKS];
+    cudaError_t e = cudaMemcpyAsync(h, part, sizeof(h), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    v = 0.0;
+    for (int b = 0; b < SQ_BLOCKS; ++b) v += h[b];
+    return e;
+  };
+  cudaError_t e = cudaMemcpyAsync(X, frames, sizeof(double) * nx, cudaMemcpyHostToDevice, st);
+  double phi = 0.0, gg = 0.0;
+  if (e == cudaSuccess) e = eval(X, true, phi);
+  if (e == cudaSuccess) e = sq(gg);
+  if (phi_hist) phi_hist[0] = phi;
+  int accepted = 0;
+  double eta = step;
+  for (int it = 0; it < n_iter && e == cudaSuccess; ++it) {
+    bool ok = false;
+    // backtracking (Armijo): accept the first step that lowers Phi by at least 1e-4 eta |g|^2
+    for (int bt = 0; bt < 40 && e == cudaSuccess && gg > 0.0; ++bt) {
+      k_descend<<<gx_blocks, 256, 0, st>>>(X, G, eta, Y, 3 * (size_t)ncv, nf);
+      double phi_y = 0.0;
+      e = eval(Y, false, phi_y);
+      if (e != cudaSuccess) break;
+      if (phi_y <= phi - 1e-4 * eta * gg) {
+        std::swap(X, Y);
+        phi = phi_y;
+        ok = true;
+        break;
+      }
+      eta *= 0.5;
+    }
+    if (e == cudaSuccess && ok) {
+      e = eval(X, true, phi);
+      if (e == cudaSuccess) e = sq(gg);
+      ++accepted;
+      eta *= 2.0;
+    }
+    if (phi_hist) phi_hist[it + 1] = phi;
+    if (!ok) {  // no step lowers Phi any more: keep the value for the remaining entries
+      for (int k = it + 2; phi_hist && k <= n_iter; ++k) phi_hist[k] = phi;
+      break;
+    }
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(frames, X, sizeof(double) * nx, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  freeall();
+  if (n_accepted) *n_accepted = accepted;
+  if (e != cudaSuccess) { err = cudaGetErrorString(e); return SIM_ECUDA; }
+  return SIM_OK;
+}
+
 int adjoint_coefficients(const double *z, const double *Q, int n, double c, double *coef, double *phi,
                          cudaStream_t st, std::string &err) {
   double *dz = nullptr, *dq = nullptr, *dc = nullptr, *dr = nullptr, *dp = nullptr;

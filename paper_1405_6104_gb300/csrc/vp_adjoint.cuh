@@ -24,5 +24,9 @@ struct AdjInput {
 int adjoint_frames(const AdjInput &in, cudaStream_t st, std::string &err);
 int adjoint_coefficients(const double *z, const double *Q, int n, double c, double *coef, double *phi,
                          cudaStream_t st, std::string &err);
+// descent on Phi over frames 1 .. n_frames-2 (in.frames is ignored; frames is
+// read and overwritten), Armijo backtracking; phi_hist[n_iter + 1]
+int refine_frames(const AdjInput &in, double *frames, int n_iter, double step, double *phi_hist, int *n_accepted,
+                  cudaStream_t st, std::string &err);
 
 }  // namespace vp

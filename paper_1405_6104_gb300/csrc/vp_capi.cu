@@ -963,6 +963,26 @@ VP_API int phi_frames_adjoint(sim_handle *h, int32_t trial, const double *frames
   return SIM_OK;
 }
 
+VP_API int phi_frames_refine(sim_handle *h, int32_t trial, double *frames, int32_t n_frames, int32_t n_iter,
+                             double step, double *phi_history, int32_t *n_accepted) {
+  int r = enter(h);
+  if (r) return r;
+  if (trial < 0 || trial >= h->n_trials || n_frames < 2 || !frames || n_iter < 0 || !(step > 0.0))
+    return fail(h, SIM_EINVAL, "bad refinement arguments");
+  TrialState S;
+  CK(cudaMemcpyAsync(&S, h->d.tstate + trial, sizeof(S), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  AdjInput in = adj_input(h, trial);
+  in.n_frames = n_frames;
+  in.zconst = S.zconst;
+  std::string err;
+  int acc = 0;
+  r = refine_frames(in, frames, n_iter, step, phi_history, &acc, h->stream, err);
+  if (n_accepted) *n_accepted = acc;
+  if (r) return fail(h, r, "phi_frames_refine: " + err);
+  return SIM_OK;
+}
+
 VP_API int phi_adjoint_coefficients(sim_handle *h, const double *z, const double *Q, int32_t n, double *coef,
                                     double *phi) {
   int r = enter(h);
