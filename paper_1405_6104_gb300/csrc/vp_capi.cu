@@ -64,6 +64,7 @@ struct sim_handle {
   size_t dbuf_n = 0;
   int32_t *d_argmin = nullptr;
   unsigned long long *d_count = nullptr;
+  int *d_flag = nullptr;  // device flag of host-side checks done on the GPU
   int max_atoms = 0;
   // native structures (host copy, per system: first CV atom in native_all, CV atoms, min separation)
   std::vector<double> native_all;
@@ -648,6 +649,7 @@ VP_API int sim_create(const sim_system *systems, int32_t n_systems, const int32_
   r |= dalloc(h, &d.skin_count, 1);
   r |= dalloc(h, &h->d_argmin, 1);
   r |= dalloc(h, &h->d_count, 1);
+  r |= dalloc(h, &h->d_flag, 1);
   if (r) return bail(SIM_ECUDA);
   float half = 0.5f;
   if (cudaMemcpy(d.kick, &half, sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess)
@@ -792,17 +794,21 @@ VP_API int sim_set_state(sim_handle *h, int32_t trial, const double *pos, const 
   int t0 = trial < 0 ? 0 : trial, t1 = trial < 0 ? h->n_trials : trial + 1;
   size_t n = 0;
   for (int t = t0; t < t1; ++t) n += (size_t)h->tinfo[t].n_atoms;
-  for (size_t k = 0; k < 3 * n; ++k)
-    if (!std::isfinite(pos[k]) || !std::isfinite(vel[k])) return fail(h, SIM_EINVAL, "non-finite state");
   r = ensure_dbuf(h, 6 * n);
   if (r) return r;
   CK(cudaMemcpyAsync(h->dbuf, pos, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, h->stream));
   CK(cudaMemcpyAsync(h->dbuf + 3 * n, vel, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, h->stream));
-  launch_scatter_state(h->d, trial, h->dbuf, h->dbuf + 3 * n, (int)n, h->stream);
+  // the state is checked on the device before it replaces the current one
+  CK(cudaMemsetAsync(h->d_flag, 0, sizeof(int), h->stream));
+  launch_check_finite(h->dbuf, 6 * n, h->d_flag, h->stream);
   // functional bookkeeping of the affected trials
   std::vector<TrialState> S(h->n_trials);
+  int bad = 0;
   CK(cudaMemcpyAsync(S.data(), h->d.tstate, sizeof(TrialState) * h->n_trials, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaMemcpyAsync(&bad, h->d_flag, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
+  if (bad) return fail(h, SIM_EINVAL, "non-finite state");
+  launch_scatter_state(h->d, trial, h->dbuf, h->dbuf + 3 * n, (int)n, h->stream);
   for (int t = t0; t < t1; ++t) {
     if (cv_state) {
       S[t].zm = cv_state[2 * (t - t0)];

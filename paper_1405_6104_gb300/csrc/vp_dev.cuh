@@ -79,6 +79,7 @@ void launch_update(const Dev &d, const SimConst &c, UpdateMode mode, cudaStream_
 void launch_init_vel(const Dev &d, float kT, const int32_t *need, cudaStream_t s);
 void launch_scatter_state(const Dev &d, int32_t trial, const double *pos, const double *vel, int32_t n, cudaStream_t s);
 void launch_gather_state(const Dev &d, int32_t trial, double *pos, double *vel, int32_t n, cudaStream_t s);
+void launch_check_finite(const double *x, size_t n, int *flag, cudaStream_t s);
 void launch_forces_out(const Dev &d, const SimConst &c, int32_t trial, double *out, int32_t n, cudaStream_t s);
 void launch_kinetic(const Dev &d, int32_t trial, cudaStream_t s);
 void launch_extract_pairs(const Dev &d, int32_t list_cap, int32_t trial, int32_t n_clus, int32_t *pairs,

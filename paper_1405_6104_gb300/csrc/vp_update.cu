@@ -127,6 +127,15 @@ __global__ void k_scatter_state(Dev d, int trial, const double *pos, const doubl
   d.ref_pos[T.atom0 + o] = make_float4(p.x, p.y, p.z, 0.f);
 }
 
+// flag = 1 if any of the n values is not finite (the caller's state is
+// checked on the device before it replaces the current one)
+__global__ void k_check_finite(const double *x, size_t n, int *flag) {
+  bool bad = false;
+  for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x)
+    bad |= !isfinite(x[k]);
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(flag, 1);
+}
+
 __global__ void k_gather_state(Dev d, int trial, double *pos, double *vel, int n) {
   int o = blockIdx.x * blockDim.x + threadIdx.x;
   if (o >= n) return;
@@ -237,6 +246,9 @@ void launch_init_vel(const Dev &d, float kT, const int32_t *need, cudaStream_t s
 void launch_scatter_state(const Dev &d, int32_t trial, const double *pos, const double *vel, int32_t n,
                           cudaStream_t s) {
   if (n > 0) k_scatter_state<<<(n + 255) / 256, 256, 0, s>>>(d, trial, pos, vel, n);
+}
+void launch_check_finite(const double *x, size_t n, int *flag, cudaStream_t s) {
+  if (n > 0) k_check_finite<<<4 * 152, 256, 0, s>>>(x, n, flag);
 }
 void launch_gather_state(const Dev &d, int32_t trial, double *pos, double *vel, int32_t n, cudaStream_t s) {
   if (n > 0) k_gather_state<<<(n + 255) / 256, 256, 0, s>>>(d, trial, pos, vel, n);

@@ -301,3 +301,20 @@ def test_in_graph_pair_timing():
             results.append([b.get_state(t) for t in range(2)])
     for x, y in zip(*results):
         assert np.array_equal(x[0], y[0]) and np.array_equal(x[1], y[1])
+
+
+def test_set_state_rejects_non_finite_input_and_keeps_the_state():
+    s, p = S.small_solvated()
+    with B.TrialBatch(s, p, [2], trial_seeds=[4, 5]) as b:
+        b.step(10)
+        before = [b.get_state(t) for t in range(2)]
+        pos, vel, _ = b.get_state(1)
+        pos = pos.copy()
+        pos[7, 1] = np.nan
+        with pytest.raises(B.SimError) as e:
+            b.set_state(1, pos, vel)
+        assert e.value.code == B.SIM_EINVAL and "non-finite" in str(e.value)
+        after = [b.get_state(t) for t in range(2)]
+        for x, y in zip(before, after):
+            assert np.array_equal(x[0], y[0]) and np.array_equal(x[1], y[1])
+        b.step(10)  # and the handle stays usable
