@@ -1,6 +1,7 @@
 // vp_capi.cu -- host side of the C ABI declared in include/vpath.h: batch
 // construction, the per-step launch sequence, CUDA-graph capture of list
 // intervals, state transfer and diagnostics.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -636,6 +637,17 @@ VP_API int sim_create(const sim_system *systems, int32_t n_systems, const int32_
   r |= upload(h, &d.bterm, bterm);
   r |= upload(h, &d.tiles, tiles);
   r |= upload(h, &d.work, work);
+  {
+    // tiles close to the diagonal hold the pairs close in sequence, which are
+    // mostly near pairs: they run first so that the long ones do not trail
+    std::vector<int32_t> order(work.size());
+    for (size_t k = 0; k < work.size(); ++k) order[k] = (int32_t)k;
+    std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
+      const int2 ta = tiles[work[a].y], tb = tiles[work[b].y];
+      return ta.y - ta.x < tb.y - tb.x;
+    });
+    r |= upload(h, &d.work_order, order);
+  }
   r |= dalloc(h, &d.cnat, tiles.size() * CV_T * CV_T);
   r |= upload(h, &d.sys_ncv, ncv_v);
   r |= upload(h, &d.sys_minsep, ms_v);

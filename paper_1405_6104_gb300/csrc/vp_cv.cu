@@ -83,9 +83,10 @@ __global__ void __launch_bounds__(CV_WARPS * 32) k_cv(Dev d, SimConst c) {
   __shared__ float s_x[CV_WARPS][2 * CV_T][3];
   __shared__ unsigned long long s_g[CV_WARPS][2 * CV_T][3];
   const int wib = threadIdx.x >> 5;
-  const int w = blockIdx.x * CV_WARPS + wib;
+  const int wq = blockIdx.x * CV_WARPS + wib;
   const int lane = threadIdx.x & 31;
-  if (w >= d.total_work) return;
+  if (wq >= d.total_work) return;
+  const int w = d.work_order[wq];  // costliest tiles first (the partial sums keep their slots)
   const int2 wk = d.work[w];
   const TrialInfo T = d.tinfo[wk.x];
   const int2 bij = d.tiles[wk.y];

@@ -39,6 +39,7 @@ struct Dev {
   // reaction coordinate
   int2 *tiles;                         // per system tile (bi, bj), concatenated
   int2 *work;                          // flat (trial, global tile) work items
+  int32_t *work_order;                 // the order warps take them: tiles near the diagonal (most near pairs) first
   double *cnat;                        // [tiles * 1024] C~ of the native structure in tile-skew order
   int32_t *sys_ncv, *sys_minsep;
   // Lennard-Jones pair table over de-duplicated types

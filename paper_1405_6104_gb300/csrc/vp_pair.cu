@@ -472,16 +472,16 @@ __global__ void __launch_bounds__(PF_WARPS * 32, MINB) k_pair_f2(Dev d, SimConst
 
   const int n = d.list_n[I];
   const uint2 *seg = d.list + (size_t)I * c.list_cap;
+  // list entries are fetched two groups ahead; the j-atom itself at the top
+  // of its iteration (fewer live registers: a higher block count per SM hides
+  // that load better than a prefetch does)
   uint2 ent = g < n ? seg[g] : make_uint2(0u, 0u);
   uint2 ent_n = 8 + g < n ? seg[8 + g] : make_uint2(0u, 0u);
-  float4 pj = d.pos[(int)(ent.x & J_MASK) * CJ + b];
-  int tj = d.type[(int)(ent.x & J_MASK) * CJ + b];
   for (int e0 = 0; e0 < n; e0 += 8) {
     const uint2 ent_nn = e0 + 16 + g < n ? seg[e0 + 16 + g] : make_uint2(0u, 0u);
-    const int sj_n = (int)(ent_n.x & J_MASK) * CJ + b;
-    const float4 pj_n = d.pos[sj_n];
-    const int tj_n = d.type[sj_n];
     const int sj = (int)(ent.x & J_MASK) * CJ + b;
+    const float4 pj = d.pos[sj];
+    const int tj = d.type[sj];
     const float4 shv = s_sh[wib][(ent.x >> J_BITS) & 63u];
     const float xj = pj.x - shv.x, yj = pj.y - shv.y, zj = pj.z - shv.z, qj = pj.w;
     const unsigned mb = ent.y >> b;
@@ -572,8 +572,6 @@ __global__ void __launch_bounds__(PF_WARPS * 32, MINB) k_pair_f2(Dev d, SimConst
     }
     ent = ent_n;
     ent_n = ent_nn;
-    pj = pj_n;
-    tj = tj_n;
   }
 
   float fi[CL][3];
