@@ -662,6 +662,12 @@ VP_API int sim_create(const sim_system *systems, int32_t n_systems, const int32_
   r |= dalloc(h, &h->d_argmin, 1);
   r |= dalloc(h, &h->d_count, 1);
   r |= dalloc(h, &h->d_flag, 1);
+  r |= dalloc(h, &d.pair_next, 1);
+  {
+    int nsm = 0;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device);
+    d.n_sm = nsm > 0 ? nsm : 1;
+  }
   if (r) return bail(SIM_ECUDA);
   float half = 0.5f;
   if (cudaMemcpy(d.kick, &half, sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess)

@@ -53,6 +53,8 @@ struct Dev {
   long long *energy;                   // [n_trials * 5] fixed point (2^24): LJ, RF, bond, angle, kin
   long long *skin_count;
   double *rec;                         // [n_trials * rec_cap * 5]: z, z_m, a, phi, Q
+  unsigned *pair_next;                 // work counter of the persistent pair kernel
+  int32_t n_sm;                        // multiprocessors of the device
 };
 
 enum UpdateMode { UPD_DRIFT = 0, UPD_FINAL = 1 };

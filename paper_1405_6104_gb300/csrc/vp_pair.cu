@@ -10,6 +10,8 @@
 // forces are bit-reproducible.  The same warp adds the bonded forces of its
 // 8 atoms (each atom computes its own share of every bond and angle it is
 // part of).
+#include <algorithm>
+
 #include "vp_dev.cuh"
 
 namespace vp {
@@ -430,19 +432,25 @@ __global__ void __launch_bounds__(PF_WARPS * 32, MINB) k_pair_f(Dev d, SimConst 
 // sums even and odd i-atoms in two partials, as the scalar variants do, so
 // all variants give bit-identical forces.
 template <int MINB>
-__global__ void __launch_bounds__(PF_WARPS * 32, MINB) k_pair_f2(Dev d, SimConst c) {
+__global__ void __launch_bounds__(PF_WARPS * 32, MINB) k_pair_f2(Dev d, SimConst c, unsigned *next) {
   constexpr int TS = SMALL_TYPES;
   __shared__ float4 s_c4[PF_WARPS][CL / 2][TS];
   __shared__ float4 s_sh[PF_WARPS][64];
   __shared__ float4 s_ip[PF_WARPS][CL / 2][2];
   __shared__ float s_red[PF_WARPS][3 * CL * 33];
   const int wib = threadIdx.x >> 5;
-  const int I = blockIdx.x * PF_WARPS + wib;
   const int lane = threadIdx.x & 31;
+  // persistent warps: each takes the next i-cluster from a counter until none
+  // is left, so that short and long lists even out across the SMs
+  for (;;) {
+  __syncwarp();  // the warp's tables of its previous cluster are no longer read
+  unsigned got = 0u;
+  if (lane == 0) got = atomicAdd(next, 1u);
+  const int I = (int)__shfl_sync(0xffffffffu, got, 0);
   if (I >= d.total_clus) return;
   const int t = d.clus_trial[I];
   const TrialInfo T = d.tinfo[t];
-  if (I - T.clus0 >= d.tstate[t].n_clus) return;
+  if (I - T.clus0 >= d.tstate[t].n_clus) continue;
   const float L = T.box, iL = T.inv_box;
   const int g = lane >> 2, b = lane & 3;
   const int NT = c.n_types;
@@ -604,6 +612,7 @@ __global__ void __launch_bounds__(PF_WARPS * 32, MINB) k_pair_f2(Dev d, SimConst
     const long long val = fx_from(sum);
     if (val != 0) red_add((comp == 0 ? d.fx : comp == 1 ? d.fy : d.fz) + I * CL + a, val);
   }
+  }  // for each cluster
 }
 
 // variants differ in the register cap (blocks per SM the compiler must fit)
@@ -627,9 +636,17 @@ void launch_pair(const Dev &d, const SimConst &c, bool energy, int32_t only_tria
     case 3: k_pair_f<6, true, SMALL_TYPES><<<fb, PF_WARPS * 32, 0, s>>>(d, c); break;
     case 4: k_pair_f<7, true, SMALL_TYPES><<<fb, PF_WARPS * 32, 0, s>>>(d, c); break;
     case 5: k_pair_f<8, true, SMALL_TYPES><<<fb, PF_WARPS * 32, 0, s>>>(d, c); break;
-    case 6: k_pair_f2<5><<<fb, PF_WARPS * 32, 0, s>>>(d, c); break;
-    case 7: k_pair_f2<6><<<fb, PF_WARPS * 32, 0, s>>>(d, c); break;
-    case 8: k_pair_f2<7><<<fb, PF_WARPS * 32, 0, s>>>(d, c); break;
+    case 6: case 7: case 8: {
+      // persistent grid: as many blocks as can be resident, sized from the SM
+      // count; the counter hands out the i-clusters
+      const int minb = variant - 1;
+      const unsigned pb = std::min(fb, (unsigned)(d.n_sm * minb));
+      cudaMemsetAsync(d.pair_next, 0, sizeof(unsigned), s);
+      if (variant == 6) k_pair_f2<5><<<pb, PF_WARPS * 32, 0, s>>>(d, c, d.pair_next);
+      else if (variant == 7) k_pair_f2<6><<<pb, PF_WARPS * 32, 0, s>>>(d, c, d.pair_next);
+      else k_pair_f2<7><<<pb, PF_WARPS * 32, 0, s>>>(d, c, d.pair_next);
+      break;
+    }
     default: k_pair_f<4, false, MAX_TYPES><<<fb, PF_WARPS * 32, 0, s>>>(d, c); break;
   }
 }
