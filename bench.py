@@ -34,10 +34,10 @@ BYTES_PER_ATOM_STEP = 1224.0         # 112 B of state + 278 int32 half-list entr
 PAIRS_PER_ATOM_STEP = 209.0          # half pairs inside r_cut = 1.0 nm
 FLOPS_PER_PAIR = 35.0                # LJ + reaction field, FP32
 # DRAM traffic of one pair-kernel launch on this workload (dram__bytes_read.sum +
-# dram__bytes_write.sum of one ncu capture, variant 7) and the kernel source it
+# dram__bytes_write.sum of one ncu capture, variant 8) and the kernel source it
 # was taken on: reported as roofline.traffic only while that source is unchanged
-PAIR_TRAFFIC = {"bytes": 147.983104e6 + 11.118848e6, "variant": 7,
-                "source_sha256": "c9802e988bc3676dddaae633648004515c25272ad610bb6e55c868533297e9b4"}
+PAIR_TRAFFIC = {"bytes": 148.0192e6 + 11.66336e6, "variant": 8,
+                "source_sha256": "08460dab7c7a81fd3b8c655d03b1311dbb4f5de78aa9ce69a2832d4a7d4416b4"}
 
 
 def pair_traffic():
@@ -337,7 +337,7 @@ def run_gpu(args):
                        "l2": "working set > L2 (lists + state ~0.5 GB)"},
             "roofline": {"bound": "alu", "kernel": "pair", "achieved": achieved / 1e12, "peak": fp32_peak / 1e12,
                          "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": pair_traffic(),
-                         "traffic_unit": "bytes per launch (ncu, variant 7)",
+                         "traffic_unit": "bytes per launch (ncu, variant 8)",
                          "launch_ms": pair_avg_s * 1e3, "launches_timed": pair_n,
                          "launch_timing": "event-record nodes around each pair launch inside the replayed graphs of the timed region",
                          "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz (SM max clock of MEASURED_PEAKS.json)",
