@@ -270,10 +270,11 @@ constexpr int CAND_MAX = 1024;  // candidate 4-atom j-clusters per i-cluster (bo
 // the entry's mask, image code and exact flag; entries are written in
 // candidate order (deterministic).  Phase 3: the i-atoms' exclusions clear
 // their bits in the written entries (found by binary search).
-__global__ void __launch_bounds__(LIST_WARPS * 32, 5) k_list(Dev d, SimConst c, float rl2_bbox) {
+__global__ void __launch_bounds__(LIST_WARPS * 32, 8) k_list(Dev d, SimConst c, float rl2_bbox) {
   __shared__ int s_cand[LIST_WARPS][CAND_MAX];
   __shared__ int s_excl[LIST_WARPS][CL][MAX_EXCL];
   __shared__ int s_nex[LIST_WARPS][CL];
+  __shared__ float4 s_xi[LIST_WARPS][CL];
   const int wib = threadIdx.x >> 5;
   const int I = blockIdx.x * LIST_WARPS + wib;
   const int lane = threadIdx.x & 31;
@@ -357,13 +358,9 @@ __global__ void __launch_bounds__(LIST_WARPS * 32, 5) k_list(Dev d, SimConst c, 
     overflow = true;
     n_cand = CAND_MAX;
   }
-  // i-atoms and their exclusions
-  float xi[CL], yi[CL], zi[CL];
-#pragma unroll
-  for (int a = 0; a < CL; ++a) {
-    const float4 p = d.pos[I * CL + a];
-    xi[a] = p.x; yi[a] = p.y; zi[a] = p.z;
-  }
+  // i-atoms (shared memory: broadcast reads leave registers for more resident
+  // warps) and their exclusions
+  if (lane < CL) s_xi[wib][lane] = d.pos[I * CL + lane];
   if (lane < CL) {
     const int o = d.orig[I * CL + lane];
     const int sa = T.sysatom0 + (o < 0 ? 0 : o);
@@ -401,9 +398,10 @@ __global__ void __launch_bounds__(LIST_WARPS * 32, 5) k_list(Dev d, SimConst c, 
           const float4 pj = d.pos[sj0 + b];
 #pragma unroll
           for (int a = 0; a < CL; ++a) {
-            const float dx = __fsub_rn(__fsub_rn(pj.x, xi[a]), sx);
-            const float dy = __fsub_rn(__fsub_rn(pj.y, yi[a]), sy);
-            const float dz = __fsub_rn(__fsub_rn(pj.z, zi[a]), sz);
+            const float4 ia = s_xi[wib][a];
+            const float dx = __fsub_rn(__fsub_rn(pj.x, ia.x), sx);
+            const float dy = __fsub_rn(__fsub_rn(pj.y, ia.y), sy);
+            const float dz = __fsub_rn(__fsub_rn(pj.z, ia.z), sz);
             const float r2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
             if (r2 < rl2) mask |= 1u << (a * CJ + b);
           }
