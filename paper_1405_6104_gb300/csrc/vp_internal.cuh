@@ -167,12 +167,13 @@ __device__ __forceinline__ ff two_prod(float a, float b) {
   float p = __fmul_rn(a, b);
   return {p, __fmaf_rn(a, b, -p)};
 }
+// sum with one TwoSum of the leading parts and the trailing parts added in
+// FP32 (the "sloppy" double-single sum): relative error about 2^-44 without
+// cancellation, absolute error below ulp(max(|x|, |y|)) * 2^-22 with it --
+// ample for sums whose required accuracy is absolute (z to ~1e-9 per term)
 __device__ __forceinline__ ff ff_add(ff x, ff y) {
   ff s = two_sum(x.hi, y.hi);
-  ff t = two_sum(x.lo, y.lo);
-  s.lo = __fadd_rn(s.lo, t.hi);
-  s = fast_two_sum(s.hi, s.lo);
-  s.lo = __fadd_rn(s.lo, t.lo);
+  s.lo = __fadd_rn(s.lo, __fadd_rn(x.lo, y.lo));
   return fast_two_sum(s.hi, s.lo);
 }
 __device__ __forceinline__ ff ff_add_f(ff x, float y) {
