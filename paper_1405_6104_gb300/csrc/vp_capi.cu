@@ -649,6 +649,7 @@ VP_API int sim_create(const sim_system *systems, int32_t n_systems, const int32_
     r |= upload(h, &d.work_order, order);
   }
   r |= dalloc(h, &d.cnat, tiles.size() * CV_T * CV_T);
+  r |= dalloc(h, &d.cnat_ff, tiles.size() * CV_T * CV_T);
   r |= upload(h, &d.sys_ncv, ncv_v);
   r |= upload(h, &d.sys_minsep, ms_v);
   r |= upload(h, &d.ljtab, ljtab);

@@ -48,6 +48,8 @@ __global__ void k_cnat(Dev d, SimConst c, const double *native, const int32_t *s
       v = C * S;
     }
     d.cnat[(size_t)tile * CV_T * CV_T + k * CV_T + lane] = v;
+    const float hi = (float)v;
+    d.cnat_ff[(size_t)tile * CV_T * CV_T + k * CV_T + lane] = make_float2(hi, (float)(v - (double)hi));
   }
 }
 
@@ -124,7 +126,7 @@ __global__ void __launch_bounds__(CV_WARPS * 32) k_cv(Dev d, SimConst c) {
   __syncwarp();
   // ---- phase 2: the near pairs, densely ----
   const CvConst k = cv_const(c);
-  const double *cn = d.cnat + (size_t)wk.y * CV_T * CV_T;
+  const float2 *cn = d.cnat_ff + (size_t)wk.y * CV_T * CV_T;
   ff zacc = {0.f, 0.f};
   for (int base = 0; base < n_near; base += 32) {
     const int idx = base + lane;
@@ -134,12 +136,13 @@ __global__ void __launch_bounds__(CV_WARPS * 32) k_cv(Dev d, SimConst c) {
       const float3 pi = make_float3(s_x[wib][il][0], s_x[wib][il][1], s_x[wib][il][2]);
       ff dx, dy, dz;
       cv_delta(pi, s_x[wib][CV_T + jc][0], s_x[wib][CV_T + jc][1], s_x[wib][CV_T + jc][2], L, iL, dx, dy, dz);
-      const ff cnat = ff_from_d(cn[((jc - il) & (CV_T - 1)) * CV_T + il]);
+      const float2 cv2 = cn[((jc - il) & (CV_T - 1)) * CV_T + il];
+      const ff cnat = {cv2.x, cv2.y};
       const ff r2 = ff_add(ff_add(ff_sqr(dx), ff_sqr(dy)), ff_sqr(dz));
       const CvPair cp = cv_contact<false>(r2, k);
       const ff h = ff_add(cp.Ct, ff_neg(cnat));
       // z term: C~ (C~ - 2 C~_nat) = (C~ - C~_nat)^2 - C~_nat^2
-      zacc = ff_add(zacc, ff_mul(cp.Ct, ff_add(cp.Ct, ff_neg(ff_mul_f(cnat, 2.0f)))));
+      zacc = ff_add(zacc, ff_mul(cp.Ct, ff_add(cp.Ct, ff{-2.0f * cnat.hi, -2.0f * cnat.lo})));  // doubling is exact
       // dz/dx_i = -w d, dz/dx_j = +w d with d = x_j - x_i, w = 2 h C~'(r)/r
       const float wgt = 2.0f * h.hi * cp.dCt / cp.r;
       if (wgt != 0.0f) {

@@ -41,6 +41,7 @@ struct Dev {
   int2 *work;                          // flat (trial, global tile) work items
   int32_t *work_order;                 // the order warps take them: tiles near the diagonal (most near pairs) first
   double *cnat;                        // [tiles * 1024] C~ of the native structure in tile-skew order
+  float2 *cnat_ff;                     // the same as float-float (hi, lo), read by the per-step kernel
   int32_t *sys_ncv, *sys_minsep;
   // Lennard-Jones pair table over de-duplicated types
   float2 *ljtab;                       // (6 c6, 12 c12)
