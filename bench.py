@@ -443,14 +443,120 @@ def run_toy(args):
     return 0
 
 
+def run_adjoint(args):
+    """Row a9 at its configuration: the functional's gradient along a
+    500-frame path of the 30 000-atom system (1800-atom solute), checkpoints
+    every 50 steps.  One bench step = forward 500 steps with checkpoints,
+    the coefficients, the reverse sweep (each segment restored and replayed
+    with the frame recorder, then the adjoint kernels)."""
+    import torch
+    rank, world, local = rank_info()
+    torch.cuda.set_device(local)
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1405_6104_gb300 import binding as B
+    from paper_1405_6104_gb300 import systems as S
+    from paper_1405_6104_gb300.adjoint import trajectory_adjoint
+    s, p = S.adjoint_30k(3)
+    p.k_ratchet = 5.0
+    n_frames, every = 500, 50
+    with B.TrialBatch(s, p, [1], trial_seeds=[3]) as b:
+        B.sim_autotune(b.h, 3, None)
+        stream = torch.cuda.ExternalStream(b.stream)
+        for _ in range(args.warmup):
+            trajectory_adjoint(b, 0, n_frames, every=every)
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0 = time.perf_counter()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            phi, G, _ = trajectory_adjoint(b, 0, n_frames, every=every)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        ms = ev0.elapsed_time(ev1)
+        # where the time goes: one more run with per-kernel timing
+        B.sim_set_timing(b.h, 1)
+        B.sim_kernel_times(b.h)
+        t1 = time.perf_counter()
+        trajectory_adjoint(b, 0, n_frames, every=every)
+        t_kt = time.perf_counter() - t1
+        kt = B.sim_kernel_times(b.h)
+        B.sim_set_timing(b.h, 0)
+    md_ms = sum(v[0] for v in kt.values())
+    line = {
+        "metric": "adjoint frames/s (gradient of the functional along a path, checkpointed replay)",
+        "value": n_frames * args.steps / (ms * 1e-3), "unit": "frames/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+i64-fixed+ff-cv", "data": "synthetic",
+        "config": {"workload": f"30 000 atoms (1800-atom solute, 9400 waters), {n_frames} frames (1 per step), "
+                               f"checkpoints every {every} steps, k_R 5", "phi": float(phi),
+                   "grad_max": float(np.abs(G).max())},
+        "wall_s_per_step": wall / args.steps,
+        "md_kernels_ms_per_step": md_ms,
+        "md_kernel_share": md_ms / (t_kt * 1e3),
+        "kernel_ms": {k: v[0] / v[1] for k, v in kt.items() if v[1] > 0},
+        "note": "1000 MD steps (forward + replay) of the 30 000-atom system per bench step; the rest is the "
+                "adjoint kernels, checkpoint transfers and the host loop",
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def run_similarity(args):
+    """Row f3: path similarity of every pair of 64 trial paths of the
+    11 040-atom system (23 160 native contacts), from formation times
+    tracked on the GPU during 100 steps."""
+    import torch
+    rank, world, local = rank_info()
+    torch.cuda.set_device(local)
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1405_6104_gb300 import binding as B
+    from paper_1405_6104_gb300 import systems as S
+    s, p, seeds = S.batched_64(1)
+    with B.TrialBatch(s, p, [len(seeds)], trial_seeds=seeds) as b:
+        B.sim_contact_tracking(b.h, 10)
+        b.step(100)
+        n_c = len(B.sim_native_contacts(b.h, 0))
+        T = np.stack([B.sim_contact_times(b.h, t, n_c) for t in range(len(seeds))])
+    pairs = [(a, c) for a in range(len(seeds)) for c in range(a + 1, len(seeds))]
+    stream = torch.cuda.Stream()
+    for _ in range(args.warmup):
+        B.path_similarity(T, pairs, cuda_stream=stream.cuda_stream)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        sim = B.path_similarity(T, pairs, cuda_stream=stream.cuda_stream)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    comparisons = float(len(pairs)) * n_c * (n_c - 1)
+    line = {
+        "metric": "path-similarity comparisons/s (ordered contact pairs x path pairs)",
+        "value": comparisons / (ms * 1e-3), "unit": "comparisons/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "int64", "data": "synthetic",
+        "config": {"workload": f"{len(seeds)} trials x 11 040 atoms, {n_c} native contacts, {len(pairs)} path pairs "
+                               f"(formation times from 100 tracked steps)", "s_mean": float(np.mean(sim)),
+                   "s_min": float(np.min(sim)), "s_max": float(np.max(sim))},
+        "note": "one call uploads the times, compares all ordered contact pairs of every path pair and reads back s",
+    }
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
-    ap.add_argument("--workload", default="batched64", choices=["batched64", "toy2d"],
-                    help="batched64: the 64 x 11 040-atom trial batch (default); toy2d: the 2-D toy model's K_R scan")
+    ap.add_argument("--workload", default="batched64", choices=["batched64", "toy2d", "adjoint30k", "similarity"],
+                    help="batched64: the 64 x 11 040-atom trial batch (default); toy2d: the 2-D toy model's K_R "
+                         "scan; adjoint30k: the functional's gradient along a 500-frame path of 30 000 atoms; "
+                         "similarity: path similarity over 64 trial paths")
     ap.add_argument("--pair-variant", type=int, default=None, help="fix the pair-kernel variant (skip autotuning)")
     ap.add_argument("--cv-variant", type=int, default=None, help="fix the reaction-coordinate kernel variant")
     ap.add_argument("--prep-steps", type=int, default=3000,
@@ -462,6 +568,10 @@ def main():
         return run_reference(args)
     if args.workload == "toy2d":
         return run_toy(args)
+    if args.workload == "adjoint30k":
+        return run_adjoint(args)
+    if args.workload == "similarity":
+        return run_similarity(args)
     return run_gpu(args)
 
 

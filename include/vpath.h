@@ -295,7 +295,8 @@ int sim_contact_times(sim_handle *h, int32_t trial, int64_t *times, int64_t cap)
 /* Path similarity on the GPU: times [n_paths][n_c] formation times (HOST,
  * read), pairs [2*n_pairs] path indices (HOST), s [n_pairs] (HOST, written):
  * s(pairs[2q], pairs[2q+1]).  n_c < 2 gives 1 (no ordered pair).  At most
- * 65535 pairs per call.  Returns SIM_OK, SIM_EINVAL or SIM_ECUDA. */
+ * 65535 pairs per call; times must be below 2^31 - 1 (steps).  Returns
+ * SIM_OK, SIM_EINVAL or SIM_ECUDA. */
 int path_similarity(const int64_t *times, int32_t n_paths, int64_t n_c, const int32_t *pairs, int32_t n_pairs,
                     double *s, void *cuda_stream, char *errbuf, int32_t errlen);
 

@@ -72,39 +72,44 @@ void launch_contacts(const Dev &d, const ContactDev &c, cudaStream_t s) {
 
 namespace {
 
-constexpr int SIM_TILE = 1024;
+constexpr int SIM_TILE = 2048;
 
-__device__ __forceinline__ long long order_key(long long t) { return t < 0 ? LLONG_MAX : t; }
+// formation steps as 32-bit order keys: -1 (not formed) orders last; the
+// caller guarantees steps below 2^31 - 1
+__device__ __forceinline__ int order_key(long long t) { return t < 0 ? INT_MAX : (int)t; }
+
+// sign of a - b in {-1, 0, 1} for keys of the same sign class (no overflow: 0 <= keys <= INT_MAX)
+__device__ __forceinline__ int cmp3(int a, int b) { return (a > b) - (a < b); }
 
 // one (path pair, block of i) per block: counts the ordered pairs (i != j)
 // on which the two paths' order relations agree
 __global__ void __launch_bounds__(256) k_similarity(const long long *__restrict__ t, long long n_c,
                                                     const int2 *__restrict__ pp, unsigned long long *count) {
-  __shared__ long long sa[SIM_TILE], sb[SIM_TILE];
+  __shared__ int2 sab[SIM_TILE];
   __shared__ unsigned long long red[256];
   const int2 ab = pp[blockIdx.y];
   const long long *ta = t + (size_t)ab.x * (size_t)n_c, *tb = t + (size_t)ab.y * (size_t)n_c;
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const long long ai = i < n_c ? order_key(ta[i]) : 0, bi = i < n_c ? order_key(tb[i]) : 0;
-  unsigned long long cnt = 0;
+  const int ai = i < n_c ? order_key(ta[i]) : 0, bi = i < n_c ? order_key(tb[i]) : 0;
+  unsigned int cnt = 0;  // per thread: at most n_c < 2^31
   for (long long j0 = 0; j0 < n_c; j0 += SIM_TILE) {
     __syncthreads();
     for (int q = threadIdx.x; q < SIM_TILE; q += blockDim.x) {
       const long long j = j0 + q;
-      sa[q] = j < n_c ? order_key(ta[j]) : 0;
-      sb[q] = j < n_c ? order_key(tb[j]) : 0;
+      sab[q] = j < n_c ? make_int2(order_key(ta[j]), order_key(tb[j])) : make_int2(0, 0);
     }
     __syncthreads();
     if (i < n_c) {
       const int m = (int)(n_c - j0 < SIM_TILE ? n_c - j0 : SIM_TILE);
+#pragma unroll 4
       for (int q = 0; q < m; ++q) {
-        const int ca = (ai > sa[q]) - (ai < sa[q]), cb = (bi > sb[q]) - (bi < sb[q]);
-        cnt += (ca == cb) ? 1ull : 0ull;
+        const int2 v = sab[q];
+        cnt += cmp3(ai, v.x) == cmp3(bi, v.y) ? 1u : 0u;
       }
     }
   }
   // the diagonal (j = i) always agrees; it is not an ordered pair
-  if (i < n_c) cnt -= 1ull;
+  if (i < n_c) cnt -= 1u;
   red[threadIdx.x] = cnt;
   __syncthreads();
   for (int off = blockDim.x / 2; off > 0; off >>= 1) {
@@ -142,6 +147,8 @@ extern "C" __attribute__((visibility("default"))) int path_similarity(const int6
     return SIM_OK;
   }
   if (n_c > (1ll << 30)) return put_err(errbuf, errlen, SIM_EINVAL, "path_similarity: too many contacts");
+  for (size_t k = 0; k < (size_t)n_paths * (size_t)n_c; ++k)
+    if (times[k] >= (int64_t)INT_MAX) return put_err(errbuf, errlen, SIM_EINVAL, "path_similarity: step >= 2^31 - 1");
   if (n_pairs > 65535) return put_err(errbuf, errlen, SIM_EINVAL, "path_similarity: at most 65535 pairs per call");
   cudaStream_t st = (cudaStream_t)cuda_stream;
   long long *dt = nullptr;
