@@ -349,7 +349,7 @@ def run_gpu(args):
             "plain": plain,
             "cpu_baseline": cb,
             "e2e": e2e,
-            "gpu_launches": args.steps * (4 * nst + 5 + 1),
+            "gpu_launches": int(round(args.steps * sum(v[1] for v in kt.values()) / kt_steps)),
             "clocks": clk,
             "diagnostics": diag,
         }
