@@ -274,7 +274,7 @@ __global__ void __launch_bounds__(LIST_WARPS * 32, 8) k_list(Dev d, SimConst c, 
   __shared__ int s_cand[LIST_WARPS][CAND_MAX];
   __shared__ int s_excl[LIST_WARPS][CL][MAX_EXCL];
   __shared__ int s_nex[LIST_WARPS][CL];
-  __shared__ float4 s_xi[LIST_WARPS][CL];
+  __shared__ float4 s_xp[LIST_WARPS][CL / 2][2];  // i-atom pairs (2p, 2p+1): {-x, -x', -y, -y'} {-z, -z', 0, 0}
   const int wib = threadIdx.x >> 5;
   const int I = blockIdx.x * LIST_WARPS + wib;
   const int lane = threadIdx.x & 31;
@@ -360,7 +360,11 @@ __global__ void __launch_bounds__(LIST_WARPS * 32, 8) k_list(Dev d, SimConst c, 
   }
   // i-atoms (shared memory: broadcast reads leave registers for more resident
   // warps) and their exclusions
-  if (lane < CL) s_xi[wib][lane] = d.pos[I * CL + lane];
+  if (lane < CL / 2) {
+    const float4 a0 = d.pos[I * CL + 2 * lane], a1 = d.pos[I * CL + 2 * lane + 1];
+    s_xp[wib][lane][0] = make_float4(-a0.x, -a1.x, -a0.y, -a1.y);
+    s_xp[wib][lane][1] = make_float4(-a0.z, -a1.z, 0.f, 0.f);
+  }
   if (lane < CL) {
     const int o = d.orig[I * CL + lane];
     const int sa = T.sysatom0 + (o < 0 ? 0 : o);
@@ -392,18 +396,23 @@ __global__ void __launch_bounds__(LIST_WARPS * 32, 8) k_list(Dev d, SimConst c, 
       const float qly = rintf(__fmul_rn(__fsub_rn(jlo4.y, hi.y), iL)), qhy = rintf(__fmul_rn(__fsub_rn(jhi4.y, lo.y), iL));
       const float qlz = rintf(__fmul_rn(__fsub_rn(jlo4.z, hi.z), iL)), qhz = rintf(__fmul_rn(__fsub_rn(jhi4.z, lo.z), iL));
       if (qlx == qhx && qly == qhy && qlz == qhz) {
+        // two i-atoms per packed FP32x2 operation; every operation rounds on
+        // its own exactly as the per-pair rule does (d = xj + (-xi) is xj - xi)
         const float sx = __fmul_rn(L, qlx), sy = __fmul_rn(L, qly), sz = __fmul_rn(L, qlz);
+        const float2 nsx = make_float2(-sx, -sx), nsy = make_float2(-sy, -sy), nsz = make_float2(-sz, -sz);
 #pragma unroll
         for (int b = 0; b < CJ; ++b) {
           const float4 pj = d.pos[sj0 + b];
+          const float2 xj2 = make_float2(pj.x, pj.x), yj2 = make_float2(pj.y, pj.y), zj2 = make_float2(pj.z, pj.z);
 #pragma unroll
-          for (int a = 0; a < CL; ++a) {
-            const float4 ia = s_xi[wib][a];
-            const float dx = __fsub_rn(__fsub_rn(pj.x, ia.x), sx);
-            const float dy = __fsub_rn(__fsub_rn(pj.y, ia.y), sy);
-            const float dz = __fsub_rn(__fsub_rn(pj.z, ia.z), sz);
-            const float r2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
-            if (r2 < rl2) mask |= 1u << (a * CJ + b);
+          for (int p = 0; p < CL / 2; ++p) {
+            const float4 i0 = s_xp[wib][p][0], i1 = s_xp[wib][p][1];
+            const float2 dx = __fadd2_rn(__fadd2_rn(xj2, make_float2(i0.x, i0.y)), nsx);
+            const float2 dy = __fadd2_rn(__fadd2_rn(yj2, make_float2(i0.z, i0.w)), nsy);
+            const float2 dz = __fadd2_rn(__fadd2_rn(zj2, make_float2(i1.x, i1.y)), nsz);
+            const float2 r2 = __fadd2_rn(__fadd2_rn(__fmul2_rn(dx, dx), __fmul2_rn(dy, dy)), __fmul2_rn(dz, dz));
+            if (r2.x < rl2) mask |= 1u << (2 * p * CJ + b);
+            if (r2.y < rl2) mask |= 1u << ((2 * p + 1) * CJ + b);
           }
         }
         if (J8 == Il) {  // inside the i-cluster itself: pairs with the j slot above the i slot
