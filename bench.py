@@ -141,11 +141,18 @@ def equilibrate(B, S, s, p, steps: int = 3000, gamma: float = 20.0):
     return out
 
 
-def make_batch(B, S, prep_steps: int, stream_ptr=0):
+def make_batch(B, S, prep_steps: int, stream_ptr=0, rank: int = 0, world: int = 1):
+    """This rank's 64 trials of the weak-scaling batch: global trials
+    rank*64 .. rank*64+63 (shard_trials), Philox seeds 1000 + global index."""
+    from paper_1405_6104_gb300.shard import shard_trials
     s, p, seeds = S.batched_64(1)
+    trials = shard_trials(len(seeds) * world, world, rank)
+    seeds = [1000 + int(t) for t in trials]
     if prep_steps > 0:
         s = equilibrate(B, S, s, p, steps=prep_steps)
-    return s, p, seeds, B.TrialBatch(s, p, [len(seeds)], trial_seeds=seeds, cuda_stream=stream_ptr)
+    batch = B.TrialBatch(s, p, [len(seeds)], trial_seeds=seeds, cuda_stream=stream_ptr)
+    batch.global_trials = trials
+    return s, p, seeds, batch
 
 
 def cpu_baseline(S, steps: int = 60):
@@ -201,7 +208,7 @@ def run_gpu(args):
     from paper_1405_6104_gb300 import binding as B
     from paper_1405_6104_gb300 import systems as S
 
-    s, p, seeds, batch = make_batch(B, S, args.prep_steps)
+    s, p, seeds, batch = make_batch(B, S, args.prep_steps, rank=rank, world=world)
     n_trials = len(seeds)
     atoms = n_trials * s.n_atoms
     nst = p.nstlist
@@ -287,6 +294,11 @@ def run_gpu(args):
     e2e = {"value": world * atoms * nst * e2e_steps / (t1 - t0), "unit": "atom-steps/s",
            "h2d_bytes_per_step": int(P.nbytes + V.nbytes), "d2h_bytes_per_step": int(phi.nbytes + 4 + 4)}
     diag = B.sim_diagnostics(batch.h)
+    # the method's selection over every rank's trials: one double per trial
+    # gathered on the host (outside the timed region)
+    from paper_1405_6104_gb300.shard import global_selection
+    phi_loc, _ = batch.bias_functional()
+    sel_trial, sel_phi = global_selection(phi_loc, batch.global_trials)
     batch.close()
 
     # plain: one trial of the same system on the same kernels (graph replay),
@@ -352,6 +364,7 @@ def run_gpu(args):
             "gpu_launches": int(round(args.steps * sum(v[1] for v in kt.values()) / kt_steps)),
             "clocks": clk,
             "diagnostics": diag,
+            "selection": {"trial": sel_trial, "phi": sel_phi, "over_trials": n_trials * world},
         }
         print(json.dumps(line))
     if world > 1:
