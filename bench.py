@@ -65,7 +65,7 @@ def peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons, sampled every 100 ms from before
+    """nvidia-smi clocks and throttle reasons, sampled every 50 ms from before
     the warm-up to after the kernel-timing pass; summarised over the samples
     whose timestamps fall inside the timed region (or, when that region is
     shorter than three sampling periods, over the whole loaded window)."""
@@ -79,7 +79,7 @@ class ClockSampler:
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
         try:
             self.p = subprocess.Popen(["nvidia-smi", f"--id={index}", f"--query-gpu={q}", "--format=csv,noheader,nounits",
-                                       "-lms", "100"], stdout=self.f, stderr=subprocess.DEVNULL)
+                                       "-lms", "50"], stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.p = None
         # wait (bounded) for the first sample so that the window is covered
@@ -341,7 +341,7 @@ def run_gpu(args):
         line = {
             "metric": METRIC, "value": value, "unit": "atom-steps/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32+i64-fixed+f64-cv", "data": "synthetic",
+            "vs_baseline": None, "dtype": "f32+i64-fixed+ff-cv", "data": "synthetic",
             "config": {"workload": WORKLOAD, "global_batch": n_trials * world, "atoms_per_trial": s.n_atoms,
                        "start": f"generated, relaxed {args.prep_steps} steps at gamma 20/ps (untimed)",
                        "md_steps_per_bench_step": nst, "parallelism": f"replicas x{world}",
