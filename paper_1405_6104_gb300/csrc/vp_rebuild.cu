@@ -40,14 +40,17 @@ __global__ void k_bin(Dev d, float half_skin2, int strict) {
     atomicAdd(reinterpret_cast<unsigned long long *>(d.skin_count), 1ull);
     if (strict) atomicOr(d.err, ERR_SKIN);
   }
-  if (!(isfinite(x) && isfinite(y) && isfinite(z))) {
+  // a coordinate that is not finite, or so large that one wrap cannot bring
+  // it into the box (a run that has blown up), is an error; the atom is put
+  // at the origin so that every index below stays inside the grid
+  if (!(isfinite(x) && isfinite(y) && isfinite(z)) || !(x >= 0.0f && x < L && y >= 0.0f && y < L && z >= 0.0f && z < L)) {
     atomicOr(d.err, ERR_NONFINITE);
     x = y = z = 0.0f;
   }
   d.ref_pos[T.atom0 + o] = make_float4(x, y, z, 0.0f);
   d.pos[slot] = make_float4(x, y, z, p.w);
-  int cx = min((int)(x * T.inv_col_w), T.ncol - 1);
-  int cy = min((int)(y * T.inv_col_w), T.ncol - 1);
+  int cx = max(0, min((int)(x * T.inv_col_w), T.ncol - 1));
+  int cy = max(0, min((int)(y * T.inv_col_w), T.ncol - 1));
   int c = cx * T.ncol + cy;
   d.slot_col[slot] = c;
   atomicAdd(&d.col_count[T.col0 + c], 1);

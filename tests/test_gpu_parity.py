@@ -318,3 +318,30 @@ def test_set_state_rejects_non_finite_input_and_keeps_the_state():
         for x, y in zip(before, after):
             assert np.array_equal(x[0], y[0]) and np.array_equal(x[1], y[1])
         b.step(10)  # and the handle stays usable
+
+
+def test_strict_skin_violation_is_reported():
+    """With SIM_STRICT_SKIN an atom moving more than skin/2 between list
+    rebuilds ends the call with SIM_ESKIN (a 0.002 nm skin is crossed within
+    a list interval)."""
+    s, p = S.small_solvated()
+    p.skin = 0.002
+    p.flags = B.SIM_STRICT_SKIN
+    with B.TrialBatch(s, p, [1], trial_seeds=[9]) as b:
+        with pytest.raises(B.SimError) as e:
+            for _ in range(5):
+                b.step(10)
+        assert e.value.code == B.SIM_ESKIN
+
+
+def test_blow_up_is_reported_as_non_finite():
+    """A time step far beyond the stable one makes the run blow up; the
+    kernels flag the non-finite (or unwrappable) coordinates and the call
+    returns SIM_ENONFINITE instead of writing outside its grid."""
+    s, p = S.small_solvated()
+    p.dt = 0.05
+    with B.TrialBatch(s, p, [1], trial_seeds=[9]) as b:
+        with pytest.raises(B.SimError) as e:
+            for _ in range(50):
+                b.step(10)
+        assert e.value.code == B.SIM_ENONFINITE
