@@ -131,7 +131,7 @@ __global__ void k_colfill(Dev d) {
 // per column: sort by (z, atom index), write the new cluster layout, update
 // slot_of, pad the last cluster and compute cluster bounding boxes
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_colsort(Dev d) {
+__global__ void __launch_bounds__(128) k_colsort(Dev d) {
   __shared__ unsigned long long key[COL_CAP];
   __shared__ int s_old[COL_CAP];
   int cg = blockIdx.x;
@@ -487,7 +487,7 @@ void launch_colfill(const Dev &d, cudaStream_t s) {
   k_colfill<<<(d.total_slots + 255) / 256, 256, 0, s>>>(d);
 }
 void launch_colsort(const Dev &d, cudaStream_t s) {
-  k_colsort<<<d.total_cols, 256, 0, s>>>(d);
+  k_colsort<<<d.total_cols, 128, 0, s>>>(d);  // columns hold about 100 atoms: 128 threads keep every thread busy in the sort
   size_t n = (size_t)d.total_slots;
   cudaMemcpyAsync(d.pos, d.pos_b, n * sizeof(float4), cudaMemcpyDeviceToDevice, s);
   cudaMemcpyAsync(d.vel, d.vel_b, n * sizeof(float4), cudaMemcpyDeviceToDevice, s);
