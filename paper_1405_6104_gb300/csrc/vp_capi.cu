@@ -631,6 +631,11 @@ VP_API int sim_create(const sim_system *systems, int32_t n_systems, const int32_
   r |= dalloc(h, &d.z_part, work.size());
   r |= upload(h, &d.asys, asys);
   r |= upload(h, &d.gm, gm);
+  {
+    std::vector<double> igm(gm.size());
+    for (size_t k = 0; k < gm.size(); ++k) igm[k] = std::isfinite(gm[k]) ? 1.0 / gm[k] : 0.0;
+    r |= upload(h, &d.inv_gm, igm);
+  }
   r |= upload(h, &d.excl, excl);
   r |= upload(h, &d.excl_n, excl_n);
   r |= upload(h, &d.bt_start, bt_start);

@@ -189,7 +189,7 @@ __global__ void __launch_bounds__(256) k_cvfin(Dev d, SimConst c) {
     double gx = (double)d.gx[T.cv0 + i] * 2.3283064365386963e-10;
     double gy = (double)d.gy[T.cv0 + i] * 2.3283064365386963e-10;
     double gz = (double)d.gz[T.cv0 + i] * 2.3283064365386963e-10;
-    q += (gx * gx + gy * gy + gz * gz) / d.gm[T.sysatom0 + i];
+    q += (gx * gx + gy * gy + gz * gz) * d.inv_gm[T.sysatom0 + i];  // FP64 division is slow on this part
   }
   rz[threadIdx.x] = zs;
   rq[threadIdx.x] = q;

@@ -33,6 +33,7 @@ struct Dev {
   // per system, caller-ordered
   AtomSys *asys;
   double *gm;                          // gamma_i m_i
+  double *inv_gm;                      // 1 / (gamma_i m_i) (0 without friction)
   int32_t *excl, *excl_n;              // [sys atoms * MAX_EXCL], counts
   int32_t *bt_start;                   // [total system atoms + 1] CSR of owner-computed bonded terms
   BTerm *bterm;
