@@ -34,6 +34,11 @@ struct sim_handle {
   cudaStream_t stream = nullptr;
   cudaStream_t caller = nullptr;
   cudaEvent_t entry_ev = nullptr;
+  // second stream of the captured chunk: the reaction coordinate (CV and its
+  // finaliser) reads only positions, so it runs beside the list build and the
+  // pair forces, joined before the next update
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   Dev d{};
   SimConst c{};
   sim_params params{};
@@ -180,16 +185,25 @@ int harvest_graph_timers(sim_handle *h) {
   return SIM_OK;
 }
 
-void rebuild(sim_handle *h) {
+// cell binning and the spatial sort (the new atom slots)
+void rebuild_cols(sim_handle *h) {
   cudaStream_t s = h->stream;
   timed(h, "bin", [&] { launch_bin(h->d, h->c, h->half_skin2, h->strict_skin, s); });
   timed(h, "colscan", [&] { launch_colscan(h->d, s); });
   timed(h, "colfill", [&] { launch_colfill(h->d, s); });
   timed(h, "colsort", [&] { launch_colsort(h->d, s); });
-  timed(h, "list", [&] { launch_list(h->d, h->c, h->rl2_bbox, s); });
 }
 
-void forces(sim_handle *h, FinMode mode) {
+void rebuild_list(sim_handle *h) {
+  timed(h, "list", [&] { launch_list(h->d, h->c, h->rl2_bbox, h->stream); });
+}
+
+void rebuild(sim_handle *h) {
+  rebuild_cols(h);
+  rebuild_list(h);
+}
+
+void pair_forces(sim_handle *h) {
   cudaStream_t s = h->stream;
   if (h->gtiming && h->cap_k >= 0) {
     cudaEventRecordWithFlags(h->gev[2 * h->cap_k], s, cudaEventRecordExternal);  // a failure ends the capture
@@ -198,15 +212,45 @@ void forces(sim_handle *h, FinMode mode) {
   } else {
     timed(h, "pair", [&] { launch_pair(h->d, h->c, false, -1, s, h->pair_variant); });
   }
+}
+
+void cv_forces(sim_handle *h, FinMode mode, cudaStream_t s) {
   timed(h, "cv", [&] { launch_cv(h->d, h->c, s, h->cv_variant); });
   timed(h, "cvfin", [&] { launch_cvfin(h->d, h->c, mode, s); });
+}
+
+// what follows the forces: contact tracking and the frame recorder read the
+// step counter that the CV finaliser has advanced
+void after_forces(sim_handle *h, FinMode mode) {
+  cudaStream_t s = h->stream;
   if (mode == FIN_STEP && h->cdev.every > 0) launch_contacts(h->d, h->cdev, s);
   if (h->frames)
     launch_rec_frames(h->d, h->frame_trial, h->tinfo[h->frame_trial].n_cv, h->frame_cap, h->frames, s);
 }
 
+void forces(sim_handle *h, FinMode mode) {
+  pair_forces(h);
+  cv_forces(h, mode, h->stream);
+  after_forces(h, mode);
+}
+
 void one_step(sim_handle *h, bool with_rebuild) {
   timed(h, "update", [&] { launch_update(h->d, h->c, UPD_DRIFT, h->stream); });
+  if (h->cap_k >= 0 && h->side && !h->timing) {
+    // captured chunk: the CV branch forks once the atoms have their slots
+    // (it reads positions through slot_of) and joins before the next update;
+    // the pair kernel and the list build never touch what it writes
+    if (with_rebuild) rebuild_cols(h);
+    cudaEventRecord(h->ev_fork, h->stream);
+    cudaStreamWaitEvent(h->side, h->ev_fork, 0);
+    cv_forces(h, FIN_STEP, h->side);
+    cudaEventRecord(h->ev_join, h->side);
+    if (with_rebuild) rebuild_list(h);
+    pair_forces(h);
+    cudaStreamWaitEvent(h->stream, h->ev_join, 0);
+    after_forces(h, FIN_STEP);
+    return;
+  }
   if (with_rebuild) rebuild(h);
   forces(h, FIN_STEP);
 }
@@ -332,6 +376,10 @@ VP_API int sim_create(const sim_system *systems, int32_t n_systems, const int32_
   if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess)
     return bail(fail(h, SIM_ECUDA, "cudaStreamCreate failed"));
   cudaEventCreateWithFlags(&h->entry_ev, cudaEventDisableTiming);
+  if (cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) != cudaSuccess)
+    return bail(fail(h, SIM_ECUDA, "cudaStreamCreate / cudaEventCreate failed"));
   h->caller = (cudaStream_t)cuda_stream;
   h->n_sys = n_systems;
   h->n_trials = total_trials;
@@ -1365,6 +1413,9 @@ VP_API void sim_destroy(sim_handle *h) {
   for (auto &t : h->timers)
     for (auto &pr : t.ev) { cudaEventDestroy(pr.first); cudaEventDestroy(pr.second); }
   if (h->entry_ev) cudaEventDestroy(h->entry_ev);
+  if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+  if (h->ev_join) cudaEventDestroy(h->ev_join);
+  if (h->side) cudaStreamDestroy(h->side);
   if (h->stream) cudaStreamDestroy(h->stream);
   delete h;
 }
