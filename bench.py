@@ -297,6 +297,8 @@ def run_gpu(args):
     e2e = {"value": world * atoms * nst * e2e_steps / (t1 - t0), "unit": "atom-steps/s",
            "h2d_bytes_per_step": int(P.nbytes + V.nbytes), "d2h_bytes_per_step": int(phi.nbytes + 4 + 4)}
     diag = B.sim_diagnostics(batch.h)
+    # 8 x 4 atom pairs per list entry, masked pairs included
+    diag["pairs_evaluated_per_atom_step"] = round(32.0 * diag["list_entries"] / atoms, 1)
     # the method's selection over every rank's trials: one double per trial
     # gathered on the host (outside the timed region)
     from paper_1405_6104_gb300.shard import global_selection

@@ -203,8 +203,10 @@ int phi_frames_refine(sim_handle *h, int32_t trial, double *frames, int32_t n_fr
  * sim_pairlist: the atom pairs (i < j, caller's indices) that the current
  *   cluster lists hold for one trial (list rule at the last rebuild);
  *   *n_pairs receives the count, pairs beyond cap are dropped.
- * sim_diagnostics: out[4] = {skin violations counted, max list entries of a
- *   cluster, list capacity per cluster, clusters in use (all trials)}. */
+ * sim_diagnostics: out[5] = {skin violations counted, max list entries of a
+ *   cluster, list capacity per cluster, clusters in use (all trials), list
+ *   entries in use (all trials; each holds 8 x 4 atom pairs, so 32 times this
+ *   over the atoms is the pair evaluations per atom-step)}. */
 int sim_pairlist(sim_handle *h, int32_t trial, int32_t *pairs, int64_t cap, int64_t *n_pairs);
 int sim_diagnostics(sim_handle *h, int64_t *out);
 

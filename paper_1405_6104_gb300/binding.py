@@ -293,10 +293,10 @@ def sim_pairlist(h, trial: int, cap: int = 0):
 
 
 def sim_diagnostics(h):
-    out = np.zeros(4, np.int64)
+    out = np.zeros(5, np.int64)
     _check(h, load().sim_diagnostics(h, out.ctypes.data))
     return dict(skin_violations=int(out[0]), max_list_entries=int(out[1]), list_capacity=int(out[2]),
-                clusters=int(out[3]))
+                clusters=int(out[3]), list_entries=int(out[4]))
 
 
 def sim_autotune(h, reps: int = 5, cache_path: Optional[str] = None):

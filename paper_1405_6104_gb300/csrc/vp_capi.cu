@@ -198,11 +198,6 @@ void rebuild_list(sim_handle *h) {
   timed(h, "list", [&] { launch_list(h->d, h->c, h->rl2_bbox, h->stream); });
 }
 
-void rebuild(sim_handle *h) {
-  rebuild_cols(h);
-  rebuild_list(h);
-}
-
 void pair_forces(sim_handle *h) {
   cudaStream_t s = h->stream;
   if (h->gtiming && h->cap_k >= 0) {
@@ -228,31 +223,33 @@ void after_forces(sim_handle *h, FinMode mode) {
     launch_rec_frames(h->d, h->frame_trial, h->tinfo[h->frame_trial].n_cv, h->frame_cap, h->frames, s);
 }
 
-void forces(sim_handle *h, FinMode mode) {
-  pair_forces(h);
-  cv_forces(h, mode, h->stream);
+// forces of the current positions, after an optional list rebuild.  Unless
+// kernels are being timed one by one, the reaction coordinate (CV and its
+// finaliser) runs on a second stream once the atoms have their slots (it
+// reads positions through slot_of) and joins before anything that follows:
+// the list build and the pair kernel write nothing it reads.  All force and
+// gradient sums are fixed-point, so both orders give bit-identical states.
+void forces(sim_handle *h, FinMode mode, bool with_rebuild) {
+  if (with_rebuild) rebuild_cols(h);
+  if (h->side && !h->timing) {
+    cudaEventRecord(h->ev_fork, h->stream);
+    cudaStreamWaitEvent(h->side, h->ev_fork, 0);
+    cv_forces(h, mode, h->side);
+    cudaEventRecord(h->ev_join, h->side);
+    if (with_rebuild) rebuild_list(h);
+    pair_forces(h);
+    cudaStreamWaitEvent(h->stream, h->ev_join, 0);
+  } else {
+    if (with_rebuild) rebuild_list(h);
+    pair_forces(h);
+    cv_forces(h, mode, h->stream);
+  }
   after_forces(h, mode);
 }
 
 void one_step(sim_handle *h, bool with_rebuild) {
   timed(h, "update", [&] { launch_update(h->d, h->c, UPD_DRIFT, h->stream); });
-  if (h->cap_k >= 0 && h->side && !h->timing) {
-    // captured chunk: the CV branch forks once the atoms have their slots
-    // (it reads positions through slot_of) and joins before the next update;
-    // the pair kernel and the list build never touch what it writes
-    if (with_rebuild) rebuild_cols(h);
-    cudaEventRecord(h->ev_fork, h->stream);
-    cudaStreamWaitEvent(h->side, h->ev_fork, 0);
-    cv_forces(h, FIN_STEP, h->side);
-    cudaEventRecord(h->ev_join, h->side);
-    if (with_rebuild) rebuild_list(h);
-    pair_forces(h);
-    cudaStreamWaitEvent(h->stream, h->ev_join, 0);
-    after_forces(h, FIN_STEP);
-    return;
-  }
-  if (with_rebuild) rebuild(h);
-  forces(h, FIN_STEP);
+  forces(h, FIN_STEP, with_rebuild);
 }
 
 int check_flags(sim_handle *h) {
@@ -745,8 +742,7 @@ VP_API int sim_create(const sim_system *systems, int32_t n_systems, const int32_
   launch_cnat(d, c, d_native, d_nat0, (int)tiles.size(), d_tsys, st);
   launch_zconst(d, d_st0, d_snt, st);
   launch_init_vel(d, (float)kT, d_need, st);
-  rebuild(h);
-  forces(h, FIN_INIT);
+  forces(h, FIN_INIT, true);
   if (cudaStreamSynchronize(st) != cudaSuccess || cudaGetLastError() != cudaSuccess)
     return bail(fail(h, SIM_ECUDA, std::string("initialisation kernels failed: ") +
                                        cudaGetErrorString(cudaGetLastError())));
@@ -905,8 +901,7 @@ VP_API int sim_set_state(sim_handle *h, int32_t trial, const double *pos, const 
   CK(cudaMemsetAsync(d.err, 0, sizeof(int), h->stream));
   float half = 0.5f;
   CK(cudaMemcpyAsync(d.kick, &half, sizeof(float), cudaMemcpyHostToDevice, h->stream));
-  rebuild(h);
-  forces(h, FIN_RESTORE);
+  forces(h, FIN_RESTORE, true);
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(h->stream));
   return check_flags(h);
@@ -1213,12 +1208,14 @@ VP_API int sim_diagnostics(sim_handle *h, int64_t *out) {
   CK(cudaStreamSynchronize(h->stream));
   int mx = 0;
   for (int v : ln) mx = std::max(mx, v);
-  long long used = 0;
+  long long used = 0, entries = 0;
   for (auto &s : S) used += s.n_clus;
+  for (int v : ln) entries += v;
   out[0] = skin;
   out[1] = mx;
   out[2] = h->c.list_cap;
   out[3] = used;
+  out[4] = entries;
   return SIM_OK;
 }
 

@@ -67,6 +67,9 @@ def test_pairlist_bitexact(name):
             ref = {tuple(x) for x in O.pairlist(s, pos.astype(np.float32), p.r_cut + p.skin).tolist()}
             assert len(gpu) == len(B.sim_pairlist(b.h, 0))  # no duplicates
             assert gpu == ref
+            # every listed pair sits in one 8 x 4 entry
+            n_ent = B.sim_diagnostics(b.h)["list_entries"]
+            assert 0 < n_ent and len(gpu) <= 32 * n_ent
 
 
 @pytest.mark.parametrize("name", list(SYSTEMS))
