@@ -102,7 +102,8 @@ typedef struct sim_params {
 } sim_params;
 
 /* Creates a batch: trials_per_system[s] independent trials of each system
- * (trial seeds from trial_seeds[total trials] or params->seed + t).  Uploads
+ * (1 to 65535 trials in all; SIM_EINVAL otherwise) (trial seeds from
+ * trial_seeds[total trials] or params->seed + t).  Uploads
  * the systems, draws velocities where vel is NULL, builds cells and lists,
  * computes the first forces and sets z_m = z(X_0), Phi = 0 for every trial.
  * cuda_stream: the caller's stream (or NULL); the library orders its own

@@ -209,7 +209,10 @@ void pair_forces(sim_handle *h) {
   }
 }
 
+// the second branch of a force evaluation: bonded forces, then the reaction
+// coordinate and its finaliser
 void cv_forces(sim_handle *h, FinMode mode, cudaStream_t s) {
+  timed(h, "bonded", [&] { launch_bonded(h->d, s); });
   timed(h, "cv", [&] { launch_cv(h->d, h->c, s, h->cv_variant); });
   timed(h, "cvfin", [&] { launch_cvfin(h->d, h->c, mode, s); });
 }
@@ -224,11 +227,12 @@ void after_forces(sim_handle *h, FinMode mode) {
 }
 
 // forces of the current positions, after an optional list rebuild.  Unless
-// kernels are being timed one by one, the reaction coordinate (CV and its
-// finaliser) runs on a second stream once the atoms have their slots (it
-// reads positions through slot_of) and joins before anything that follows:
-// the list build and the pair kernel write nothing it reads.  All force and
-// gradient sums are fixed-point, so both orders give bit-identical states.
+// kernels are being timed one by one, the bonded forces and the reaction
+// coordinate (CV and its finaliser) run on a second stream once the atoms
+// have their slots (they read positions through slot_of) and join before
+// anything that follows: the list build and the pair kernel write nothing
+// they read, and pair and bonded forces meet only in order-independent
+// fixed-point sums, so both orders give bit-identical states.
 void forces(sim_handle *h, FinMode mode, bool with_rebuild) {
   if (with_rebuild) rebuild_cols(h);
   if (h->side && !h->timing) {
@@ -363,6 +367,8 @@ VP_API int sim_create(const sim_system *systems, int32_t n_systems, const int32_
   int total_trials = 0;
   for (int s = 0; s < n_systems; ++s) {
     if (trials_per_system[s] < 0) return bail(fail(h, SIM_EINVAL, "negative trial count"));
+    if (trials_per_system[s] > MAX_TRIALS || total_trials + trials_per_system[s] > MAX_TRIALS)
+      return bail(fail(h, SIM_EINVAL, "more than 65535 trials in one batch"));
     std::string m = check_system(systems[s], p);
     if (!m.empty()) return bail(fail(h, SIM_EINVAL, "system " + std::to_string(s) + ": " + m));
     total_trials += trials_per_system[s];
@@ -475,6 +481,8 @@ VP_API int sim_create(const sim_system *systems, int32_t n_systems, const int32_
   std::vector<int32_t> excl((size_t)total_sys_atoms * MAX_EXCL, -1), excl_n(total_sys_atoms, 0);
   std::vector<int32_t> bt_start(total_sys_atoms + 1, 0);
   std::vector<BTerm> bterm;
+  std::vector<BGroup> bgrp;
+  std::vector<int32_t> sys_bg0(n_systems), sys_nbg(n_systems);
   std::vector<int2> tiles;
   std::vector<int32_t> sys_tile0(n_systems), sys_ntiles(n_systems), sys_ncv(n_systems), sys_minsep(n_systems),
       tile_sys, sys_nat0(n_systems);
@@ -537,6 +545,60 @@ VP_API int sim_create(const sim_system *systems, int32_t n_systems, const int32_
       bt_start[a0 + i] = (int)bterm.size();
       for (auto &t : per[i]) bterm.push_back(t);
     }
+    // the same terms once each, for the force kernel, grouped: every angle
+    // opens a group of its three atoms; a bond joins the first group that
+    // holds both its atoms, else one it can extend to three atoms, else opens
+    // a group of its own (a water: its angle and both bonds in one group)
+    sys_bg0[s] = (int)bgrp.size();
+    {
+      std::vector<std::vector<int>> of_atom(S.n_atoms);  // groups (local index) that hold an atom
+      std::vector<BGroup> G;
+      auto local = [](const BGroup &g, int atom) {
+        for (int m = 0; m < 3; ++m)
+          if (g.at[m] == atom) return m;
+        return -1;
+      };
+      for (int a = 0; a < S.n_angles; ++a) {
+        BGroup g{};
+        g.at[0] = S.angles[3 * a]; g.at[1] = S.angles[3 * a + 1]; g.at[2] = S.angles[3 * a + 2];
+        g.n = 1;
+        g.code[0] = 1 | (0 << 1) | (1 << 3) | (2 << 5);
+        g.par[0] = make_float2((float)S.angle_t0[a], (float)S.angle_k[a]);
+        for (int m = 0; m < 3; ++m) of_atom[g.at[m]].push_back((int)G.size());
+        G.push_back(g);
+      }
+      for (int b = 0; b < S.n_bonds; ++b) {
+        const int i = S.bonds[2 * b], j = S.bonds[2 * b + 1];
+        int gi = -1;
+        for (int q : of_atom[i])
+          if (G[q].n < 3 && local(G[q], j) >= 0) { gi = q; break; }
+        if (gi < 0)
+          for (int atom : {i, j}) {
+            for (int q : of_atom[atom])
+              if (G[q].n < 3 && G[q].at[2] < 0) { gi = q; break; }
+            if (gi >= 0) break;
+          }
+        if (gi < 0) {
+          BGroup g{};
+          g.at[0] = i; g.at[1] = j; g.at[2] = -1;
+          gi = (int)G.size();
+          G.push_back(g);
+          of_atom[i].push_back(gi);
+          of_atom[j].push_back(gi);
+        }
+        BGroup &g = G[gi];
+        for (int atom : {i, j})
+          if (local(g, atom) < 0) {  // the third atom of a two-atom group
+            g.at[2] = atom;
+            of_atom[atom].push_back(gi);
+          }
+        g.code[g.n] = 0 | (local(g, i) << 1) | (local(g, j) << 3);
+        g.par[g.n] = make_float2((float)S.bond_r0[b], (float)S.bond_k[b]);
+        g.n += 1;
+      }
+      for (auto &g : G) bgrp.push_back(g);
+    }
+    sys_nbg[s] = (int)bgrp.size() - sys_bg0[s];
     // reaction-coordinate tiles
     sys_ncv[s] = S.n_cv;
     sys_minsep[s] = p.cv_min_sep;
@@ -685,6 +747,10 @@ VP_API int sim_create(const sim_system *systems, int32_t n_systems, const int32_
   r |= upload(h, &d.excl_n, excl_n);
   r |= upload(h, &d.bt_start, bt_start);
   r |= upload(h, &d.bterm, bterm);
+  r |= upload(h, &d.bgrp, bgrp);
+  r |= upload(h, &d.sys_bg0, sys_bg0);
+  r |= upload(h, &d.sys_nbg, sys_nbg);
+  d.max_nbg = sys_nbg.empty() ? 0 : *std::max_element(sys_nbg.begin(), sys_nbg.end());
   r |= upload(h, &d.tiles, tiles);
   r |= upload(h, &d.work, work);
   {

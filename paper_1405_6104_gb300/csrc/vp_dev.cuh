@@ -35,8 +35,11 @@ struct Dev {
   double *gm;                          // gamma_i m_i
   double *inv_gm;                      // 1 / (gamma_i m_i) (0 without friction)
   int32_t *excl, *excl_n;              // [sys atoms * MAX_EXCL], counts
-  int32_t *bt_start;                   // [total system atoms + 1] CSR of owner-computed bonded terms
+  int32_t *bt_start;                   // [total system atoms + 1] CSR of owner-computed bonded terms (energies)
   BTerm *bterm;
+  BGroup *bgrp;                        // bonded terms for forces in groups over at most 3 atoms
+  int32_t *sys_bg0, *sys_nbg;          // per system: first group, count
+  int32_t max_nbg;                     // largest group count of a system
   // reaction coordinate
   int2 *tiles;                         // per system tile (bi, bj), concatenated
   int2 *work;                          // flat (trial, global tile) work items
@@ -70,6 +73,7 @@ void launch_colsort(const Dev &d, cudaStream_t s);
 void launch_list(const Dev &d, const SimConst &c, float rl2_bbox, cudaStream_t s);
 // forces (vp_pair.cu)
 void launch_pair(const Dev &d, const SimConst &c, bool energy, int32_t only_trial, cudaStream_t s, int variant = 0);
+void launch_bonded(const Dev &d, cudaStream_t s);
 constexpr int PAIR_VARIANTS = 9;
 // reaction coordinate and functional (vp_cv.cu)
 void launch_cnat(const Dev &d, const SimConst &c, const double *native, const int32_t *sys_nat0, int32_t n_tiles_total,

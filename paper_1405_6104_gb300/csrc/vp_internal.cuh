@@ -14,6 +14,7 @@ constexpr double KB = 0.0083144626;    // kJ/mol/K
 constexpr double FCOUL = 138.935458;   // kJ mol^-1 nm e^-2
 constexpr int CL = 8;                  // atoms per i-cluster
 constexpr int CJ = 4;                  // atoms per j-cluster (half an i-cluster)
+constexpr int MAX_TRIALS = 65535;      // trials per batch (one grid row each in the per-trial kernels)
 constexpr int MAX_EXCL = 16;           // excluded partners per atom
 constexpr int MAX_TYPES = 64;          // distinct LJ types after de-duplication
 constexpr int COL_CAP = 1024;          // atoms per grid column
@@ -86,6 +87,18 @@ struct BTerm {
   int32_t kind;   // 0 bond, 1 angle end, 2 angle vertex
   int32_t p1, p2; // bond: partner; end: vertex, other end; vertex: the two ends
   float x0, k;    // r0 or theta0, force constant
+};
+
+// a group of bonded terms over at most 3 atoms (one thread each): the terms'
+// forces are summed per atom in fixed point before one reduction per atom
+// and component.  code[k] of term k < n: bit 0 kind (0 bond, 1 angle), bits
+// 1-2, 3-4, 5-6 the local atoms i, j, l (bond i-j; angle i-j-l, j the vertex)
+struct BGroup {
+  int32_t at[3];   // system atoms (at[2] = -1 for a two-atom group)
+  int32_t n;       // terms, 1..3
+  int32_t code[3];
+  int32_t pad;
+  float2 par[3];   // {r0 or theta0, force constant}
 };
 
 struct SimConst {

@@ -7,9 +7,9 @@
 // reduction per component.  i-forces stay in registers over the whole list
 // and are reduced across the warp at the end.  FP32 pair arithmetic,
 // order-independent int64 accumulation (2^32 units per kJ/mol/nm), so the
-// forces are bit-reproducible.  The same warp adds the bonded forces of its
-// 8 atoms (each atom computes its own share of every bond and angle it is
-// part of).
+// forces are bit-reproducible.  Bonded forces (each atom computes its own
+// share of every bond and angle it is part of) come from k_bonded; the
+// energy kernel k_pair computes the bonded energies itself.
 #include <algorithm>
 
 #include "vp_dev.cuh"
@@ -389,22 +389,6 @@ __global__ void __launch_bounds__(PF_WARPS * 32, MINB) k_pair_f(Dev d, SimConst 
     tj = tj_n;
   }
 
-  // bonded terms of the 8 i-atoms (lanes 0..7)
-  if (lane < CL) {
-    const int o = d.orig[I * CL + lane];
-    if (o >= 0) {
-      float4 self = make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-      for (int a = 0; a < CL; ++a)
-        if (a == lane) self = make_float4(xi[a], yi[a], zi[a], 0.f);
-      if (SHI) self = make_float4(s_i[wib][lane].x, s_i[wib][lane].y, s_i[wib][lane].z, 0.f);
-      float eb = 0.f, ea = 0.f;
-      const float3 fb = bonded_force(d, T, o, self, eb, ea);
-#pragma unroll
-      for (int a = 0; a < CL; ++a)
-        if (a == lane) { fi[a][0] += fb.x; fi[a][1] += fb.y; fi[a][2] += fb.z; }
-    }
-  }
   // i-forces: column sums of the 32 lanes' partials in a fixed order
   float *r = s_red[wib];
 #pragma unroll
@@ -588,17 +572,6 @@ __global__ void __launch_bounds__(PF_WARPS * 32, MINB) k_pair_f2(Dev d, SimConst
     fi[2 * p][0] = -fx[p].x; fi[2 * p][1] = -fy[p].x; fi[2 * p][2] = -fz[p].x;
     fi[2 * p + 1][0] = -fx[p].y; fi[2 * p + 1][1] = -fy[p].y; fi[2 * p + 1][2] = -fz[p].y;
   }
-  if (lane < CL) {
-    const int o = d.orig[I * CL + lane];
-    if (o >= 0) {
-      const float4 sp = d.pos[I * CL + lane];
-      float eb = 0.f, ea = 0.f;
-      const float3 fb = bonded_force(d, T, o, make_float4(sp.x, sp.y, sp.z, 0.f), eb, ea);
-#pragma unroll
-      for (int a = 0; a < CL; ++a)
-        if (a == lane) { fi[a][0] += fb.x; fi[a][1] += fb.y; fi[a][2] += fb.z; }
-    }
-  }
   float *r = s_red[wib];
 #pragma unroll
   for (int a = 0; a < CL; ++a)
@@ -613,6 +586,91 @@ __global__ void __launch_bounds__(PF_WARPS * 32, MINB) k_pair_f2(Dev d, SimConst
     if (val != 0) red_add((comp == 0 ? d.fx : comp == 1 ? d.fy : d.fz) + I * CL + a, val);
   }
   }  // for each cluster
+}
+
+// Bonded forces, one thread per (trial, group of terms over at most 3 atoms;
+// a water's angle and bonds form one group): every term's forces are
+// converted to fixed point and summed per atom, exactly, so the group issues
+// one reduction per atom and component (exact action-reaction: a bond's
+// second atom and an angle's vertex take minus the others' forces).  The
+// arithmetic of a term is that of bonded_force for the bond's first atom and
+// for the angle's vertex.  A kernel of its own, beside the pair kernel: inside
+// the pair kernel's warps the per-atom term loops ran on 8 of 32 lanes behind
+// chains of dependent loads.
+__device__ __forceinline__ void add3(long long (&F)[3][3], int m, long long x, long long y, long long z) {
+#pragma unroll
+  for (int q = 0; q < 3; ++q)
+    if (q == m) { F[q][0] += x; F[q][1] += y; F[q][2] += z; }
+}
+
+__device__ __forceinline__ float4 pick3(const float4 (&p)[3], int m) { return m == 0 ? p[0] : m == 1 ? p[1] : p[2]; }
+
+__global__ void __launch_bounds__(256) k_bonded(Dev d) {
+  const int t = blockIdx.y;
+  const TrialInfo T = d.tinfo[t];
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= d.sys_nbg[T.sys]) return;
+  const BGroup G = d.bgrp[d.sys_bg0[T.sys] + k];
+  const float L = T.box, iL = T.inv_box;
+  int sl[3];
+  float4 p[3];
+#pragma unroll
+  for (int m = 0; m < 3; ++m) {
+    sl[m] = G.at[m] >= 0 ? d.slot_of[T.atom0 + G.at[m]] : -1;
+    p[m] = sl[m] >= 0 ? d.pos[sl[m]] : make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+  long long F[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    if (q >= G.n) break;
+    const int code = G.code[q];
+    const float2 par = G.par[q];
+    const int li = (code >> 1) & 3, lj = (code >> 3) & 3, ll = (code >> 5) & 3;
+    const float4 pa = pick3(p, li), pb = pick3(p, lj);
+    if ((code & 1) == 0) {
+      // bond a-b, V = k/2 (r - r0)^2: the stretch in float-float (exact coordinate differences)
+      const float nx = rintf((pb.x - pa.x) * iL), ny = rintf((pb.y - pa.y) * iL), nz = rintf((pb.z - pa.z) * iL);
+      const ff dx = ff_diff(pb.x - L * nx, pa.x), dy = ff_diff(pb.y - L * ny, pa.y), dz = ff_diff(pb.z - L * nz, pa.z);
+      const ff r = ff_sqrt(ff_add(ff_add(ff_sqr(dx), ff_sqr(dy)), ff_sqr(dz)));
+      const float dr = ff_add_f(r, -par.x).hi;
+      const float fs = par.y * dr / r.hi;  // force on a = +k dr (b - a)/r
+      const long long fx = fx_from(fs * dx.hi), fy = fx_from(fs * dy.hi), fz = fx_from(fs * dz.hi);
+      add3(F, li, fx, fy, fz);
+      add3(F, lj, -fx, -fy, -fz);
+    } else {
+      // angle a-b-c (vertex b), V = k/2 (theta - theta0)^2
+      const float4 pc = pick3(p, ll);
+      const float3 u = min_disp(pb, pa, L, iL), v = min_disp(pb, pc, L, iL);
+      const float uu = u.x * u.x + u.y * u.y + u.z * u.z, vv = v.x * v.x + v.y * v.y + v.z * v.z;
+      const float iuv = rsqrtf(uu * vv);
+      float cs = (u.x * v.x + u.y * v.y + u.z * v.z) * iuv;
+      cs = fminf(1.0f, fmaxf(-1.0f, cs));
+      const float dth = acosf(cs) - par.x;
+      const float sn = fmaxf(sqrtf(fmaxf(0.0f, 1.0f - cs * cs)), 1e-6f);
+      const float g = par.y * dth / sn;
+      const float iuu = 1.0f / uu, ivv = 1.0f / vv;
+      // forces on the ends: g d cos / d u and g d cos / d v
+      const long long ax = fx_from(g * (v.x * iuv - cs * u.x * iuu)), ay = fx_from(g * (v.y * iuv - cs * u.y * iuu)),
+                      az = fx_from(g * (v.z * iuv - cs * u.z * iuu));
+      const long long cx = fx_from(g * (u.x * iuv - cs * v.x * ivv)), cy = fx_from(g * (u.y * iuv - cs * v.y * ivv)),
+                      cz = fx_from(g * (u.z * iuv - cs * v.z * ivv));
+      add3(F, li, ax, ay, az);
+      add3(F, ll, cx, cy, cz);
+      add3(F, lj, -(ax + cx), -(ay + cy), -(az + cz));
+    }
+  }
+#pragma unroll
+  for (int m = 0; m < 3; ++m)
+    if (sl[m] >= 0) {
+      red_add(d.fx + sl[m], F[m][0]);
+      red_add(d.fy + sl[m], F[m][1]);
+      red_add(d.fz + sl[m], F[m][2]);
+    }
+}
+
+void launch_bonded(const Dev &d, cudaStream_t s) {
+  if (d.max_nbg <= 0) return;
+  k_bonded<<<dim3((unsigned)((d.max_nbg + 255) / 256), (unsigned)d.n_trials), 256, 0, s>>>(d);
 }
 
 // variants differ in the register cap (blocks per SM the compiler must fit)

@@ -78,6 +78,7 @@ def test_invalid_systems_are_rejected_on_the_host(lib):
     p2 = S.Params(**{**p.__dict__, "nstlist": 0})
     assert "params" in _expect_einval([s], p2)
     _expect_einval([s], p, trials=(0,))
+    assert "65535" in _expect_einval([s, s], p, trials=(40000, 40000))
 
 
 def test_toy2d_host_validation(lib):
