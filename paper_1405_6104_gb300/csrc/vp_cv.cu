@@ -73,17 +73,24 @@ __global__ void k_zconst(Dev d, const int32_t *sys_tile0, const int32_t *sys_nti
   if (threadIdx.x == 0) d.tstate[t].zconst = red[0];
 }
 
+__device__ __forceinline__ long long gsum(int hi, unsigned lo) { return (long long)hi * 16777216ll + (long long)lo; }
+
 // Two phases per (trial, tile) warp: (1) a cheap FP32 distance test of the
 // 1024 pairs of the tile lists the pairs closer than the contact cut-off in
 // shared memory; (2) the warp evaluates only those, 32 at a time, in
-// float-float, accumulating the gradient of the tile's 64 atoms with int64
+// float-float, accumulating the gradient of the tile's 64 atoms with integer
 // shared-memory atomics (order-independent, so deterministic) and flushing it
 // once per tile.  Far pairs (C~ = 0) contribute only to the constant Z0.
 template <int CV_WARPS>
 __global__ void __launch_bounds__(CV_WARPS * 32) k_cv(Dev d, SimConst c) {
   __shared__ unsigned short s_near[CV_WARPS][CV_T * CV_T];
   __shared__ float s_x[CV_WARPS][2 * CV_T][3];
-  __shared__ unsigned long long s_g[CV_WARPS][2 * CV_T][3];
+  // gradient of the tile's 64 atoms: each fixed-point contribution c splits
+  // into c >> 24 (signed) and its low 24 bits, summed in 32-bit shared
+  // atomics (native, unlike 64-bit ones); at most 32 contributions per entry
+  // keep both sums far from overflow, and (hi << 24) + lo is the exact sum
+  __shared__ int s_ghi[CV_WARPS][2 * CV_T][3];
+  __shared__ unsigned s_glo[CV_WARPS][2 * CV_T][3];
   const int wib = threadIdx.x >> 5;
   const int wq = blockIdx.x * CV_WARPS + wib;
   const int lane = threadIdx.x & 31;
@@ -102,7 +109,10 @@ __global__ void __launch_bounds__(CV_WARPS * 32) k_cv(Dev d, SimConst c) {
   s_x[wib][lane][0] = xi.x; s_x[wib][lane][1] = xi.y; s_x[wib][lane][2] = xi.z;
   s_x[wib][CV_T + lane][0] = xj.x; s_x[wib][CV_T + lane][1] = xj.y; s_x[wib][CV_T + lane][2] = xj.z;
 #pragma unroll
-  for (int q = 0; q < 3; ++q) { s_g[wib][lane][q] = 0ull; s_g[wib][CV_T + lane][q] = 0ull; }
+  for (int q = 0; q < 3; ++q) {
+    s_ghi[wib][lane][q] = 0; s_ghi[wib][CV_T + lane][q] = 0;
+    s_glo[wib][lane][q] = 0u; s_glo[wib][CV_T + lane][q] = 0u;
+  }
   // ---- phase 1: near pairs of the tile ----
   int n_near = 0;
   for (int k = 0; k < CV_T; ++k) {
@@ -147,25 +157,29 @@ __global__ void __launch_bounds__(CV_WARPS * 32) k_cv(Dev d, SimConst c) {
       const float wgt = 2.0f * h.hi * cp.dCt / cp.r;
       if (wgt != 0.0f) {
         const long long gx = fx_from(wgt * dx.hi), gy = fx_from(wgt * dy.hi), gz = fx_from(wgt * dz.hi);
-        atomicAdd(&s_g[wib][il][0], (unsigned long long)(-gx));
-        atomicAdd(&s_g[wib][il][1], (unsigned long long)(-gy));
-        atomicAdd(&s_g[wib][il][2], (unsigned long long)(-gz));
-        atomicAdd(&s_g[wib][CV_T + jc][0], (unsigned long long)gx);
-        atomicAdd(&s_g[wib][CV_T + jc][1], (unsigned long long)gy);
-        atomicAdd(&s_g[wib][CV_T + jc][2], (unsigned long long)gz);
+        const long long gv[3] = {gx, gy, gz};
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+          atomicAdd(&s_ghi[wib][il][q], (int)((-gv[q]) >> 24));
+          atomicAdd(&s_glo[wib][il][q], (unsigned)((-gv[q]) & 0xffffff));
+          atomicAdd(&s_ghi[wib][CV_T + jc][q], (int)(gv[q] >> 24));
+          atomicAdd(&s_glo[wib][CV_T + jc][q], (unsigned)(gv[q] & 0xffffff));
+        }
       }
     }
   }
   __syncwarp();
   if (n_near > 0) {
     if (i < ncv) {
-      const long long a0 = (long long)s_g[wib][lane][0], a1 = (long long)s_g[wib][lane][1],
-                      a2 = (long long)s_g[wib][lane][2];
+      const long long a0 = gsum(s_ghi[wib][lane][0], s_glo[wib][lane][0]),
+                      a1 = gsum(s_ghi[wib][lane][1], s_glo[wib][lane][1]),
+                      a2 = gsum(s_ghi[wib][lane][2], s_glo[wib][lane][2]);
       if (a0 | a1 | a2) { red_add(d.gx + T.cv0 + i, a0); red_add(d.gy + T.cv0 + i, a1); red_add(d.gz + T.cv0 + i, a2); }
     }
     if (jl < ncv) {
-      const long long a0 = (long long)s_g[wib][CV_T + lane][0], a1 = (long long)s_g[wib][CV_T + lane][1],
-                      a2 = (long long)s_g[wib][CV_T + lane][2];
+      const long long a0 = gsum(s_ghi[wib][CV_T + lane][0], s_glo[wib][CV_T + lane][0]),
+                      a1 = gsum(s_ghi[wib][CV_T + lane][1], s_glo[wib][CV_T + lane][1]),
+                      a2 = gsum(s_ghi[wib][CV_T + lane][2], s_glo[wib][CV_T + lane][2]);
       if (a0 | a1 | a2) { red_add(d.gx + T.cv0 + jl, a0); red_add(d.gy + T.cv0 + jl, a1); red_add(d.gz + T.cv0 + jl, a2); }
     }
   }
