@@ -594,6 +594,7 @@ VP_API int sim_create(const sim_system *systems, int32_t n_systems, const int32_
           }
         g.code[g.n] = 0 | (local(g, i) << 1) | (local(g, j) << 3);
         g.par[g.n] = make_float2((float)S.bond_r0[b], (float)S.bond_k[b]);
+        g.x0lo[g.n] = (float)(S.bond_r0[b] - (double)g.par[g.n].x);
         g.n += 1;
       }
       for (auto &g : G) bgrp.push_back(g);
@@ -729,6 +730,7 @@ VP_API int sim_create(const sim_system *systems, int32_t n_systems, const int32_
   r |= dalloc(h, &d.col_start, col0);
   r |= dalloc(h, &d.col_cstart, col0);
   r |= dalloc(h, &d.col_fill, col0);
+  r |= dalloc(h, &d.col_ztab, (size_t)col0 * (ZBINS + 1));
   r |= dalloc(h, &d.bucket, total_atoms);
   r |= upload(h, &d.slot_of, slot_of);
   r |= upload(h, &d.ref_pos, ref);

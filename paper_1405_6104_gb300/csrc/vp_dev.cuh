@@ -24,6 +24,7 @@ struct Dev {
   // grid columns
   int32_t *col_trial;                  // static
   int32_t *col_count, *col_start, *col_cstart, *col_fill;
+  int32_t *col_ztab;                   // [columns * (ZBINS + 1)]: halves of the column with z_lo below b L / ZBINS
   int32_t *bucket;                     // [total trial atoms]
   // per trial, caller-ordered
   int32_t *slot_of;                    // [total trial atoms]

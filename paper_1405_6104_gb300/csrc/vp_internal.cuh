@@ -14,6 +14,7 @@ constexpr double KB = 0.0083144626;    // kJ/mol/K
 constexpr double FCOUL = 138.935458;   // kJ mol^-1 nm e^-2
 constexpr int CL = 8;                  // atoms per i-cluster
 constexpr int CJ = 4;                  // atoms per j-cluster (half an i-cluster)
+constexpr int ZBINS = 16;             // z-bins of the per-column half table the list build searches
 constexpr int MAX_TRIALS = 65535;      // trials per batch (one grid row each in the per-trial kernels)
 constexpr int MAX_EXCL = 16;           // excluded partners per atom
 constexpr int MAX_TYPES = 64;          // distinct LJ types after de-duplication
@@ -99,6 +100,8 @@ struct BGroup {
   int32_t code[3];
   int32_t pad;
   float2 par[3];   // {r0 or theta0, force constant}
+  float x0lo[3];   // r0 - par.x (a bond's rest length in float-float: k (r - r0) with k ~ 1e5 needs it)
+  int32_t pad2;
 };
 
 struct SimConst {

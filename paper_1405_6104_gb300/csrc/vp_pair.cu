@@ -632,7 +632,7 @@ __global__ void __launch_bounds__(256) k_bonded(Dev d) {
       const float nx = rintf((pb.x - pa.x) * iL), ny = rintf((pb.y - pa.y) * iL), nz = rintf((pb.z - pa.z) * iL);
       const ff dx = ff_diff(pb.x - L * nx, pa.x), dy = ff_diff(pb.y - L * ny, pa.y), dz = ff_diff(pb.z - L * nz, pa.z);
       const ff r = ff_sqrt(ff_add(ff_add(ff_sqr(dx), ff_sqr(dy)), ff_sqr(dz)));
-      const float dr = ff_add_f(r, -par.x).hi;
+      const float dr = ff_add_f(ff_add_f(r, -par.x), -G.x0lo[q]).hi;  // r - r0 with r0 in float-float
       const float fs = par.y * dr / r.hi;  // force on a = +k dr (b - a)/r
       const long long fx = fx_from(fs * dx.hi), fy = fx_from(fs * dy.hi), fz = fx_from(fs * dz.hi);
       add3(F, li, fx, fy, fz);

@@ -134,6 +134,7 @@ __global__ void k_colfill(Dev d) {
 __global__ void __launch_bounds__(128) k_colsort(Dev d) {
   __shared__ unsigned long long key[COL_CAP];
   __shared__ int s_old[COL_CAP];
+  __shared__ float s_zlo[COL_CAP / CJ + 2];  // lower z-bound of every half
   int cg = blockIdx.x;
   int t = d.col_trial[cg];
   const TrialInfo T = d.tinfo[t];
@@ -205,6 +206,16 @@ __global__ void __launch_bounds__(128) k_colsort(Dev d) {
     int hj = 2 * (T.clus0 + cstart) + k;
     d.bb_lo[hj] = make_float4(lo.x, lo.y, lo.z, 0.f);
     d.bb_hi[hj] = make_float4(hi.x, hi.y, hi.z, 0.f);
+    s_zlo[k] = lo.z;
+  }
+  __syncthreads();
+  // z-bin table: the halves are in ascending z, so the number of halves whose
+  // lower z-bound lies below b L / ZBINS is the first half at or above it
+  for (int b = threadIdx.x; b <= ZBINS; b += blockDim.x) {
+    const float zt = (float)b * (T.box / ZBINS);
+    int cnt = 0;
+    for (int k = 0; k < 2 * ncl; ++k) cnt += s_zlo[k] < zt ? 1 : 0;
+    d.col_ztab[(size_t)cg * (ZBINS + 1) + b] = cnt;
   }
 }
 
@@ -306,19 +317,59 @@ __global__ void __launch_bounds__(LIST_WARPS * 32, 8) k_list(Dev d, SimConst c, 
   // that the bounding-box loads of a whole step are in flight together
   for (int cb = 0; cb < nc2; cb += 32) {
     const int cc = cb + lane;
-    int jlo = 0, cntc = 0;
+    // this lane's column: up to two ranges [a1, a1 + n1), [a2, a2 + n2) of
+    // half indices (relative to the trial's first half) whose z-extent can
+    // reach the i-cluster: the z-window (and its periodic image) comes from
+    // the column's xy gap, the ranges from the column's z-bin table, one bin
+    // wider on each side than needed (every half in them is still tested)
+    int a1 = 0, n1 = 0, a2 = 0, n2 = 0;
     if (cc < nc2) {
       const int n = d.col_count[T.col0 + cc];
       const int ccs = d.col_cstart[T.col0 + cc];
       const int ncl = (n + CL - 1) / CL;
-      jlo = max(ccs, Il);
+      const int jlo = max(ccs, Il);
       if (ccs + ncl > jlo) {
         const int cx = cc / T.ncol, cy = cc - cx * T.ncol;
         const float gx = periodic_gap(lo.x, hi.x, cx * w, (cx + 1) * w, L);
         const float gy = periodic_gap(lo.y, hi.y, cy * w, (cy + 1) * w, L);
-        if (gx * gx + gy * gy < rl2_bbox) cntc = 2 * (ccs + ncl - jlo);
+        const float g2 = gx * gx + gy * gy;
+        if (g2 < rl2_bbox) {
+          const int hs = 2 * (jlo - ccs), he = 2 * ncl;  // local half range of the half list
+          const float rz = sqrtf(rl2_bbox - g2) * 1.001f + 1e-3f;
+          const float za = lo.z - rz, zb = hi.z + rz;
+          if (zb - za >= L) {
+            a1 = hs; n1 = he - hs;
+          } else {
+            const int *tab = d.col_ztab + (size_t)(T.col0 + cc) * (ZBINS + 1);
+            const float zs = ZBINS * iL;
+            // halves that may meet [u, v] (0 <= u <= v <= L)
+            auto range = [&](float u, float v, int &ra, int &rb) {
+              const int bu = max(0, min(ZBINS, (int)floorf(u * zs) - 1));
+              const int bv = max(0, min(ZBINS, (int)floorf(v * zs) + 2));
+              ra = max(tab[bu] - 1, 0);
+              rb = bv >= ZBINS ? he : tab[bv];
+            };
+            int r1a, r1b, r2a = 0, r2b = 0;
+            if (za < 0.f) {          // [0, zb] and [za + L, L]
+              range(0.f, zb, r1a, r1b);
+              range(za + L, L, r2a, r2b);
+            } else if (zb > L) {     // [0, zb - L] and [za, L]
+              range(0.f, zb - L, r1a, r1b);
+              range(za, L, r2a, r2b);
+            } else {
+              range(za, zb, r1a, r1b);
+            }
+            r1a = max(r1a, hs); r1b = min(r1b, he);
+            r2a = max(max(r2a, hs), r1b); r2b = min(r2b, he);  // ascending, no half twice
+            a1 = r1a; n1 = max(r1b - r1a, 0);
+            a2 = r2a; n2 = max(r2b - r2a, 0);
+          }
+          a1 += 2 * ccs;
+          a2 += 2 * ccs;
+        }
       }
     }
+    const int cntc = n1 + n2;
     // inclusive scan of the per-column candidate counts
     int incl = cntc;
 #pragma unroll
@@ -340,11 +391,14 @@ __global__ void __launch_bounds__(LIST_WARPS * 32, 8) k_list(Dev d, SimConst c, 
       }
       const int own_incl = __shfl_sync(0xffffffffu, incl, lo_l);
       const int own_cnt = __shfl_sync(0xffffffffu, cntc, lo_l);
-      const int own_jlo = __shfl_sync(0xffffffffu, jlo, lo_l);
+      const int own_a1 = __shfl_sync(0xffffffffu, a1, lo_l);
+      const int own_n1 = __shfl_sync(0xffffffffu, n1, lo_l);
+      const int own_a2 = __shfl_sync(0xffffffffu, a2, lo_l);
       bool ok = false;
       int J4 = 0;
       if (tt < total) {
-        J4 = 2 * own_jlo + (tt - (own_incl - own_cnt));
+        const int u = tt - (own_incl - own_cnt);
+        J4 = u < own_n1 ? own_a1 + u : own_a2 + (u - own_n1);
         const float4 jlo4 = d.bb_lo[2 * T.clus0 + J4], jhi4 = d.bb_hi[2 * T.clus0 + J4];
         const float gx = periodic_gap(lo.x, hi.x, jlo4.x, jhi4.x, L);
         const float gy = periodic_gap(lo.y, hi.y, jlo4.y, jhi4.y, L);

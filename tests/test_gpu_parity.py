@@ -92,6 +92,30 @@ def test_forces_and_energies_parity(name):
 
 
 @pytest.mark.parametrize("name", ["tiny", "small"])
+def test_bonded_forces_alone(name):
+    """Bonds and angles only (no charges, no Lennard-Jones, no bias): the
+    grouped bonded kernel against the oracle atom by atom on thermalised
+    molecules (at the generated start every bond and angle sits at its rest
+    value and the forces are rounding noise), and exact action-reaction (the
+    fixed-point forces of every group sum to zero)."""
+    s, p = SYSTEMS[name]()
+    s = s.copy()
+    s.charge = np.zeros_like(s.charge)
+    s.epsilon = np.zeros_like(s.epsilon)
+    p = S.Params(**{**p.__dict__, "k_ratchet": 0.0})
+    with B.TrialBatch(s, p, [2], trial_seeds=[3, 4]) as b:
+        for n_steps in (20, 20):
+            b.step(n_steps)
+            for t in range(2):
+                pos, _, _ = b.get_state(t)
+                _, F = b.energy_forces(t)
+                Fr, _ = O.forces(s, p, pos, use_list=False)
+                assert rel_rms(F, Fr) < 1e-5
+                assert np.abs(F - Fr).max() < 1e-4 * np.abs(Fr).max()
+                assert np.abs(F.sum(axis=0)).max() == 0.0
+
+
+@pytest.mark.parametrize("name", ["tiny", "small"])
 def test_trajectory_parity_100_steps(name):
     s, p = SYSTEMS[name]()
     seed = 4242
