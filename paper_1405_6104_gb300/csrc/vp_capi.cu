@@ -1468,6 +1468,7 @@ VP_API void sim_destroy(sim_handle *h) {
   if (!h) return;
   cudaSetDevice(h->device);
   if (h->stream) cudaStreamSynchronize(h->stream);
+  if (h->side) cudaStreamSynchronize(h->side);
   if (h->chunk) cudaGraphExecDestroy(h->chunk);
   for (auto &e : h->gev) cudaEventDestroy(e);
   for (void *p : h->callocs) cudaFree(p);
