@@ -43,7 +43,10 @@ extern "C" {
 #define SIM_OK 0
 #define SIM_EINVAL (-1)          /* invalid argument or system description */
 #define SIM_ECUDA (-2)           /* a CUDA call failed */
-#define SIM_ELIST_OVERFLOW (-3)  /* a cluster's neighbour list or a grid column exceeded capacity */
+#define SIM_ELIST_OVERFLOW (-3)  /* a cluster's neighbour list or a grid column exceeded capacity
+                                   (512 entries per cluster; the environment variable
+                                   VPATH_LIST_CAP, read at sim_create, lowers it to 8..511 for
+                                   fault-injection tests) */
 #define SIM_ESKIN (-4)           /* an atom moved more than skin/2 between list rebuilds (SIM_STRICT_SKIN) */
 #define SIM_ENONFINITE (-5)      /* a position, velocity or z became non-finite */
 #define SIM_ETIMEOUT (-6)        /* a bounded device wait gave up */

@@ -4,6 +4,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <string>
@@ -412,6 +413,11 @@ VP_API int sim_create(const sim_system *systems, int32_t n_systems, const int32_
   c.kR_half = (float)(0.5 * p.k_ratchet);
   c.kR_half_d = 0.5 * p.k_ratchet;
   c.list_cap = 512;
+  // debug knob (fault injection): a smaller list capacity, 8..512 entries per cluster
+  if (const char *e = std::getenv("VPATH_LIST_CAP")) {
+    const int v = std::atoi(e);
+    if (v >= 8 && v <= 512) c.list_cap = v;
+  }
   ff_split(1.0 / (p.cv_r0 * p.cv_r0), c.cv_inv_r0sq_hi, c.cv_inv_r0sq_lo);
   ff_split(p.cv_r_switch, c.cv_rs_hi, c.cv_rs_lo);
   ff_split(1.0 / (p.cv_r_cut - p.cv_r_switch), c.cv_inv_w_hi, c.cv_inv_w_lo);

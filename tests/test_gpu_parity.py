@@ -361,6 +361,20 @@ def test_strict_skin_violation_is_reported():
         assert e.value.code == B.SIM_ESKIN
 
 
+def test_list_overflow_is_reported(monkeypatch):
+    """A cluster list capacity forced below what the system needs: the list
+    build's own bounds checks drop the excess entries, flag the overflow, and
+    sim_create returns SIM_ELIST_OVERFLOW (nothing is written out of bounds)."""
+    s, p = S.small_solvated()
+    monkeypatch.setenv("VPATH_LIST_CAP", "16")
+    with pytest.raises(B.SimError) as e:
+        B.TrialBatch(s, p, [1])
+    assert e.value.code == B.SIM_ELIST_OVERFLOW
+    monkeypatch.delenv("VPATH_LIST_CAP")
+    with B.TrialBatch(s, p, [1]) as b:  # the default capacity holds it
+        b.step(10)
+
+
 def test_blow_up_is_reported_as_non_finite():
     """A time step far beyond the stable one makes the run blow up; the
     kernels flag the non-finite (or unwrappable) coordinates and the call
