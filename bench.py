@@ -552,14 +552,17 @@ def run_similarity(args):
     ms = ev0.elapsed_time(ev1) / args.steps
     comparisons = float(len(pairs)) * n_c * (n_c - 1)
     line = {
-        "metric": "path-similarity comparisons/s (ordered contact pairs x path pairs)",
-        "value": comparisons / (ms * 1e-3), "unit": "comparisons/s", "n_gpus": 1, "steps": args.steps,
+        "metric": "path-pair similarities/s (every pair of trial paths)",
+        "value": len(pairs) / (ms * 1e-3), "unit": "path pairs/s", "n_gpus": 1, "steps": args.steps,
+        "definition_rate": {"value": comparisons / (ms * 1e-3), "unit": "ordered contact pairs/s",
+                            "note": "the definition's n_c (n_c - 1) comparisons per path pair / time"},
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "int64", "data": "synthetic",
         "config": {"workload": f"{len(seeds)} trials x 11 040 atoms, {n_c} native contacts, {len(pairs)} path pairs "
                                f"(formation times from 100 tracked steps)", "s_mean": float(np.mean(sim)),
                    "s_min": float(np.min(sim)), "s_max": float(np.max(sim))},
-        "note": "one call uploads the times, compares all ordered contact pairs of every path pair and reads back s",
+        "note": "one call ranks the times on the host, uploads the ranks, counts the agreeing ordered contact pairs "
+                "of every path pair (joint histogram of the ranks when the paths hold few distinct times) and reads back s",
     }
     print(json.dumps(line))
     return 0

@@ -299,10 +299,16 @@ int sim_native_contacts(sim_handle *h, int32_t trial, int32_t *pairs, int64_t ca
 int sim_contact_times(sim_handle *h, int32_t trial, int64_t *times, int64_t cap);
 
 /* Path similarity on the GPU: times [n_paths][n_c] formation times (HOST,
- * read), pairs [2*n_pairs] path indices (HOST), s [n_pairs] (HOST, written):
- * s(pairs[2q], pairs[2q+1]).  n_c < 2 gives 1 (no ordered pair).  At most
- * 65535 pairs per call; times must be below 2^31 - 1 (steps).  Returns
- * SIM_OK, SIM_EINVAL or SIM_ECUDA. */
+ * read; a negative time: not formed, ordered after every formed contact),
+ * pairs [2*n_pairs] path indices (HOST), s [n_pairs] (HOST, written):
+ * s(pairs[2q], pairs[2q+1]).  Only the order of the times within a path
+ * enters s, so the host replaces them by dense ranks.  A path pair whose
+ * paths hold K_a and K_b distinct times with K_a K_b <= 4096 is counted from
+ * the joint histogram of its ranks (every pair of contacts in one cell ties
+ * in both paths, pairs of cells strictly below-left / above-right are
+ * concordant); other pairs compare all ordered contact pairs.  Both counts
+ * are exact.  n_c < 2 gives 1 (no ordered pair); n_c <= 2^30.  At most 65535
+ * pairs per call.  Returns SIM_OK, SIM_EINVAL or SIM_ECUDA. */
 int path_similarity(const int64_t *times, int32_t n_paths, int64_t n_c, const int32_t *pairs, int32_t n_pairs,
                     double *s, void *cuda_stream, char *errbuf, int32_t errlen);
 

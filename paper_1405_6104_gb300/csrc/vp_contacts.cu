@@ -11,9 +11,18 @@
 // error) decides alone.  The formation time of a native contact is the step
 // from which it has stayed formed (-1: not formed at the last check); checks
 // run every `every` steps.
+//
+// The similarity of two paths counts the ordered contact pairs on which
+// their order relations agree.  Only the order of the times within a path
+// matters, so the host replaces them by dense ranks; with few distinct times
+// (formation times are check steps) the count comes from the joint histogram
+// of the two rank arrays in O(n_c + K_a K_b), otherwise from all n_c^2
+// ordered pairs.
+#include <algorithm>
 #include <climits>
 #include <cstring>
 #include <string>
+#include <vector>
 
 #include "../../include/vpath.h"
 #include "vp_contacts.cuh"
@@ -73,30 +82,28 @@ void launch_contacts(const Dev &d, const ContactDev &c, cudaStream_t s) {
 namespace {
 
 constexpr int SIM_TILE = 2048;
+constexpr int HIST_CELLS = 4096;  // joint histogram capacity (K_a x K_b) of the counting kernel
 
-// formation steps as 32-bit order keys: -1 (not formed) orders last; the
-// caller guarantees steps below 2^31 - 1
-__device__ __forceinline__ int order_key(long long t) { return t < 0 ? INT_MAX : (int)t; }
-
-// sign of a - b in {-1, 0, 1} for keys of the same sign class (no overflow: 0 <= keys <= INT_MAX)
+// sign of a - b in {-1, 0, 1}
 __device__ __forceinline__ int cmp3(int a, int b) { return (a > b) - (a < b); }
 
-// one (path pair, block of i) per block: counts the ordered pairs (i != j)
-// on which the two paths' order relations agree
-__global__ void __launch_bounds__(256) k_similarity(const long long *__restrict__ t, long long n_c,
+// all ordered pairs: one (path pair, block of i) per block counts the pairs
+// (i != j) on which the two paths' order relations agree; keys are the
+// paths' dense ranks (order-preserving, unformed contacts last)
+__global__ void __launch_bounds__(256) k_similarity(const int *__restrict__ rk, long long n_c,
                                                     const int2 *__restrict__ pp, unsigned long long *count) {
   __shared__ int2 sab[SIM_TILE];
   __shared__ unsigned long long red[256];
   const int2 ab = pp[blockIdx.y];
-  const long long *ta = t + (size_t)ab.x * (size_t)n_c, *tb = t + (size_t)ab.y * (size_t)n_c;
+  const int *ta = rk + (size_t)ab.x * (size_t)n_c, *tb = rk + (size_t)ab.y * (size_t)n_c;
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const int ai = i < n_c ? order_key(ta[i]) : 0, bi = i < n_c ? order_key(tb[i]) : 0;
+  const int ai = i < n_c ? ta[i] : 0, bi = i < n_c ? tb[i] : 0;
   unsigned int cnt = 0;  // per thread: at most n_c < 2^31
   for (long long j0 = 0; j0 < n_c; j0 += SIM_TILE) {
     __syncthreads();
     for (int q = threadIdx.x; q < SIM_TILE; q += blockDim.x) {
       const long long j = j0 + q;
-      sab[q] = j < n_c ? make_int2(order_key(ta[j]), order_key(tb[j])) : make_int2(0, 0);
+      sab[q] = j < n_c ? make_int2(ta[j], tb[j]) : make_int2(0, 0);
     }
     __syncthreads();
     if (i < n_c) {
@@ -117,6 +124,69 @@ __global__ void __launch_bounds__(256) k_similarity(const long long *__restrict_
     __syncthreads();
   }
   if (threadIdx.x == 0) atomicAdd(count + blockIdx.y, red[0]);
+}
+
+// few distinct times (K_a K_b <= HIST_CELLS): one block per path pair counts
+// the same agreements from the joint histogram H[x][y] of the two paths'
+// ranks.  Two contacts in one cell tie in both paths (M = 1/2 in both:
+// c (c - 1) ordered pairs agree); two contacts in cells strictly below-left
+// and above-right of each other are concordant (both ordered pairs agree);
+// every other pair disagrees.  So the count is sum c (c - 1) + 2 sum c P,
+// with P the number of contacts strictly below-left of the cell.
+__global__ void __launch_bounds__(256) k_similarity_hist(const int *__restrict__ rk, long long n_c,
+                                                         const int2 *__restrict__ pp, const int *__restrict__ kk,
+                                                         const int *__restrict__ list,
+                                                         unsigned long long *count) {
+  __shared__ unsigned H[HIST_CELLS];
+  __shared__ unsigned long long red[256];
+  const int q = list[blockIdx.x];
+  const int2 ab = pp[q];
+  const int Ka = kk[ab.x], Kb = kk[ab.y], nc = Ka * Kb;
+  const int *ta = rk + (size_t)ab.x * (size_t)n_c, *tb = rk + (size_t)ab.y * (size_t)n_c;
+  for (int c = threadIdx.x; c < nc; c += blockDim.x) H[c] = 0u;
+  __syncthreads();
+  for (long long i = threadIdx.x; i < n_c; i += blockDim.x) atomicAdd(&H[ta[i] * Kb + tb[i]], 1u);
+  __syncthreads();
+  // P over the grid, in place, after each cell's own count has been used:
+  // first the row prefix sums (exclusive along y), then the column ones
+  // (exclusive along x) of those: then the cell holds the contacts strictly
+  // below-left.  The cell counts are needed twice, so they are kept aside.
+  unsigned long long acc = 0;
+  for (int c = threadIdx.x; c < nc; c += blockDim.x) {
+    const unsigned long long v = H[c];
+    acc += v * (v - (v > 0 ? 1ull : 0ull));
+  }
+  // row prefix (exclusive) per x: one thread per row
+  __syncthreads();
+  __shared__ unsigned rowcnt[HIST_CELLS];
+  for (int c = threadIdx.x; c < nc; c += blockDim.x) rowcnt[c] = H[c];
+  __syncthreads();
+  for (int x = threadIdx.x; x < Ka; x += blockDim.x) {
+    unsigned run = 0;
+    for (int y = 0; y < Kb; ++y) {
+      const unsigned v = H[x * Kb + y];
+      H[x * Kb + y] = run;
+      run += v;
+    }
+  }
+  __syncthreads();
+  for (int y = threadIdx.x; y < Kb; y += blockDim.x) {
+    unsigned run = 0;
+    for (int x = 0; x < Ka; ++x) {
+      const unsigned v = H[x * Kb + y];
+      H[x * Kb + y] = run;
+      run += v;
+    }
+  }
+  __syncthreads();
+  for (int c = threadIdx.x; c < nc; c += blockDim.x) acc += 2ull * (unsigned long long)rowcnt[c] * H[c];
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int off = blockDim.x / 2; off > 0; off >>= 1) {
+    if (threadIdx.x < off) red[threadIdx.x] += red[threadIdx.x + off];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) count[q] = red[0];
 }
 
 int put_err(char *errbuf, int32_t errlen, int code, const std::string &msg) {
@@ -147,42 +217,89 @@ extern "C" __attribute__((visibility("default"))) int path_similarity(const int6
     return SIM_OK;
   }
   if (n_c > (1ll << 30)) return put_err(errbuf, errlen, SIM_EINVAL, "path_similarity: too many contacts");
-  for (size_t k = 0; k < (size_t)n_paths * (size_t)n_c; ++k)
-    if (times[k] >= (int64_t)INT_MAX) return put_err(errbuf, errlen, SIM_EINVAL, "path_similarity: step >= 2^31 - 1");
   if (n_pairs > 65535) return put_err(errbuf, errlen, SIM_EINVAL, "path_similarity: at most 65535 pairs per call");
+  // dense ranks per path (order-preserving; a negative time, not formed,
+  // ranks after every formed contact): only the order relations enter s
+  const size_t nt = (size_t)n_paths * (size_t)n_c;
+  std::vector<int> rk(nt), K(n_paths);
+  {
+    std::vector<int64_t> v((size_t)n_c);
+    for (int32_t p = 0; p < n_paths; ++p) {
+      const int64_t *tp = times + (size_t)p * (size_t)n_c;
+      for (int64_t i = 0; i < n_c; ++i) v[(size_t)i] = tp[i] < 0 ? INT64_MAX : tp[i];
+      std::vector<int64_t> u(v);
+      std::sort(u.begin(), u.end());
+      u.erase(std::unique(u.begin(), u.end()), u.end());
+      K[p] = (int)u.size();
+      for (int64_t i = 0; i < n_c; ++i)
+        rk[(size_t)p * (size_t)n_c + (size_t)i] = (int)(std::lower_bound(u.begin(), u.end(), v[(size_t)i]) - u.begin());
+    }
+  }
+  // path pairs with few distinct times take the counting kernel, the rest
+  // compare all ordered contact pairs
+  std::vector<int> hist_list, all_list;
+  for (int32_t q = 0; q < n_pairs; ++q) {
+    const long long cells = (long long)K[pairs[2 * q]] * (long long)K[pairs[2 * q + 1]];
+    (cells <= HIST_CELLS ? hist_list : all_list).push_back(q);
+  }
+  std::vector<int2> all_pp;
+  for (int q : all_list) all_pp.push_back(make_int2(pairs[2 * q], pairs[2 * q + 1]));
   cudaStream_t st = (cudaStream_t)cuda_stream;
-  long long *dt = nullptr;
-  int2 *dp = nullptr;
-  unsigned long long *dc = nullptr;
+  int *dr = nullptr, *dk = nullptr, *dl = nullptr;
+  int2 *dp = nullptr, *dpa = nullptr;
+  unsigned long long *dc = nullptr, *dca = nullptr;
   std::string err;
   auto ck = [&](cudaError_t e, const char *what) {
     if (e != cudaSuccess && err.empty()) err = std::string(what) + ": " + cudaGetErrorString(e);
     return e == cudaSuccess;
   };
-  const size_t nt = (size_t)n_paths * (size_t)n_c;
-  bool ok = ck(cudaMalloc(&dt, nt * sizeof(long long)), "cudaMalloc") &&
-            ck(cudaMalloc(&dp, (size_t)n_pairs * sizeof(int2)), "cudaMalloc") &&
-            ck(cudaMalloc(&dc, (size_t)n_pairs * sizeof(unsigned long long)), "cudaMalloc");
-  ok = ok && ck(cudaMemcpyAsync(dt, times, nt * sizeof(long long), cudaMemcpyHostToDevice, st), "cudaMemcpyAsync") &&
-       ck(cudaMemcpyAsync(dp, pairs, (size_t)n_pairs * sizeof(int2), cudaMemcpyHostToDevice, st), "cudaMemcpyAsync") &&
-       ck(cudaMemsetAsync(dc, 0, (size_t)n_pairs * sizeof(unsigned long long), st), "cudaMemsetAsync");
-  if (ok) {
-    dim3 grid((unsigned)((n_c + 255) / 256), (unsigned)n_pairs);
-    k_similarity<<<grid, 256, 0, st>>>(dt, (long long)n_c, dp, dc);
-    ok = ck(cudaGetLastError(), "k_similarity launch");
+  const size_t np = (size_t)n_pairs, na = all_list.size(), nh = hist_list.size();
+  bool ok = ck(cudaMalloc(&dr, nt * sizeof(int)), "cudaMalloc") &&
+            ck(cudaMalloc(&dk, (size_t)n_paths * sizeof(int)), "cudaMalloc") &&
+            ck(cudaMalloc(&dp, np * sizeof(int2)), "cudaMalloc") &&
+            ck(cudaMalloc(&dc, np * sizeof(unsigned long long)), "cudaMalloc") &&
+            (nh == 0 || ck(cudaMalloc(&dl, nh * sizeof(int)), "cudaMalloc")) &&
+            (na == 0 || (ck(cudaMalloc(&dpa, na * sizeof(int2)), "cudaMalloc") &&
+                         ck(cudaMalloc(&dca, na * sizeof(unsigned long long)), "cudaMalloc")));
+  ok = ok && ck(cudaMemcpyAsync(dr, rk.data(), nt * sizeof(int), cudaMemcpyHostToDevice, st), "cudaMemcpyAsync") &&
+       ck(cudaMemcpyAsync(dk, K.data(), (size_t)n_paths * sizeof(int), cudaMemcpyHostToDevice, st), "cudaMemcpyAsync") &&
+       ck(cudaMemcpyAsync(dp, pairs, np * sizeof(int2), cudaMemcpyHostToDevice, st), "cudaMemcpyAsync");
+  if (ok && nh > 0) {
+    ok = ck(cudaMemcpyAsync(dl, hist_list.data(), nh * sizeof(int), cudaMemcpyHostToDevice, st), "cudaMemcpyAsync");
+    if (ok) {
+      k_similarity_hist<<<(unsigned)nh, 256, 0, st>>>(dr, (long long)n_c, dp, dk, dl, dc);
+      ok = ck(cudaGetLastError(), "k_similarity_hist launch");
+    }
   }
-  unsigned long long *hc = new unsigned long long[(size_t)n_pairs];
-  ok = ok && ck(cudaMemcpyAsync(hc, dc, (size_t)n_pairs * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st),
-                "cudaMemcpyAsync");
+  if (ok && na > 0) {
+    ok = ck(cudaMemcpyAsync(dpa, all_pp.data(), na * sizeof(int2), cudaMemcpyHostToDevice, st), "cudaMemcpyAsync") &&
+         ck(cudaMemsetAsync(dca, 0, na * sizeof(unsigned long long), st), "cudaMemsetAsync");
+    if (ok) {
+      dim3 grid((unsigned)((n_c + 255) / 256), (unsigned)na);
+      k_similarity<<<grid, 256, 0, st>>>(dr, (long long)n_c, dpa, dca);
+      ok = ck(cudaGetLastError(), "k_similarity launch");
+    }
+  }
+  std::vector<unsigned long long> hc(np, 0ull), ha(na, 0ull);
+  if (ok && nh > 0)
+    ok = ck(cudaMemcpyAsync(hc.data(), dc, np * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st),
+            "cudaMemcpyAsync");
+  if (ok && na > 0)
+    ok = ck(cudaMemcpyAsync(ha.data(), dca, na * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st),
+            "cudaMemcpyAsync");
   ck(cudaStreamSynchronize(st), "cudaStreamSynchronize");
   if (ok && err.empty()) {
+    for (size_t k = 0; k < na; ++k) hc[(size_t)all_list[k]] = ha[k];
     const double denom = (double)n_c * (double)(n_c - 1);
-    for (int32_t q = 0; q < n_pairs; ++q) s[q] = (double)hc[q] / denom;
+    for (int32_t q = 0; q < n_pairs; ++q) s[q] = (double)hc[(size_t)q] / denom;
   }
-  delete[] hc;
-  cudaFree(dt);
+  cudaFree(dr);
+  cudaFree(dk);
   cudaFree(dp);
   cudaFree(dc);
+  cudaFree(dl);
+  cudaFree(dpa);
+  cudaFree(dca);
   if (!err.empty()) return put_err(errbuf, errlen, SIM_ECUDA, "path_similarity: " + err);
   return SIM_OK;
 }

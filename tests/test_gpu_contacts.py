@@ -61,6 +61,23 @@ def test_similarity_matches_the_oracle():
     assert np.array_equal(B.path_similarity(T[:, :1], [(0, 1)]), [1.0])  # one contact: no ordered pair
 
 
+def test_similarity_both_counting_paths_match_the_oracle():
+    """Path pairs with few distinct times (joint-histogram count) and with
+    many (all ordered contact pairs), in one call, exact against the oracle;
+    times of any size (only their order in a path matters), ties, and
+    negative values of any kind as 'not formed'."""
+    rng = np.random.default_rng(11)
+    n_c = 900
+    few = [rng.integers(-1, 30, n_c) for _ in range(3)]                      # <= 31 distinct each
+    many = [rng.permutation(n_c) * 7919 + (1 << 40) for _ in range(2)]      # all distinct, beyond 2^31
+    many.append(np.where(rng.random(n_c) < 0.2, -5, rng.integers(0, 10 ** 12, n_c)))
+    T = np.stack(few + many).astype(np.int64)
+    pairs = [(a, b) for a in range(len(T)) for b in range(len(T)) if a != b]
+    s_gpu = B.path_similarity(T, pairs)
+    for (a, b), v in zip(pairs, s_gpu):
+        assert v == O.path_similarity(np.where(T[a] < 0, -1, T[a]), np.where(T[b] < 0, -1, T[b])), (a, b)
+
+
 def test_similarity_of_trials_at_full_size():
     """The 11 040-atom system (23 160 native contacts): formation times of a
     few trials and their pairwise similarities, GPU against the oracle."""
