@@ -22,6 +22,7 @@
 #include <climits>
 #include <cstring>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "../../include/vpath.h"
@@ -223,17 +224,26 @@ extern "C" __attribute__((visibility("default"))) int path_similarity(const int6
   const size_t nt = (size_t)n_paths * (size_t)n_c;
   std::vector<int> rk(nt), K(n_paths);
   {
-    std::vector<int64_t> v((size_t)n_c);
-    for (int32_t p = 0; p < n_paths; ++p) {
-      const int64_t *tp = times + (size_t)p * (size_t)n_c;
-      for (int64_t i = 0; i < n_c; ++i) v[(size_t)i] = tp[i] < 0 ? INT64_MAX : tp[i];
-      std::vector<int64_t> u(v);
-      std::sort(u.begin(), u.end());
-      u.erase(std::unique(u.begin(), u.end()), u.end());
-      K[p] = (int)u.size();
-      for (int64_t i = 0; i < n_c; ++i)
-        rk[(size_t)p * (size_t)n_c + (size_t)i] = (int)(std::lower_bound(u.begin(), u.end(), v[(size_t)i]) - u.begin());
-    }
+    // paths are ranked independently, on up to 16 host threads
+    auto rank_paths = [&](int32_t p0, int32_t p1) {
+      std::vector<int64_t> v((size_t)n_c), u;
+      for (int32_t p = p0; p < p1; ++p) {
+        const int64_t *tp = times + (size_t)p * (size_t)n_c;
+        for (int64_t i = 0; i < n_c; ++i) v[(size_t)i] = tp[i] < 0 ? INT64_MAX : tp[i];
+        u = v;
+        std::sort(u.begin(), u.end());
+        u.erase(std::unique(u.begin(), u.end()), u.end());
+        K[p] = (int)u.size();
+        for (int64_t i = 0; i < n_c; ++i)
+          rk[(size_t)p * (size_t)n_c + (size_t)i] = (int)(std::lower_bound(u.begin(), u.end(), v[(size_t)i]) - u.begin());
+      }
+    };
+    const int nw = (int)std::max(1u, std::min({std::thread::hardware_concurrency(), 16u, (unsigned)n_paths}));
+    std::vector<std::thread> pool;
+    for (int w = 1; w < nw; ++w)
+      pool.emplace_back(rank_paths, (int32_t)((long long)n_paths * w / nw), (int32_t)((long long)n_paths * (w + 1) / nw));
+    rank_paths(0, (int32_t)((long long)n_paths / nw));
+    for (auto &th : pool) th.join();
   }
   // path pairs with few distinct times take the counting kernel, the rest
   // compare all ordered contact pairs
