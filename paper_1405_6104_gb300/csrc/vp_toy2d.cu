@@ -201,8 +201,10 @@ extern "C" __attribute__((visibility("default"))) int toy2d_run(const toy2d_para
   ok = ok && ck(cudaMemcpyAsync(dk, k, n * sizeof(double), cudaMemcpyHostToDevice, st), "cudaMemcpyAsync") &&
        ck(cudaMemcpyAsync(dseed, seeds, n * sizeof(uint64_t), cudaMemcpyHostToDevice, st), "cudaMemcpyAsync");
   if (ok) {
-    k_toy2d<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(c, n_trials, dk, dseed, (long long)n_steps, p->x0, p->y0,
-                                                          dstate, dphi, dpass, dpath, path_every, n_rec);
+    // one warp per block: the trials (a few per SM at most) spread evenly over
+    // the SMs, so no SM runs two blocks' worth of the FP64 pipe while others idle
+    k_toy2d<<<(unsigned)((n + 31) / 32), 32, 0, st>>>(c, n_trials, dk, dseed, (long long)n_steps, p->x0, p->y0,
+                                                      dstate, dphi, dpass, dpath, path_every, n_rec);
     ok = ck(cudaGetLastError(), "k_toy2d launch");
   }
   ok = ok && ck(cudaMemcpyAsync(phi, dphi, n * sizeof(double), cudaMemcpyDeviceToHost, st), "cudaMemcpyAsync") &&
