@@ -569,7 +569,7 @@ VP_API int sim_create(const sim_system *systems, int32_t n_systems, const int32_
         g.at[0] = S.angles[3 * a]; g.at[1] = S.angles[3 * a + 1]; g.at[2] = S.angles[3 * a + 2];
         g.n = 1;
         g.code[0] = 1 | (0 << 1) | (1 << 3) | (2 << 5);
-        g.par[0] = make_float2((float)S.angle_t0[a], (float)S.angle_k[a]);
+        g.par[0] = make_float4((float)S.angle_t0[a], (float)S.angle_k[a], 0.f, 0.f);
         for (int m = 0; m < 3; ++m) of_atom[g.at[m]].push_back((int)G.size());
         G.push_back(g);
       }
@@ -599,8 +599,8 @@ VP_API int sim_create(const sim_system *systems, int32_t n_systems, const int32_
             of_atom[atom].push_back(gi);
           }
         g.code[g.n] = 0 | (local(g, i) << 1) | (local(g, j) << 3);
-        g.par[g.n] = make_float2((float)S.bond_r0[b], (float)S.bond_k[b]);
-        g.x0lo[g.n] = (float)(S.bond_r0[b] - (double)g.par[g.n].x);
+        const float r0 = (float)S.bond_r0[b];
+        g.par[g.n] = make_float4(r0, (float)S.bond_k[b], (float)(S.bond_r0[b] - (double)r0), 0.f);
         g.n += 1;
       }
       for (auto &g : G) bgrp.push_back(g);

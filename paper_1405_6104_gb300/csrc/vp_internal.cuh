@@ -94,14 +94,13 @@ struct BTerm {
 // forces are summed per atom in fixed point before one reduction per atom
 // and component.  code[k] of term k < n: bit 0 kind (0 bond, 1 angle), bits
 // 1-2, 3-4, 5-6 the local atoms i, j, l (bond i-j; angle i-j-l, j the vertex)
-struct BGroup {
+struct __align__(16) BGroup {
   int32_t at[3];   // system atoms (at[2] = -1 for a two-atom group)
   int32_t n;       // terms, 1..3
   int32_t code[3];
   int32_t pad;
-  float2 par[3];   // {r0 or theta0, force constant}
-  float x0lo[3];   // r0 - par.x (a bond's rest length in float-float: k (r - r0) with k ~ 1e5 needs it)
-  int32_t pad2;
+  float4 par[3];   // {r0 or theta0, force constant, r0 - x (a bond's rest length in float-float:
+                   //  k (r - r0) with k ~ 1e5 needs it), 0}
 };
 
 struct SimConst {

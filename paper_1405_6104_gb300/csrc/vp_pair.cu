@@ -624,7 +624,7 @@ __global__ void __launch_bounds__(256) k_bonded(Dev d) {
   for (int q = 0; q < 3; ++q) {
     if (q >= G.n) break;
     const int code = G.code[q];
-    const float2 par = G.par[q];
+    const float4 par = G.par[q];
     const int li = (code >> 1) & 3, lj = (code >> 3) & 3, ll = (code >> 5) & 3;
     const float4 pa = pick3(p, li), pb = pick3(p, lj);
     if ((code & 1) == 0) {
@@ -632,7 +632,7 @@ __global__ void __launch_bounds__(256) k_bonded(Dev d) {
       const float nx = rintf((pb.x - pa.x) * iL), ny = rintf((pb.y - pa.y) * iL), nz = rintf((pb.z - pa.z) * iL);
       const ff dx = ff_diff(pb.x - L * nx, pa.x), dy = ff_diff(pb.y - L * ny, pa.y), dz = ff_diff(pb.z - L * nz, pa.z);
       const ff r = ff_sqrt(ff_add(ff_add(ff_sqr(dx), ff_sqr(dy)), ff_sqr(dz)));
-      const float dr = ff_add_f(ff_add_f(r, -par.x), -G.x0lo[q]).hi;  // r - r0 with r0 in float-float
+      const float dr = ff_add_f(ff_add_f(r, -par.x), -par.z).hi;  // r - r0 with r0 in float-float
       const float fs = par.y * dr / r.hi;  // force on a = +k dr (b - a)/r
       const long long fx = fx_from(fs * dx.hi), fy = fx_from(fs * dy.hi), fz = fx_from(fs * dz.hi);
       add3(F, li, fx, fy, fz);

@@ -53,7 +53,11 @@ __global__ void k_bin(Dev d, float half_skin2, int strict) {
   int cy = max(0, min((int)(y * T.inv_col_w), T.ncol - 1));
   int c = cx * T.ncol + cy;
   d.slot_col[slot] = c;
-  atomicAdd(&d.col_count[T.col0 + c], 1);
+  // slots are in column order from the last rebuild, so a warp's atoms fall
+  // into one or two columns: one atomic per column and warp
+  const int cg = T.col0 + c;
+  const unsigned peers = __match_any_sync(__activemask(), cg);
+  if ((threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&d.col_count[cg], __popc(peers));
 }
 
 // ---------------------------------------------------------------------------
@@ -123,7 +127,15 @@ __global__ void k_colfill(Dev d) {
   int t = d.slot_trial[slot];
   const TrialInfo &T = d.tinfo[t];
   int cg = T.col0 + c;
-  int p = atomicAdd(&d.col_fill[cg], 1);
+  // one atomic per column and warp; the lanes of a column take consecutive
+  // places (the order inside a bucket is irrelevant: the column sort orders it)
+  const unsigned act = __activemask();
+  const unsigned peers = __match_any_sync(act, cg);
+  const int lane = threadIdx.x & 31, leader = __ffs(peers) - 1;
+  int base = 0;
+  if (lane == leader) base = atomicAdd(&d.col_fill[cg], __popc(peers));
+  base = __shfl_sync(act, base, leader);
+  const int p = base + __popc(peers & ((1u << lane) - 1u));
   if (p < COL_CAP && d.col_count[cg] <= COL_CAP) d.bucket[T.atom0 + d.col_start[cg] + p] = slot;
 }
 
