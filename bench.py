@@ -207,6 +207,10 @@ def run_gpu(args):
     if world > 1:
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     import __graft_entry__
+    if world > 1:  # one rank per node compiles (the others would race on the object files)
+        if local == 0:
+            __graft_entry__.build()
+        dist.barrier()
     __graft_entry__.build()
     from paper_1405_6104_gb300 import binding as B
     from paper_1405_6104_gb300 import systems as S

@@ -41,8 +41,13 @@ def build(force: bool = False, verbose: bool = False) -> str:
         return LIB
     nvcc = _nvcc()
 
+    # objects of this process only (several processes may build at once; the
+    # library itself is replaced atomically)
+    objdir = os.path.join(OUT, f"obj.{os.getpid()}")
+    os.makedirs(objdir, exist_ok=True)
+
     def compile_one(src):
-        obj = os.path.join(OUT, os.path.basename(src).replace(".cu", ".o"))
+        obj = os.path.join(objdir, os.path.basename(src).replace(".cu", ".o"))
         cmd = [nvcc, *ARCH, *FLAGS, *EXTRA.get(os.path.basename(src), []), "-c", src, "-o", obj]
         if verbose:
             cmd.insert(1, "-Xptxas=-v")
@@ -62,6 +67,9 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
     os.replace(tmp, LIB)
+    for o, _ in results:
+        os.remove(o)
+    os.rmdir(objdir)
     return LIB
 
 
