@@ -575,7 +575,8 @@ def run_similarity(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=60,
+                    help="timed bench steps (60 x 10 MD steps keep the clock sampler inside the timed region)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--workload", default="batched64", choices=["batched64", "toy2d", "adjoint30k", "similarity"],
