@@ -115,6 +115,32 @@ def test_bonded_forces_alone(name):
                 assert np.abs(F.sum(axis=0)).max() == 0.0
 
 
+def test_many_lj_types_take_the_general_kernel():
+    """More distinct Lennard-Jones types than the packed kernels' tables hold
+    (16): the general pair kernel runs, with the same parity to the oracle,
+    and graph replay and direct launches stay bit-identical."""
+    s, p = S.small_solvated()
+    s = s.copy()
+    k = np.arange(s.n_solute) % 30
+    n0 = len(s.sigma)
+    s.sigma = np.concatenate([s.sigma, 0.30 + 0.002 * np.arange(30)])
+    s.epsilon = np.concatenate([s.epsilon, 0.40 + 0.01 * np.arange(30)])
+    s.lj_type = s.lj_type.copy()
+    s.lj_type[: s.n_solute] = n0 + k
+    results = []
+    for flags in (0, B.SIM_NO_GRAPH):
+        q = S.Params(**{**p.__dict__, "flags": flags})
+        with B.TrialBatch(s, q, [2], trial_seeds=[21, 22]) as b:
+            b.step(20)
+            pos, vel, cv = b.get_state(1)
+            e, F = b.energy_forces(1)
+            Fr, er = oracle_total_force(s, q, pos, cv[2])
+            assert rel_rms(F, Fr) < 1e-5
+            results.append([b.get_state(t) for t in range(2)])
+    for x, y in zip(*results):
+        assert np.array_equal(x[0], y[0]) and np.array_equal(x[1], y[1])
+
+
 @pytest.mark.parametrize("name", ["tiny", "small"])
 def test_trajectory_parity_100_steps(name):
     s, p = SYSTEMS[name]()
