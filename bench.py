@@ -487,8 +487,10 @@ def run_adjoint(args):
         stream = torch.cuda.ExternalStream(b.stream)
         for _ in range(args.warmup):
             trajectory_adjoint(b, 0, n_frames, every=every)
+        clocks = ClockSampler(local) if rank == 0 else None
         torch.cuda.synchronize()
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t_begin = time.time()
         t0 = time.perf_counter()
         ev0.record(stream)
         for _ in range(args.steps):
@@ -496,7 +498,9 @@ def run_adjoint(args):
         ev1.record(stream)
         torch.cuda.synchronize()
         wall = time.perf_counter() - t0
+        t_end = time.time()
         ms = ev0.elapsed_time(ev1)
+        clk = clocks.stop(t_begin, t_end) if clocks else None
         # where the time goes: one more run with per-kernel timing
         B.sim_set_timing(b.h, 1)
         B.sim_kernel_times(b.h)
@@ -506,6 +510,12 @@ def run_adjoint(args):
         kt = B.sim_kernel_times(b.h)
         B.sim_set_timing(b.h, 0)
     md_ms = sum(v[0] for v in kt.values())
+    pk, _ = peaks()
+    sm_mhz = pk.get("sm_max_mhz", 2070.0)
+    fp32_peak = 152 * 128 * 2 * sm_mhz * 1e6
+    pair_ms = kt["pair"][0] / kt["pair"][1]
+    pair_flops = s.n_atoms * PAIRS_PER_ATOM_STEP * FLOPS_PER_PAIR
+    n_seg = n_frames // every
     line = {
         "metric": "adjoint frames/s (gradient of the functional along a path, checkpointed replay)",
         "value": n_frames * args.steps / (ms * 1e-3), "unit": "frames/s", "n_gpus": 1, "steps": args.steps,
@@ -520,9 +530,37 @@ def run_adjoint(args):
         "kernel_ms": {k: v[0] / v[1] for k, v in kt.items() if v[1] > 0},
         "note": "1000 MD steps (forward + replay) of the 30 000-atom system per bench step; the rest is the "
                 "adjoint kernels, checkpoint transfers and the host loop",
+        "roofline": {"bound": "alu", "kernel": "pair (one 30 000-atom trial)", "achieved": pair_flops / (pair_ms * 1e-3) / 1e12,
+                     "peak": fp32_peak / 1e12, "unit": "TFLOP/s", "frac": pair_flops / (pair_ms * 1e-3) / fp32_peak,
+                     "traffic": None, "launch_ms": pair_ms,
+                     "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz",
+                     "work": f"{PAIRS_PER_ATOM_STEP:.0f} half pairs x {FLOPS_PER_PAIR:.0f} flops per atom-step",
+                     "launch_timing": "direct launches timed by CUDA events in a pass after the timed region"},
+        "cpu_baseline": adjoint_cpu_baseline(S, s, p),
+        # the step kernels of one gradient (from the timing pass) and the four
+        # adjoint kernels of each segment, over the timed gradients
+        "gpu_launches": args.steps * (int(sum(v[1] for v in kt.values())) + 4 * n_seg),
+        "clocks": clk,
     }
     print(json.dumps(line))
     return 0
+
+
+def adjoint_cpu_baseline(S, s, p, n_md: int = 10, n_grad: int = 10):
+    """The FP64 oracle on the host cores for one adjoint frame: two MD steps
+    (forward run and replay) and the gradient of Phi at one frame, from a
+    bounded sample (n_md MD steps, n_grad frames) of the same system."""
+    import oracle as O
+    t0 = time.perf_counter()
+    r = O.run(s, p, 3, n_md, record_every=1)
+    t_md = (time.perf_counter() - t0) / n_md
+    frames = np.asarray(r["frames"])[:n_grad] if "frames" in r else np.repeat(np.asarray(s.pos)[None], n_grad, 0)
+    t1 = time.perf_counter()
+    O.phi_frames_grad(s, p, frames)
+    t_grad = (time.perf_counter() - t1) / len(frames)
+    return {"value": 1.0 / (2 * t_md + t_grad), "unit": "frames/s", "cores": O.num_threads(), "kind": "oracle",
+            "sample": f"{n_md} MD steps and the gradient at {len(frames)} frames of the 30 000-atom system; "
+                      "one frame = 2 MD steps + its gradient"}
 
 
 def run_similarity(args):
@@ -546,14 +584,22 @@ def run_similarity(args):
     stream = torch.cuda.Stream()
     for _ in range(args.warmup):
         B.path_similarity(T, pairs, cuda_stream=stream.cuda_stream)
+    clocks = ClockSampler(local) if rank == 0 else None
     torch.cuda.synchronize()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t_begin = time.time()
     ev0.record(stream)
     for _ in range(args.steps):
         sim = B.path_similarity(T, pairs, cuda_stream=stream.cuda_stream)
     ev1.record(stream)
     torch.cuda.synchronize()
+    t_end = time.time()
+    clk = clocks.stop(t_begin, t_end) if clocks else None
     ms = ev0.elapsed_time(ev1) / args.steps
+    import oracle as O
+    t0 = time.perf_counter()
+    O.path_similarity(T[0], T[1])
+    t_or = time.perf_counter() - t0
     comparisons = float(len(pairs)) * n_c * (n_c - 1)
     line = {
         "metric": "path-pair similarities/s (every pair of trial paths)",
@@ -567,6 +613,10 @@ def run_similarity(args):
                    "s_min": float(np.min(sim)), "s_max": float(np.max(sim))},
         "note": "one call ranks the times on the host, uploads the ranks, counts the agreeing ordered contact pairs "
                 "of every path pair (joint histogram of the ranks when the paths hold few distinct times) and reads back s",
+        "cpu_baseline": {"value": 1.0 / t_or, "unit": "path pairs/s", "cores": 1, "kind": "oracle",
+                         "sample": f"one path pair, all {n_c * (n_c - 1)} ordered contact pairs (the definition)"},
+        "gpu_launches": args.steps * (1 if all(len(set(r)) * len(set(r)) <= 4096 for r in T) else 2),
+        "clocks": clk
     }
     print(json.dumps(line))
     return 0
