@@ -189,10 +189,15 @@ __global__ void __launch_bounds__(CV_WARPS * 32) k_cv(Dev d, SimConst c) {
   if (lane == 0) d.z_part[w] = zl;
 }
 
-// per trial: z, the ratchet amplitude a, z_m and Phi (Eqs. VR, VMDcondition)
+// per trial: z, the ratchet amplitude a, z_m and Phi (Eqs. VR, VMDcondition).
+// One block per trial; the block size is fixed (not chosen by batch size), so
+// the reduction order, and with it every trial's z, does not depend on the
+// batch.  1024 threads keep a single trial's gather and sum short.
+constexpr int CVFIN_THREADS = 1024;
+
 template <int MODE>
-__global__ void __launch_bounds__(256) k_cvfin(Dev d, SimConst c) {
-  __shared__ double rz[256], rq[256];
+__global__ void __launch_bounds__(CVFIN_THREADS) k_cvfin(Dev d, SimConst c) {
+  __shared__ double rz[CVFIN_THREADS], rq[CVFIN_THREADS];
   __shared__ bool last;
   const int t = blockIdx.x;
   const TrialInfo T = d.tinfo[t];
@@ -285,9 +290,9 @@ void launch_cv(const Dev &d, const SimConst &c, cudaStream_t s, int variant) {
   else k_cv<4><<<(unsigned)((d.total_work + 3) / 4), 128, 0, s>>>(d, c);
 }
 void launch_cvfin(const Dev &d, const SimConst &c, FinMode mode, cudaStream_t s) {
-  if (mode == FIN_STEP) k_cvfin<FIN_STEP><<<d.n_trials, 256, 0, s>>>(d, c);
-  else if (mode == FIN_INIT) k_cvfin<FIN_INIT><<<d.n_trials, 256, 0, s>>>(d, c);
-  else k_cvfin<FIN_RESTORE><<<d.n_trials, 256, 0, s>>>(d, c);
+  if (mode == FIN_STEP) k_cvfin<FIN_STEP><<<d.n_trials, CVFIN_THREADS, 0, s>>>(d, c);
+  else if (mode == FIN_INIT) k_cvfin<FIN_INIT><<<d.n_trials, CVFIN_THREADS, 0, s>>>(d, c);
+  else k_cvfin<FIN_RESTORE><<<d.n_trials, CVFIN_THREADS, 0, s>>>(d, c);
 }
 
 }  // namespace vp
