@@ -151,6 +151,18 @@ int64_t sim_step_count(const sim_handle *h);
  * multiples of nstlist of this counter. */
 int sim_set_step_count(sim_handle *h, int64_t step);
 
+/* Noise counter offset of one trial: its Langevin noise of step n is drawn
+ * with the Philox counter of step n + offset (Eq. Lang; the noise is a
+ * function of (trial seed, atom, step) only).  0 at creation.  A batch that
+ * replays segments of one trajectory side by side (each segment a trial with
+ * the original seed) sets each segment's start step as its offset, so every
+ * segment draws the noise of the original run.  SIM_EINVAL for a bad trial. */
+int sim_set_noise_offset(sim_handle *h, int32_t trial, int64_t offset);
+
+/* The Philox key (seed) of a trial: trial_seeds[trial] at creation, or
+ * params->seed + trial.  SIM_EINVAL for a bad trial or NULL seed. */
+int sim_trial_seed(sim_handle *h, int32_t trial, uint64_t *seed);
+
 int32_t sim_num_trials(const sim_handle *h);
 int32_t sim_num_atoms(const sim_handle *h, int32_t trial);
 
@@ -164,7 +176,9 @@ int sim_get_record(sim_handle *h, int32_t trial, double *out /* [5*capacity] */)
 /* Per-step record of the reaction-coordinate atom positions of one trial
  * (the frames X_n of the path): capacity frames, the frame of step n at index
  * n % capacity, written after every force evaluation (also at sim_set_state).
- * sim_get_frames copies [capacity][n_cv][3] (nm) to out. */
+ * sim_get_frames copies [capacity][n_cv][3] (nm) to out.  trial = -1 records
+ * every trial: out is then [n_trials][capacity][m][3], m the largest n_cv of
+ * the batch (a trial with fewer CV atoms leaves the rest of its rows 0). */
 int sim_record_frames(sim_handle *h, int32_t trial, int32_t capacity);
 int sim_get_frames(sim_handle *h, double *out);
 

@@ -12,13 +12,18 @@ of one trial, computed entirely by the library's kernels:
    and Q_n of the trial;
 2. the coefficients A_n, B_n of dPhi/dX_n = A_n grad z + B_n H_z w follow
    from the record (``phi_adjoint_coefficients``);
-3. reverse: segment by segment, from the last one back, the checkpoint is
-   restored and the segment re-run with the frame recorder on (bit-identical
-   to the forward run: same list schedule, same call boundaries, counter-based
-   noise), and ``phi_frames_adjoint`` turns the segment's frames into
-   gradients.
+3. replay: each segment is re-run from its checkpoint with the frame
+   recorder on, bit-identical to the forward run (same list schedule, same
+   call boundaries, counter-based noise).  By default the segments are
+   replayed side by side as the trials of a second batch of the trial's
+   system ("batched": every trial carries the original seed and its
+   segment's start step as noise offset, so it draws the original noise;
+   trials of a batch do not influence each other), up to ``group`` segments
+   per call; "sequential" restores and re-runs them one after another on the
+   original batch;
+4. ``phi_frames_adjoint`` turns each segment's frames into gradients.
 
-Only ``every`` + 1 frames and the checkpoints are held at a time.
+Only the frames of the segments being replayed and the checkpoints are held.
 """
 from __future__ import annotations
 
@@ -44,10 +49,51 @@ def _restore(batch, ck):
     B.sim_set_state(batch.h, -1, pos, vel, cv)
 
 
-def trajectory_adjoint(batch, trial: int, n_steps: int, every: int = 50, keep_frames: bool = False):
+def _replay_batch(batch, trial: int, size: int):
+    """A batch of `size` trials of `trial`'s system with its seed, kept on
+    the batch object for later calls."""
+    cache = batch.__dict__.setdefault("_replay_batches", {})
+    key = (trial, size)
+    if key not in cache:
+        sys_ = batch.systems[_system_of(batch, trial)]
+        seed = B.sim_trial_seed(batch.h, trial)
+        rb = B.TrialBatch(sys_, batch.params, [size], trial_seeds=[seed] * size)
+        B.sim_autotune(rb.h, 3, None)  # launch shapes for this batch size (all give the same results)
+        cache[key] = rb
+    return cache[key]
+
+
+def _replay_group(batch, trial, ckpts, segs, every, n_cv, group):
+    """Frames (len(segs), every + 1, n_cv, 3) of the segments `segs`, replayed
+    side by side from their checkpoints."""
+    rb = _replay_batch(batch, trial, group)
+    h = rb.h
+    B.sim_record_frames(h, -1, every + 1)
+    B.sim_set_step_count(h, 0)
+    # padding trials (a short last group) replay the group's first segment
+    src = list(segs) + [segs[0]] * (group - len(segs))
+    for k, sg in enumerate(src):
+        B.sim_set_noise_offset(h, k, ckpts[sg][0])
+    states = [ckpts[sg][1][trial] for sg in src]
+    pos = np.concatenate([st[0] for st in states])
+    vel = np.concatenate([st[1] for st in states])
+    cv = np.array([[st[2][1], st[2][3]] for st in states])
+    B.sim_set_state(h, -1, pos, vel, cv)
+    rb.step(every)
+    fr = B.sim_get_frames(h, every + 1, n_cv, group)
+    B.sim_record_frames(h, -1, 0)
+    return fr[: len(segs)]
+
+
+def trajectory_adjoint(batch, trial: int, n_steps: int, every: int = 50, keep_frames: bool = False,
+                       replay: str = "batched", group: int = 16):
     """Runs the batch n_steps forward and returns (Phi over the path, dPhi/dX
     of shape (n_steps + 1, n_cv, 3), info).  The batch ends in its forward
-    end state.  info holds the forward and replayed frames when keep_frames."""
+    end state.  info holds the forward and replayed frames when keep_frames.
+    replay: "batched" (segments side by side, up to `group` per call, on a
+    second batch kept with this one) or "sequential"."""
+    if replay not in ("batched", "sequential"):
+        raise ValueError("replay must be 'batched' or 'sequential'")
     h = batch.h
     nst = batch.params.nstlist
     step0 = B.sim_step_count(h)
@@ -76,28 +122,38 @@ def trajectory_adjoint(batch, trial: int, n_steps: int, every: int = 50, keep_fr
         fwd = fr[[(step0 + k) % cap for k in range(n_steps + 1)]]
         fwd[0] = ckpts[0][1][trial][0][:n_cv]  # the start state was computed before recording began
         info["forward_frames"] = fwd
-    # reverse sweep over the segments
     grad = np.zeros((n_steps + 1, n_cv, 3))
-    replay = np.zeros((n_steps + 1, n_cv, 3)) if keep_frames else None
-    B.sim_record_frames(h, trial, every + 1)
-    for s in reversed(range(nseg)):
-        _restore(batch, ckpts[s])
-        batch.step(every)
-        seg_step0 = ckpts[s][0]
-        fr = B.sim_get_frames(h, every + 1, n_cv)
-        order = [(seg_step0 + k) % (every + 1) for k in range(every + 1)]
+    replayed = np.zeros((n_steps + 1, n_cv, 3)) if keep_frames else None
+
+    def consume(s, seg_frames):
+        # seg_frames[k]: the frame of step ckpt_s + k, k = 0 .. every
         lo = 0 if s == 0 else 1
-        frames = fr[order[lo:]]
-        g0 = s * every + lo
-        rows = slice(g0, s * every + every + 1)
+        frames = seg_frames[lo:]
+        rows = slice(s * every + lo, s * every + every + 1)
         _, _, G = B.phi_frames_adjoint(h, trial, frames, coef=coef[rows])
         grad[rows] = G
         if keep_frames:
-            replay[rows] = frames
-    B.sim_record_frames(h, trial, 0)
-    _restore(batch, ckpts[-1])
+            replayed[rows] = frames
+
+    if replay == "batched":
+        g = max(1, min(group, nseg))
+        for s0 in range(0, nseg, g):
+            segs = list(range(s0, min(s0 + g, nseg)))
+            fr = _replay_group(batch, trial, ckpts, segs, every, n_cv, g)
+            for k, s in enumerate(segs):
+                consume(s, fr[k])
+    else:
+        B.sim_record_frames(h, trial, every + 1)
+        for s in reversed(range(nseg)):
+            _restore(batch, ckpts[s])
+            batch.step(every)
+            seg_step0 = ckpts[s][0]
+            fr = B.sim_get_frames(h, every + 1, n_cv)
+            consume(s, fr[[(seg_step0 + k) % (every + 1) for k in range(every + 1)]])
+        B.sim_record_frames(h, trial, 0)
+        _restore(batch, ckpts[-1])
     if keep_frames:
-        info["replayed_frames"] = replay
+        info["replayed_frames"] = replayed
     return phi, grad, info
 
 

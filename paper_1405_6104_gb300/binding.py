@@ -77,6 +77,8 @@ _SIGS = {
     "sim_set_state": ([C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
     "sim_step_count": ([C.c_void_p], C.c_int64),
     "sim_set_step_count": ([C.c_void_p, C.c_int64], C.c_int),
+    "sim_set_noise_offset": ([C.c_void_p, C.c_int32, C.c_int64], C.c_int),
+    "sim_trial_seed": ([C.c_void_p, C.c_int32, C.c_void_p], C.c_int),
     "sim_num_trials": ([C.c_void_p], C.c_int32),
     "sim_num_atoms": ([C.c_void_p, C.c_int32], C.c_int32),
     "sim_record": ([C.c_void_p, C.c_int32], C.c_int),
@@ -252,10 +254,23 @@ def sim_record_frames(h, trial: int, capacity: int):
     _check(h, load().sim_record_frames(h, int(trial), int(capacity)))
 
 
-def sim_get_frames(h, capacity: int, n_cv: int):
-    out = np.zeros((capacity, n_cv, 3))
+def sim_get_frames(h, capacity: int, n_cv: int, n_trials: int = 0):
+    """The frame record: (capacity, n_cv, 3) for one recorded trial, or
+    (n_trials, capacity, n_cv, 3) when every trial is recorded (n_cv then the
+    largest of the batch)."""
+    out = np.zeros((n_trials, capacity, n_cv, 3) if n_trials else (capacity, n_cv, 3))
     _check(h, load().sim_get_frames(h, out.ctypes.data))
     return out
+
+
+def sim_set_noise_offset(h, trial: int, offset: int):
+    _check(h, load().sim_set_noise_offset(h, int(trial), int(offset)))
+
+
+def sim_trial_seed(h, trial: int) -> int:
+    v = C.c_uint64(0)
+    _check(h, load().sim_trial_seed(h, int(trial), C.byref(v)))
+    return int(v.value)
 
 
 def phi_frames_adjoint(h, trial: int, frames, coef=None):
@@ -460,6 +475,8 @@ class TrialBatch:
         return sim_stream(self.h)
 
     def close(self):
+        for rb in self.__dict__.pop("_replay_batches", {}).values():
+            rb.close()
         if self.h is not None:
             sim_destroy(self.h)
             self.h = None

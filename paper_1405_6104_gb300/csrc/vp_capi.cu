@@ -218,13 +218,22 @@ void cv_forces(sim_handle *h, FinMode mode, cudaStream_t s) {
   timed(h, "cvfin", [&] { launch_cvfin(h->d, h->c, mode, s); });
 }
 
+// reaction-coordinate atoms per frame: of the recorded trial, or the largest
+// n_cv when every trial is recorded (frame_trial < 0)
+int frame_stride(const sim_handle *h) {
+  if (h->frame_trial >= 0) return h->tinfo[h->frame_trial].n_cv;
+  int m = 0;
+  for (const auto &T : h->tinfo) m = std::max(m, T.n_cv);
+  return m;
+}
+
 // what follows the forces: contact tracking and the frame recorder read the
 // step counter that the CV finaliser has advanced
 void after_forces(sim_handle *h, FinMode mode) {
   cudaStream_t s = h->stream;
   if (mode == FIN_STEP && h->cdev.every > 0) launch_contacts(h->d, h->cdev, s);
   if (h->frames)
-    launch_rec_frames(h->d, h->frame_trial, h->tinfo[h->frame_trial].n_cv, h->frame_cap, h->frames, s);
+    launch_rec_frames(h->d, h->frame_trial, frame_stride(h), h->frame_cap, h->frames, s);
 }
 
 // forces of the current positions, after an optional list rebuild.  Unless
@@ -994,6 +1003,23 @@ VP_API int sim_set_step_count(sim_handle *h, int64_t step) {
   return SIM_OK;
 }
 
+VP_API int sim_set_noise_offset(sim_handle *h, int32_t trial, int64_t offset) {
+  int r = enter(h);
+  if (r) return r;
+  if (trial < 0 || trial >= h->n_trials) return fail(h, SIM_EINVAL, "trial out of range");
+  h->tinfo[trial].noise_off = offset;
+  CK(cudaMemcpyAsync(h->d.tinfo + trial, &h->tinfo[trial], sizeof(TrialInfo), cudaMemcpyHostToDevice, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return SIM_OK;
+}
+
+VP_API int sim_trial_seed(sim_handle *h, int32_t trial, uint64_t *seed) {
+  if (!h) return SIM_EINVAL;
+  if (trial < 0 || trial >= h->n_trials || !seed) return fail(h, SIM_EINVAL, "trial out of range or seed is NULL");
+  *seed = (uint64_t)h->tinfo[trial].key0 | ((uint64_t)h->tinfo[trial].key1 << 32);
+  return SIM_OK;
+}
+
 VP_API int32_t sim_num_trials(const sim_handle *h) { return h ? h->n_trials : 0; }
 
 VP_API int32_t sim_num_atoms(const sim_handle *h, int32_t trial) {
@@ -1036,7 +1062,7 @@ VP_API int sim_get_record(sim_handle *h, int32_t trial, double *out) {
 VP_API int sim_record_frames(sim_handle *h, int32_t trial, int32_t capacity) {
   int r = enter(h);
   if (r) return r;
-  if (capacity < 0 || (capacity > 0 && (trial < 0 || trial >= h->n_trials)))
+  if (capacity < 0 || (capacity > 0 && (trial < -1 || trial >= h->n_trials)))
     return fail(h, SIM_EINVAL, "bad frame-record arguments");
   if (h->frames) {
     cudaFree(h->frames);
@@ -1049,7 +1075,8 @@ VP_API int sim_record_frames(sim_handle *h, int32_t trial, int32_t capacity) {
   h->frame_cap = capacity;
   h->frame_trial = capacity > 0 ? trial : -1;
   if (capacity > 0) {
-    size_t n = (size_t)capacity * 3 * (size_t)std::max(1, h->tinfo[trial].n_cv);
+    const size_t nt = trial >= 0 ? 1 : (size_t)h->n_trials;
+    size_t n = nt * (size_t)capacity * 3 * (size_t)std::max(1, frame_stride(h));
     CK(cudaMalloc(&h->frames, n * sizeof(float)));
     CK(cudaMemset(h->frames, 0, n * sizeof(float)));
   }
@@ -1060,7 +1087,8 @@ VP_API int sim_get_frames(sim_handle *h, double *out) {
   int r = enter(h);
   if (r) return r;
   if (!h->frames || !out) return fail(h, SIM_EINVAL, "no frame record");
-  size_t n = (size_t)h->frame_cap * 3 * (size_t)h->tinfo[h->frame_trial].n_cv;
+  const size_t nt = h->frame_trial >= 0 ? 1 : (size_t)h->n_trials;
+  size_t n = nt * (size_t)h->frame_cap * 3 * (size_t)frame_stride(h);
   std::vector<float> tmp(n);
   CK(cudaMemcpyAsync(tmp.data(), h->frames, n * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));

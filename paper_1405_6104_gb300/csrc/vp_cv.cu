@@ -259,18 +259,25 @@ __global__ void __launch_bounds__(CVFIN_THREADS) k_cvfin(Dev d, SimConst c) {
 
 // CV-atom positions of one trial after every force evaluation (the step
 // counter has already advanced for a step; frame index = step % capacity)
-__global__ void k_rec_frames(Dev d, int trial, int cap, float *frames) {
-  const TrialInfo &T = d.tinfo[trial];
+// frame of step n: one trial ([cap][n_cv][3]) or, with trial < 0, every
+// trial ([n_trials][cap][stride][3], stride = the largest n_cv; blockIdx.y
+// is the trial)
+__global__ void k_rec_frames(Dev d, int trial, int cap, int stride, float *frames) {
+  const int t = trial >= 0 ? trial : (int)blockIdx.y;
+  const TrialInfo &T = d.tinfo[t];
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= T.n_cv) return;
   const long long n = *d.step;
   const float4 p = d.pos[d.slot_of[T.atom0 + i]];
-  float *f = frames + ((size_t)(n % cap) * T.n_cv + i) * 3;
+  const size_t base = trial >= 0 ? 0 : (size_t)t * (size_t)cap * (size_t)stride;
+  float *f = frames + (base + (size_t)(n % cap) * stride + i) * 3;
   f[0] = p.x; f[1] = p.y; f[2] = p.z;
 }
 
 void launch_rec_frames(const Dev &d, int trial, int n_cv, int cap, float *frames, cudaStream_t s) {
-  if (n_cv > 0 && cap > 0) k_rec_frames<<<(n_cv + 127) / 128, 128, 0, s>>>(d, trial, cap, frames);
+  if (n_cv <= 0 || cap <= 0) return;
+  dim3 grid((unsigned)((n_cv + 127) / 128), trial >= 0 ? 1u : (unsigned)d.n_trials);
+  k_rec_frames<<<grid, 128, 0, s>>>(d, trial, cap, n_cv, frames);
 }
 
 void launch_cnat(const Dev &d, const SimConst &c, const double *native, const int32_t *sys_nat0, int32_t n_tiles,

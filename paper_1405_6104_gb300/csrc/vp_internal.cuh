@@ -69,6 +69,7 @@ struct TrialInfo {
   int32_t systile0;    // first CV tile of the system
   float box, inv_box, col_w, inv_col_w;
   uint32_t key0, key1; // Philox key (trial seed)
+  long long noise_off; // the noise of step n uses the counter n + noise_off (0 unless set)
 };
 
 struct TrialState {

@@ -29,6 +29,7 @@ __global__ void __launch_bounds__(256) k_update(Dev d, SimConst c) {
   if (o < 0) return;
   const int n_cv = __ldg(&d.tinfo[t].n_cv), cv0 = __ldg(&d.tinfo[t].cv0);
   const uint32_t key0 = __ldg(&d.tinfo[t].key0), key1 = __ldg(&d.tinfo[t].key1);
+  const unsigned long long nstep = step + (unsigned long long)__ldg(&d.tinfo[t].noise_off);
   float Fx = fx_to(fxi), Fy = fx_to(fyi), Fz = fx_to(fzi);
   if (o < n_cv) {
     // ratchet force F_i = -(k_R/2) a grad_i z (Eq. VR); a = 0 when z <= z_m
@@ -55,7 +56,7 @@ __global__ void __launch_bounds__(256) k_update(Dev d, SimConst c) {
       c2sd = as.c2sd;
     }
     p.x += c.half_dt * v.x; p.y += c.half_dt * v.y; p.z += c.half_dt * v.z;
-    const float3 xi = normal3(key0, key1, (uint32_t)o, step, 0u);
+    const float3 xi = normal3(key0, key1, (uint32_t)o, nstep, 0u);
     v.x = c1 * v.x + c2sd * xi.x;
     v.y = c1 * v.y + c2sd * xi.y;
     v.z = c1 * v.z + c2sd * xi.z;

@@ -101,6 +101,24 @@ def test_checkpointed_trajectory_adjoint():
     assert np.isfinite(end_state[0]).all()
 
 
+def test_batched_and_sequential_replays_agree():
+    """Segments replayed side by side (groups of 4 of 10 segments, the last
+    group padded) and one after another give bit-identical frames and
+    gradients; both leave the batch in its forward end state."""
+    s, p = S.small_solvated()
+    out = {}
+    for mode in ("batched", "sequential"):
+        with B.TrialBatch(s, p, [3], trial_seeds=[41, 42, 43]) as b:
+            phi, G, info = trajectory_adjoint(b, 2, 100, every=10, keep_frames=True, replay=mode, group=4)
+            out[mode] = (phi, G, info, b.get_state(2), B.sim_step_count(b.h))
+    pb, Gb, ib, eb, nb = out["batched"]
+    ps, Gs, is_, es, ns = out["sequential"]
+    assert np.array_equal(ib["forward_frames"], ib["replayed_frames"])
+    assert np.array_equal(ib["replayed_frames"], is_["replayed_frames"])
+    assert np.array_equal(Gb, Gs) and pb == ps
+    assert np.array_equal(eb[0], es[0]) and np.array_equal(eb[1], es[1]) and nb == ns
+
+
 @pytest.mark.slow
 def test_adjoint_30k_system_500_frames():
     """30 000 atoms (1800-atom solute), 500 frames, checkpoints every 50
