@@ -11,8 +11,10 @@
 
 namespace vp {
 
+// eight blocks per SM (32 registers): the kernel waits on memory round trips
+// and needs every resident warp it can get
 template <int MODE>
-__global__ void __launch_bounds__(256) k_update(Dev d, SimConst c) {
+__global__ void __launch_bounds__(256, 8) k_update(Dev d, SimConst c) {
   const int slot = blockIdx.x * blockDim.x + threadIdx.x;
   if (slot >= d.total_slots) return;
   if (MODE == UPD_FINAL && slot == 0) *d.kick = 0.5f;
