@@ -542,7 +542,7 @@ VP_API int sim_create(const sim_system *systems, int32_t n_systems, const int32_
       ok &= add_ex(i, j) && add_ex(j, i);
     }
     if (!ok) return bail(fail(h, SIM_EINVAL, "more than 16 excluded partners for an atom"));
-    // bonded terms, owner computes
+    // bonded terms per owning atom (the energy kernel computes each atom's share)
     std::vector<std::vector<BTerm>> per(S.n_atoms);
     for (int b = 0; b < S.n_bonds; ++b) {
       int i = S.bonds[2 * b], j = S.bonds[2 * b + 1];
