@@ -99,7 +99,7 @@ typedef struct sim_params {
   double cv_r0;            /* r0 of the contact function, nm */
   double cv_r_switch;      /* switching of C~ starts, nm */
   double cv_r_cut;         /* C~ = 0 beyond, nm */
-  int32_t cv_min_sep;      /* contact pairs have j - i > cv_min_sep */
+  int32_t cv_min_sep;      /* contact pairs have j - i > cv_min_sep, >= 0 */
   uint64_t seed;           /* trial t uses seed + t unless trial_seeds is given */
   int32_t flags;           /* SIM_* flags */
 } sim_params;
@@ -159,6 +159,10 @@ int sim_set_step_count(sim_handle *h, int64_t step);
  * segment draws the noise of the original run.  SIM_EINVAL for a bad trial. */
 int sim_set_noise_offset(sim_handle *h, int32_t trial, int64_t offset);
 
+/* The noise counter offset of a trial (see sim_set_noise_offset) into
+ * *offset.  SIM_EINVAL for a bad trial or NULL offset. */
+int sim_noise_offset(sim_handle *h, int32_t trial, int64_t *offset);
+
 /* The Philox key (seed) of a trial: trial_seeds[trial] at creation, or
  * params->seed + trial.  SIM_EINVAL for a bad trial or NULL seed. */
 int sim_trial_seed(sim_handle *h, int32_t trial, uint64_t *seed);
@@ -176,11 +180,16 @@ int sim_get_record(sim_handle *h, int32_t trial, double *out /* [5*capacity] */)
 /* Per-step record of the reaction-coordinate atom positions of one trial
  * (the frames X_n of the path): capacity frames, the frame of step n at index
  * n % capacity, written after every force evaluation (also at sim_set_state).
- * sim_get_frames copies [capacity][n_cv][3] (nm) to out.  trial = -1 records
- * every trial: out is then [n_trials][capacity][m][3], m the largest n_cv of
- * the batch (a trial with fewer CV atoms leaves the rest of its rows 0). */
+ * trial = -1 records every trial.  sim_frame_shape writes shape[3] =
+ * {trials recorded (1, or n_trials for -1), capacity, m}, all 0 without a
+ * record, m = n_cv of the recorded trial or the largest n_cv of the batch.
+ * sim_get_frames copies the record, [shape[0]][capacity][m][3] doubles (nm;
+ * a trial with fewer CV atoms leaves the rest of its rows 0), to out, which
+ * holds out_len doubles: SIM_EINVAL without a record or when out_len is
+ * smaller than the record (nothing is written then). */
 int sim_record_frames(sim_handle *h, int32_t trial, int32_t capacity);
-int sim_get_frames(sim_handle *h, double *out);
+int sim_frame_shape(sim_handle *h, int32_t *shape);
+int sim_get_frames(sim_handle *h, double *out, int64_t out_len);
 
 /* Gradient of the bias functional (Eq. VMDcondition, discretised as in
  * bias_functional) with respect to the reaction-coordinate atoms of every
@@ -240,6 +249,9 @@ int sim_diagnostics(sim_handle *h, int64_t *out);
  * consulted first and appended to.  choice[2] (may be NULL) receives the
  * picked variants. */
 int sim_autotune(sim_handle *h, int32_t reps, const char *cache_path, int32_t *choice);
+/* Sets the launch shapes directly (the numbering of sim_autotune), e.g. to
+ * test one of them.  SIM_EINVAL for a variant out of range. */
+int sim_set_variants(sim_handle *h, int32_t pair_variant, int32_t cv_variant);
 
 /* Kernel timing.  on = 1: the next sim_step_batch calls launch kernels
  * directly and time each launch with CUDA events on the library stream.
@@ -280,7 +292,10 @@ int sim_philox_normals(uint64_t seed, int64_t step, uint32_t stream, int32_t n, 
  * GPU that loads the library until exit): n_cv above 2048 is rejected with
  * SIM_EINVAL.  The first call on a device looks the array up on that device
  * (do it before any stream capture there).  Calls share the array: calls that
- * overlap on the GPU race.  Returns SIM_OK, SIM_EINVAL or SIM_ECUDA. */
+ * overlap on the GPU race.  Returns SIM_OK, SIM_EINVAL (also for
+ * cv_r_switch <= 0, cv_r_cut <= cv_r_switch or cv_min_sep < 0) or SIM_ECUDA
+ * (also, before anything is launched, when an earlier CUDA error is pending
+ * on the calling thread; the message names it). */
 int cv_eval_noalloc(const float *d_pos, const double *d_native, int32_t n_cv, double box, const sim_params *params,
                     double *d_z, double *d_grad, void *cuda_stream, char *errbuf, int32_t errlen);
 

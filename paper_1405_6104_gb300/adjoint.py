@@ -72,8 +72,11 @@ def _replay_group(batch, trial, ckpts, segs, every, n_cv, group):
     B.sim_set_step_count(h, 0)
     # padding trials (a short last group) replay the group's first segment
     src = list(segs) + [segs[0]] * (group - len(segs))
+    # the forward trial's own noise offset carries over (a forward batch may
+    # itself be a replay batch)
+    off0 = B.sim_noise_offset(batch.h, trial)
     for k, sg in enumerate(src):
-        B.sim_set_noise_offset(h, k, ckpts[sg][0])
+        B.sim_set_noise_offset(h, k, off0 + ckpts[sg][0])
     states = [ckpts[sg][1][trial] for sg in src]
     pos = np.concatenate([st[0] for st in states])
     vel = np.concatenate([st[1] for st in states])

@@ -84,7 +84,10 @@ _SIGS = {
     "sim_record": ([C.c_void_p, C.c_int32], C.c_int),
     "sim_get_record": ([C.c_void_p, C.c_int32, C.c_void_p], C.c_int),
     "sim_record_frames": ([C.c_void_p, C.c_int32, C.c_int32], C.c_int),
-    "sim_get_frames": ([C.c_void_p, C.c_void_p], C.c_int),
+    "sim_frame_shape": ([C.c_void_p, C.c_void_p], C.c_int),
+    "sim_get_frames": ([C.c_void_p, C.c_void_p, C.c_int64], C.c_int),
+    "sim_noise_offset": ([C.c_void_p, C.c_int32, C.c_void_p], C.c_int),
+    "sim_set_variants": ([C.c_void_p, C.c_int32, C.c_int32], C.c_int),
     "phi_frames_adjoint": ([C.c_void_p, C.c_int32, C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p,
                             C.c_void_p], C.c_int),
     "phi_adjoint_coefficients": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p], C.c_int),
@@ -254,13 +257,37 @@ def sim_record_frames(h, trial: int, capacity: int):
     _check(h, load().sim_record_frames(h, int(trial), int(capacity)))
 
 
-def sim_get_frames(h, capacity: int, n_cv: int, n_trials: int = 0):
+def sim_frame_shape(h):
+    """(trials recorded, capacity, CV atoms per frame) of the frame record."""
+    sh = np.zeros(3, np.int32)
+    _check(h, load().sim_frame_shape(h, sh.ctypes.data))
+    return int(sh[0]), int(sh[1]), int(sh[2])
+
+
+def sim_get_frames(h, capacity: Optional[int] = None, n_cv: Optional[int] = None, n_trials: int = 0):
     """The frame record: (capacity, n_cv, 3) for one recorded trial, or
     (n_trials, capacity, n_cv, 3) when every trial is recorded (n_cv then the
-    largest of the batch)."""
-    out = np.zeros((n_trials, capacity, n_cv, 3) if n_trials else (capacity, n_cv, 3))
-    _check(h, load().sim_get_frames(h, out.ctypes.data))
+    largest of the batch).  The shape comes from the handle; capacity, n_cv
+    and n_trials, when given, must match it."""
+    nt, cap, m = sim_frame_shape(h)
+    if ((capacity is not None and capacity != cap) or (n_cv is not None and n_cv != m)
+            or (n_trials and n_trials != nt)):
+        raise ValueError(f"the frame record holds {nt} trial(s) x {cap} frames x {m} atoms, "
+                         f"not {n_trials or 1} x {capacity} x {n_cv}")
+    out = np.zeros((nt, cap, m, 3) if (n_trials or nt != 1) else (cap, m, 3))
+    _check(h, load().sim_get_frames(h, out.ctypes.data, out.size))
     return out
+
+
+def sim_noise_offset(h, trial: int) -> int:
+    v = C.c_int64(0)
+    _check(h, load().sim_noise_offset(h, int(trial), C.byref(v)))
+    return int(v.value)
+
+
+def sim_set_variants(h, pair_variant: int, cv_variant: int = 0):
+    """Fixes the launch shapes (the autotuner's numbering)."""
+    _check(h, load().sim_set_variants(h, int(pair_variant), int(cv_variant)))
 
 
 def sim_set_noise_offset(h, trial: int, offset: int):

@@ -372,7 +372,7 @@ VP_API int sim_create(const sim_system *systems, int32_t n_systems, const int32_
   const sim_params &p = *params;
   h->params = p;
   if (!(p.dt > 0) || !(p.temperature >= 0) || !(p.r_cut > 0) || !(p.skin >= 0) || p.nstlist < 1 ||
-      !(p.cv_r0 > 0) || !(p.cv_r_cut > p.cv_r_switch) || !(p.cv_r_switch > 0))
+      !(p.cv_r0 > 0) || !(p.cv_r_cut > p.cv_r_switch) || !(p.cv_r_switch > 0) || p.cv_min_sep < 0)
     return bail(fail(h, SIM_EINVAL, "invalid sim_params"));
   int total_trials = 0;
   for (int s = 0; s < n_systems; ++s) {
@@ -1013,6 +1013,13 @@ VP_API int sim_set_noise_offset(sim_handle *h, int32_t trial, int64_t offset) {
   return SIM_OK;
 }
 
+VP_API int sim_noise_offset(sim_handle *h, int32_t trial, int64_t *offset) {
+  if (!h) return SIM_EINVAL;
+  if (trial < 0 || trial >= h->n_trials || !offset) return fail(h, SIM_EINVAL, "trial out of range or offset is NULL");
+  *offset = h->tinfo[trial].noise_off;
+  return SIM_OK;
+}
+
 VP_API int sim_trial_seed(sim_handle *h, int32_t trial, uint64_t *seed) {
   if (!h) return SIM_EINVAL;
   if (trial < 0 || trial >= h->n_trials || !seed) return fail(h, SIM_EINVAL, "trial out of range or seed is NULL");
@@ -1083,12 +1090,24 @@ VP_API int sim_record_frames(sim_handle *h, int32_t trial, int32_t capacity) {
   return SIM_OK;
 }
 
-VP_API int sim_get_frames(sim_handle *h, double *out) {
+VP_API int sim_frame_shape(sim_handle *h, int32_t *shape) {
+  if (!h) return SIM_EINVAL;
+  if (!shape) return fail(h, SIM_EINVAL, "shape is NULL");
+  shape[0] = h->frames ? (h->frame_trial >= 0 ? 1 : h->n_trials) : 0;
+  shape[1] = h->frames ? h->frame_cap : 0;
+  shape[2] = h->frames ? frame_stride(h) : 0;
+  return SIM_OK;
+}
+
+VP_API int sim_get_frames(sim_handle *h, double *out, int64_t out_len) {
   int r = enter(h);
   if (r) return r;
   if (!h->frames || !out) return fail(h, SIM_EINVAL, "no frame record");
   const size_t nt = h->frame_trial >= 0 ? 1 : (size_t)h->n_trials;
   size_t n = nt * (size_t)h->frame_cap * 3 * (size_t)frame_stride(h);
+  if (out_len < 0 || (size_t)out_len < n)
+    return fail(h, SIM_EINVAL, "output holds " + std::to_string(out_len) + " doubles, the frame record needs " +
+                                   std::to_string(n));
   std::vector<float> tmp(n);
   CK(cudaMemcpyAsync(tmp.data(), h->frames, n * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
@@ -1270,6 +1289,19 @@ VP_API int sim_autotune(sim_handle *h, int32_t reps, const char *cache_path, int
     h->chunk = nullptr;
   }
   if (choice) { choice[0] = pv; choice[1] = cv; }
+  return SIM_OK;
+}
+
+VP_API int sim_set_variants(sim_handle *h, int32_t pair_variant, int32_t cv_variant) {
+  if (!h) return SIM_EINVAL;
+  if (pair_variant < 0 || pair_variant >= PAIR_VARIANTS || cv_variant < 0 || cv_variant >= CV_VARIANTS)
+    return fail(h, SIM_EINVAL, "variant out of range");
+  h->pair_variant = pair_variant;
+  h->cv_variant = cv_variant;
+  if (h->chunk) {
+    cudaGraphExecDestroy(h->chunk);
+    h->chunk = nullptr;
+  }
   return SIM_OK;
 }
 

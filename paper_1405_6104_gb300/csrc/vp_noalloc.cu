@@ -21,6 +21,7 @@
 // that overlap on the GPU (on different streams) race.
 #include <cstring>
 #include <mutex>
+#include <string>
 
 #include "../../include/vpath.h"
 #include "vp_internal.cuh"
@@ -234,9 +235,20 @@ VP_API int cv_eval_noalloc(const float *d_pos, const double *d_native, int32_t n
     set_msg(errbuf, errlen, "cv_eval_noalloc: n_cv exceeds the fixed scratch limit of 2048 atoms");
     return SIM_EINVAL;
   }
-  if (!(box > 0.0) || !(params->cv_r0 > 0.0) || !(params->cv_r_cut > params->cv_r_switch)) {
+  if (!(box > 0.0) || !(params->cv_r0 > 0.0) || !(params->cv_r_cut > params->cv_r_switch) ||
+      !(params->cv_r_switch > 0.0) || params->cv_min_sep < 0) {
     set_msg(errbuf, errlen, "cv_eval_noalloc: invalid box or contact parameters");
     return SIM_EINVAL;
+  }
+  // an error left on this thread by earlier work is reported as such, before
+  // anything is launched, so that the check after the launches sees only ours
+  {
+    const cudaError_t pending = cudaGetLastError();
+    if (pending != cudaSuccess) {
+      set_msg(errbuf, errlen, (std::string("cv_eval_noalloc: an earlier CUDA error is pending: ") +
+                               cudaGetErrorString(pending)).c_str());
+      return SIM_ECUDA;
+    }
   }
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEVICES) {

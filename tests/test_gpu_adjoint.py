@@ -122,8 +122,10 @@ def test_batched_and_sequential_replays_agree():
 @pytest.mark.slow
 def test_adjoint_30k_system_500_frames():
     """30 000 atoms (1800-atom solute), 500 frames, checkpoints every 50
-    steps: replayed frames bit-identical; gradient on a 21-frame prefix
-    against the FP64 oracle; central differences of the GPU functional."""
+    steps: replayed frames bit-identical; the whole gradient (all 501
+    frames, segment by segment from the recorded coefficients) against the
+    FP64 oracle's gradient of Phi along the same frames, a 21-frame prefix
+    on its own as well; central differences of the GPU functional."""
     s, p = S.adjoint_30k(3)
     p.k_ratchet = 5.0
     with B.TrialBatch(s, p, [1], trial_seeds=[3]) as b:
@@ -131,6 +133,9 @@ def test_adjoint_30k_system_500_frames():
         fwd, rep = info["forward_frames"], info["replayed_frames"]
         assert np.array_equal(fwd, rep)
         assert phi == pytest.approx(info["phi_handle"], rel=1e-10, abs=1e-300)
+        Phi_all, G_all = O.phi_frames_grad(s, p, fwd)
+        assert phi == pytest.approx(Phi_all, rel=1e-6)
+        assert rel(G, G_all) < 1e-4
         pre = fwd[:21]
         phi_p, _, Gp = B.phi_frames_adjoint(b.h, 0, pre)
         Phi_ref, G_ref = O.phi_frames_grad(s, p, pre)

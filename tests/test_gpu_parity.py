@@ -266,12 +266,27 @@ def test_recorded_functional_bookkeeping_and_restart():
         assert cv2[0] == pytest.approx(cv[0], rel=1e-12)
 
 
+def _pick_variant(b, variant):
+    """Fixes the pair-kernel launch shape: a variant number, or "tuned" for
+    whatever the autotuner picks on this batch (as the benchmark does)."""
+    if variant == "tuned":
+        return B.sim_autotune(b.h, 3, None)[0]
+    B.sim_set_variants(b.h, variant, 0)
+    return variant
+
+
+# 0: the general kernel; 8: the persistent packed kernel (FP32x2 arithmetic,
+# i-clusters handed out by a counter over a resident grid), the one the
+# benchmark's autotuner picks for the 64-trial batch
 @pytest.mark.slow
-def test_full_size_batch_sampled():
+@pytest.mark.parametrize("variant", [0, 8, "tuned"])
+def test_full_size_batch_sampled(variant):
     """64 trials of the 11 040-atom system in one batch (the benchmarked
-    configuration): sampled trials checked element by element."""
+    configuration and launch shape): sampled trials checked element by
+    element after a chunk of graph-replayed steps."""
     s, p, seeds = S.batched_64(1)
     with B.TrialBatch(s, p, [64], trial_seeds=seeds) as b:
+        _pick_variant(b, variant)
         b.step(10)  # ends on a list rebuild
         diag = B.sim_diagnostics(b.h)
         assert diag["max_list_entries"] < diag["list_capacity"]
@@ -412,3 +427,51 @@ def test_blow_up_is_reported_as_non_finite():
             for _ in range(50):
                 b.step(10)
         assert e.value.code == B.SIM_ENONFINITE
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("variant", [8, "tuned"])
+def test_benchmarked_system_functional_parity(variant):
+    """The 11 040-atom system (540-atom reaction coordinate, 127 260 contact
+    pairs, k_R of the paper): 100 graph-replayed steps with the per-step
+    record and the frame recorder on; the GPU's frames are fed to the oracle,
+    which must reproduce z at every step and the accumulated Phi to 1e-6
+    relative (Eq. VMDcondition; a = z - z_m is a small difference of large
+    sums here)."""
+    s, p = S.plain_single(1)
+    n = 100
+    with B.TrialBatch(s, p, [1], trial_seeds=[1000]) as b:
+        _pick_variant(b, variant)
+        x0, _, cv0 = b.get_state(0)
+        B.sim_record(b.h, n + 1)
+        B.sim_record_frames(b.h, 0, n + 1)
+        b.step(n)
+        _, _, cv = b.get_state(0)
+        rec = B.sim_get_record(b.h, 0, n + 1)
+        fr = B.sim_get_frames(b.h, n + 1, s.n_cv)
+    fr[0] = x0[: s.n_cv]
+    Phi, z, a, phi = O.phi_frames(s, p, fr)
+    assert Phi > 0 and np.count_nonzero(a[1:]) > 10
+    assert cv[3] - cv0[3] == pytest.approx(Phi, rel=1e-6)
+    assert np.allclose(rec[1:, 0], z[1:], rtol=1e-10, atol=0.0)
+    assert np.allclose(rec[1:, 2], a[1:], rtol=1e-6, atol=1e-9 * max(1.0, z.max()))
+    assert np.allclose(rec[1:, 3], phi[1:], rtol=1e-5, atol=1e-12 * max(1.0, phi.max()))
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("variant", [8])
+def test_benchmarked_system_trajectory_100_steps(variant):
+    """The 11 040-atom system, 100 steps in ten graph replays on the
+    benchmarked pair kernel, against the FP64 oracle's own 100-step run with
+    the shared Philox noise: positions to 1e-4 nm."""
+    s, p = S.plain_single(1)
+    seed = 1000
+    with B.TrialBatch(s, p, [1], trial_seeds=[seed]) as b:
+        _pick_variant(b, variant)
+        b.step(100)
+        pos, vel, cv = b.get_state(0)
+    r = O.run(s, p, seed, 100)
+    assert r["status"] == 0
+    d = min_image(pos - r["pos"], s.box)
+    assert np.abs(d).max() < 1e-4
+    assert np.abs(vel - r["vel"]).max() < 1e-2 * np.abs(r["vel"]).max()
