@@ -248,6 +248,7 @@ def run_gpu(args):
         batch.step(nst)
     barrier()
     B.sim_kernel_times(batch.h)  # drop the warm-up's launches
+    diag0 = B.sim_diagnostics(batch.h)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     t_begin = time.time()
     torch.cuda.nvtx.range_push("timed")  # lets a profiler select the timed launches
@@ -259,6 +260,7 @@ def run_gpu(args):
     torch.cuda.nvtx.range_pop()
     t_end = time.time()
     ms = ev0.elapsed_time(ev1)
+    diag1 = B.sim_diagnostics(batch.h)
     in_graph = B.sim_kernel_times(batch.h).get("pair_in_graph", (float("nan"), 0))
     B.sim_set_timing(batch.h, 0)
     if world > 1:
@@ -303,6 +305,16 @@ def run_gpu(args):
     diag = B.sim_diagnostics(batch.h)
     # 8 x 4 atom pairs per list entry, masked pairs included
     diag["pairs_evaluated_per_atom_step"] = round(32.0 * diag["list_entries"] / atoms, 1)
+    # list rebuilds of the timed region: a trial's list is rebuilt when one of
+    # its atoms has moved skin/2 - 1e-5 nm since the list was built, or after
+    # nstlist steps, so no pair within r_cut is ever missing from it
+    trial_steps = n_trials * nst * args.steps
+    rb = diag1["trial_rebuilds"] - diag0["trial_rebuilds"]
+    diag["timed_region"] = {
+        "skin_violations": diag1["skin_violations"] - diag0["skin_violations"],
+        "trial_rebuilds": rb, "trial_steps": trial_steps,
+        "mean_steps_between_rebuilds": round(trial_steps / max(rb, 1), 2),
+        "displacement_triggered": diag1["displacement_rebuilds"] - diag0["displacement_rebuilds"]}
     # the method's selection over every rank's trials: one double per trial
     # gathered on the host (outside the timed region)
     from paper_1405_6104_gb300.shard import global_selection

@@ -47,13 +47,20 @@ extern "C" {
                                    (512 entries per cluster; the environment variable
                                    VPATH_LIST_CAP, read at sim_create, lowers it to 8..511 for
                                    fault-injection tests) */
-#define SIM_ESKIN (-4)           /* an atom moved more than skin/2 between list rebuilds (SIM_STRICT_SKIN) */
-#define SIM_ENONFINITE (-5)      /* a position, velocity or z became non-finite */
+#define SIM_ESKIN (-4)           /* an atom moved more than skin/2 between fixed-interval list rebuilds
+                                   (SIM_FIXED_INTERVAL | SIM_STRICT_SKIN) */
+#define SIM_ENONFINITE (-5)      /* a position, velocity or z became non-finite, a force exceeded
+                                   2^30 kJ/mol/nm or an atom moved more than a box length in one
+                                   step (the run has blown up) */
 #define SIM_ETIMEOUT (-6)        /* a bounded device wait gave up */
 
 /* sim_params.flags */
-#define SIM_STRICT_SKIN 1        /* treat skin violations as errors instead of counting them */
+#define SIM_STRICT_SKIN 1        /* with SIM_FIXED_INTERVAL: treat skin violations as errors instead of
+                                   counting them (SIM_EINVAL without SIM_FIXED_INTERVAL) */
 #define SIM_NO_GRAPH 2           /* launch every kernel directly instead of replaying CUDA graphs */
+#define SIM_FIXED_INTERVAL 4     /* rebuild lists only at steps that are multiples of nstlist (no
+                                   displacement trigger: pairs may be missed when an atom moves more
+                                   than skin/2 within an interval; such moves are counted) */
 
 typedef struct sim_handle sim_handle;
 
@@ -93,7 +100,12 @@ typedef struct sim_params {
   double gamma;            /* 1/ps, default friction */
   double r_cut;            /* LJ and reaction-field cut-off, nm */
   double skin;             /* Verlet buffer, nm: lists hold pairs within r_cut + skin */
-  int32_t nstlist;         /* steps between list rebuilds, >= 1 */
+  int32_t nstlist;         /* longest interval between two list rebuilds of a trial, >= 1 (with
+                              SIM_FIXED_INTERVAL: the interval).  A trial's list is also rebuilt,
+                              before the forces, in the first step in which one of its atoms is
+                              farther than skin/2 - 1e-5 nm from where the list was built, so that
+                              no pair closer than r_cut is ever missing from it (the cut-off model
+                              of U in Eq. Lang); nstlist steps are also one CUDA-graph chunk */
   double eps_rf;           /* reaction-field dielectric; <= 0 means infinity */
   double k_ratchet;        /* k_R of Eq. VR, kJ/mol */
   double cv_r0;            /* r0 of the contact function, nm */
@@ -142,13 +154,19 @@ int sim_get_state(sim_handle *h, int32_t trial, double *pos, double *vel, double
  * arrays concatenated in trial order).  pos and vel must both be given.
  * cv_state = {z_m, Phi} per affected trial, or NULL to restart the functional
  * (z_m = z(X), Phi = 0).  Lists are rebuilt and forces recomputed for the
- * whole batch; the step counter is unchanged. */
+ * affected trials (forces of the whole batch); the step counter is unchanged. */
 int sim_set_state(sim_handle *h, int32_t trial, const double *pos, const double *vel, const double *cv_state);
+
+/* Rebuilds the lists of every trial at the current positions and recomputes
+ * the forces, leaving the state (positions, velocities, z_m, Phi, step
+ * counter, records) as it is.  A run that calls this at a checkpoint and a run
+ * restored there with sim_set_state continue bit-identically. */
+int sim_rebuild(sim_handle *h);
 
 /* Steps taken since creation (the Philox counter of the next step is this + 1). */
 int64_t sim_step_count(const sim_handle *h);
-/* Sets the step counter (resume from a checkpoint); list rebuilds happen at
- * multiples of nstlist of this counter. */
+/* Sets the step counter (resume from a checkpoint; with SIM_FIXED_INTERVAL
+ * lists are rebuilt at multiples of nstlist of this counter). */
 int sim_set_step_count(sim_handle *h, int64_t step);
 
 /* Noise counter offset of one trial: its Langevin noise of step n is drawn
@@ -230,11 +248,17 @@ int phi_frames_refine(sim_handle *h, int32_t trial, double *frames, int32_t n_fr
  * sim_pairlist: the atom pairs (i < j, caller's indices) that the current
  *   cluster lists hold for one trial (list rule at the last rebuild);
  *   *n_pairs receives the count, pairs beyond cap are dropped.
- * sim_diagnostics: out[5] = {skin violations counted, max list entries of a
- *   cluster, list capacity per cluster, clusters in use (all trials), list
- *   entries in use (all trials; each holds 8 x 4 atom pairs, so 32 times this
- *   over the atoms is the pair evaluations per atom-step)}. */
+ * sim_list_positions: pos[3*n_atoms] (caller order) receives the positions
+ *   the trial's current list was built from (wrapped into the box).
+ * sim_diagnostics: out[7] = {skin violations counted (SIM_FIXED_INTERVAL:
+ *   atoms farther than skin/2 from where their list was built when it was
+ *   rebuilt; 0 otherwise, where a list is rebuilt before that can happen), max
+ *   list entries of a cluster, list capacity per cluster, clusters in use (all
+ *   trials), list entries in use (all trials; each holds 8 x 4 atom pairs, so
+ *   32 times this over the atoms is the pair evaluations per atom-step), list
+ *   rebuilds of trials since creation, of them triggered by a displacement}. */
 int sim_pairlist(sim_handle *h, int32_t trial, int32_t *pairs, int64_t cap, int64_t *n_pairs);
+int sim_list_positions(sim_handle *h, int32_t trial, double *pos);
 int sim_diagnostics(sim_handle *h, int64_t *out);
 
 /* Autotuner: times the launch-shape variants of the pair kernel (0-2: the

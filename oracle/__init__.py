@@ -53,7 +53,7 @@ class OrParams(C.Structure):
         ("dt", C.c_double), ("temperature", C.c_double), ("gamma", C.c_double), ("r_cut", C.c_double),
         ("skin", C.c_double), ("nstlist", C.c_int32),
         ("eps_rf", C.c_double), ("k_ratchet", C.c_double), ("cv_r0", C.c_double), ("cv_r_switch", C.c_double),
-        ("cv_r_cut", C.c_double), ("cv_min_sep", C.c_int32),
+        ("cv_r_cut", C.c_double), ("cv_min_sep", C.c_int32), ("list_fixed", C.c_int32),
     ]
 
 
@@ -145,7 +145,8 @@ class _Sys:
 def _params(p):
     return OrParams(dt=p.dt, temperature=p.temperature, gamma=p.gamma, r_cut=p.r_cut, skin=p.skin,
                     nstlist=p.nstlist, eps_rf=p.eps_rf, k_ratchet=p.k_ratchet, cv_r0=p.cv_r0,
-                    cv_r_switch=p.cv_r_switch, cv_r_cut=p.cv_r_cut, cv_min_sep=p.cv_min_sep)
+                    cv_r_switch=p.cv_r_switch, cv_r_cut=p.cv_r_cut, cv_min_sep=p.cv_min_sep,
+                    list_fixed=int((getattr(p, "flags", 0) & 4) != 0))  # bit 4 of the flags: fixed-interval lists
 
 
 # ---------------------------------------------------------------------------

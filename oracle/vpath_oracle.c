@@ -72,6 +72,7 @@ typedef struct {
   int32_t nstlist;
   double eps_rf, k_ratchet, cv_r0, cv_r_switch, cv_r_cut;
   int32_t cv_min_sep;
+  int32_t list_fixed; /* 1: lists rebuilt only at multiples of nstlist */
 } or_params;
 
 /* ------------------------------------------------------------------------ */
@@ -522,8 +523,12 @@ static void wrap(double *pos, int n, double L) {
 
 /* Integrates n_steps BAOAB steps of Eq. Lang with the rMD bias:
  *   v += dt/2 F/m; x += dt/2 v; v = c1 v + c2 sqrt(kT/m) xi_n; x += dt/2 v;
- *   [every nstlist steps: wrap, rebuild list]; F = -grad U + F^bias;
+ *   [list due: wrap, rebuild list]; F = -grad U + F^bias;
  *   v += dt/2 F/m; Phi += dt * phi_n,
+ * where U is the cut-off potential: the list (pairs within r_cut + skin) is
+ * due when an atom is farther than skin/2 - 1e-5 nm from where it was at the
+ * last rebuild (then no pair within r_cut can be missing from it) or nstlist
+ * steps after it (list_fixed: at multiples of nstlist only),
  * with c1 = exp(-gamma dt), c2 = sqrt(1 - c1^2), xi_n the Philox normals of
  * (seed, atom, n, stream 0).  vel_in NULL -> Maxwell-Boltzmann start.
  * Returns 0 on success, -1 on bad input, -2 on a non-finite state. */
@@ -549,6 +554,10 @@ int or_run(const or_system *s, const or_params *p, uint64_t seed, const double *
   }
   wrap(x, n, L);
   vlist_t vl = vlist_build(s, x, p->r_cut + p->skin, &e);
+  double *xref = (double *)malloc(sizeof(double) * 3 * (size_t)n);
+  memcpy(xref, x, sizeof(double) * 3 * (size_t)n);
+  int last_rebuild = 0;
+  const double trig = 0.5 * p->skin - 1e-5 > 0.0 ? 0.5 * p->skin - 1e-5 : 0.0;
   double en[4];
   phys_forces(s, p, x, &vl, &e, F, en);
   double z = or_cv(x, s->native, s->n_cv, L, p->cv_r0, p->cv_r_switch, p->cv_r_cut, p->cv_min_sep, g);
@@ -576,10 +585,22 @@ int or_run(const or_system *s, const or_params *p, uint64_t seed, const double *
         v[3 * i + k] = vi;
       }
     }
-    if (p->nstlist > 0 && step % p->nstlist == 0) {
+    int due;
+    if (p->list_fixed) {
+      due = p->nstlist > 0 && step % p->nstlist == 0;
+    } else {
+      due = step - last_rebuild >= p->nstlist;
+      for (int i = 0; i < n && !due; ++i) {
+        double dx = x[3 * i] - xref[3 * i], dy = x[3 * i + 1] - xref[3 * i + 1], dz = x[3 * i + 2] - xref[3 * i + 2];
+        due = dx * dx + dy * dy + dz * dz > trig * trig;
+      }
+    }
+    if (due) {
       wrap(x, n, L);
       vlist_free(&vl);
       vl = vlist_build(s, x, p->r_cut + p->skin, &e);
+      memcpy(xref, x, sizeof(double) * 3 * (size_t)n);
+      last_rebuild = step;
     }
     phys_forces(s, p, x, &vl, &e, F, en);
     z = or_cv(x, s->native, s->n_cv, L, p->cv_r0, p->cv_r_switch, p->cv_r_cut, p->cv_min_sep, g);
@@ -610,7 +631,7 @@ int or_run(const or_system *s, const or_params *p, uint64_t seed, const double *
   if (out->force_out) memcpy(out->force_out, F, sizeof(double) * 3 * (size_t)n);
   vlist_free(&vl);
   excl_free(&e);
-  free(x); free(v); free(F); free(g); free(c1); free(c2);
+  free(x); free(v); free(F); free(g); free(c1); free(c2); free(xref);
   return status;
 }
 

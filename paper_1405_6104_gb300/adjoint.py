@@ -13,8 +13,10 @@ of one trial, computed entirely by the library's kernels:
 2. the coefficients A_n, B_n of dPhi/dX_n = A_n grad z + B_n H_z w follow
    from the record (``phi_adjoint_coefficients``);
 3. replay: each segment is re-run from its checkpoint with the frame
-   recorder on, bit-identical to the forward run (same list schedule, same
-   call boundaries, counter-based noise).  By default the segments are
+   recorder on, bit-identical to the forward run (the forward run rebuilds
+   every list at each checkpoint, as the restore there does; same call
+   boundaries, counter-based noise, list rebuilds decided per trial from its
+   own state).  By default the segments are
    replayed side by side as the trials of a second batch of the trial's
    system ("batched": every trial carries the original seed and its
    segment's start step as noise offset, so it draws the original noise;
@@ -98,20 +100,23 @@ def trajectory_adjoint(batch, trial: int, n_steps: int, every: int = 50, keep_fr
     if replay not in ("batched", "sequential"):
         raise ValueError("replay must be 'batched' or 'sequential'")
     h = batch.h
-    nst = batch.params.nstlist
     step0 = B.sim_step_count(h)
-    if every % nst or n_steps % every or step0 % nst:
-        raise ValueError("every must be a multiple of nstlist, n_steps of every, and the start a list step")
+    if every < 1 or n_steps % every:
+        raise ValueError("n_steps must be a multiple of every >= 1")
     n_cv = batch.systems[_system_of(batch, trial)].n_cv
     nseg = n_steps // every
     cap = n_steps + 1
     B.sim_record(h, cap)
     B.sim_record_frames(h, trial, cap if keep_frames else 0)
+    # every checkpoint holds freshly built lists, like the state a restore
+    # there produces
+    B.sim_rebuild(h)
     z0 = B.sim_get_state(h, trial)[2][0]
     phi_start = B.sim_get_state(h, trial)[2][3]
     ckpts = [_capture(batch)]
     for _ in range(nseg):
         batch.step(every)
+        B.sim_rebuild(h)
         ckpts.append(_capture(batch))
     phi_end = ckpts[-1][1][trial][2][3]
     rec = B.sim_get_record(h, trial, cap)

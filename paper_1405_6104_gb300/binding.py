@@ -28,6 +28,7 @@ SIM_ENONFINITE = -5
 SIM_ETIMEOUT = -6
 SIM_STRICT_SKIN = 1
 SIM_NO_GRAPH = 2
+SIM_FIXED_INTERVAL = 4
 
 _ERRNAMES = {SIM_EINVAL: "SIM_EINVAL", SIM_ECUDA: "SIM_ECUDA", SIM_ELIST_OVERFLOW: "SIM_ELIST_OVERFLOW",
              SIM_ESKIN: "SIM_ESKIN", SIM_ENONFINITE: "SIM_ENONFINITE", SIM_ETIMEOUT: "SIM_ETIMEOUT"}
@@ -93,6 +94,8 @@ _SIGS = {
     "phi_adjoint_coefficients": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p], C.c_int),
     "sim_pairlist": ([C.c_void_p, C.c_int32, C.c_void_p, C.c_int64, C.c_void_p], C.c_int),
     "sim_diagnostics": ([C.c_void_p, C.c_void_p], C.c_int),
+    "sim_list_positions": ([C.c_void_p, C.c_int32, C.c_void_p], C.c_int),
+    "sim_rebuild": ([C.c_void_p], C.c_int),
     "sim_autotune": ([C.c_void_p, C.c_int32, C.c_char_p, C.c_void_p], C.c_int),
     "sim_set_timing": ([C.c_void_p, C.c_int32], C.c_int),
     "sim_kernel_times": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32], C.c_int),
@@ -335,10 +338,24 @@ def sim_pairlist(h, trial: int, cap: int = 0):
 
 
 def sim_diagnostics(h):
-    out = np.zeros(5, np.int64)
+    out = np.zeros(7, np.int64)
     _check(h, load().sim_diagnostics(h, out.ctypes.data))
     return dict(skin_violations=int(out[0]), max_list_entries=int(out[1]), list_capacity=int(out[2]),
-                clusters=int(out[3]), list_entries=int(out[4]))
+                clusters=int(out[3]), list_entries=int(out[4]), trial_rebuilds=int(out[5]),
+                displacement_rebuilds=int(out[6]))
+
+
+def sim_list_positions(h, trial: int):
+    """(n_atoms, 3): the positions the trial's current list was built from."""
+    n = load().sim_num_atoms(h, trial)
+    out = np.zeros((n, 3))
+    _check(h, load().sim_list_positions(h, int(trial), out.ctypes.data))
+    return out
+
+
+def sim_rebuild(h):
+    """Rebuilds every list at the current positions (state unchanged)."""
+    _check(h, load().sim_rebuild(h))
 
 
 def sim_autotune(h, reps: int = 5, cache_path: Optional[str] = None):

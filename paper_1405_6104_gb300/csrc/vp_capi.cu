@@ -190,7 +190,7 @@ int harvest_graph_timers(sim_handle *h) {
 void rebuild_cols(sim_handle *h) {
   cudaStream_t s = h->stream;
   timed(h, "bin", [&] { launch_bin(h->d, h->c, h->half_skin2, h->strict_skin, s); });
-  timed(h, "colscan", [&] { launch_colscan(h->d, s); });
+  timed(h, "colscan", [&] { launch_colscan(h->d, h->c, s); });
   timed(h, "colfill", [&] { launch_colfill(h->d, s); });
   timed(h, "colsort", [&] { launch_colsort(h->d, s); });
 }
@@ -236,44 +236,53 @@ void after_forces(sim_handle *h, FinMode mode) {
     launch_rec_frames(h->d, h->frame_trial, frame_stride(h), h->frame_cap, h->frames, s);
 }
 
-// forces of the current positions, after an optional list rebuild.  Unless
-// kernels are being timed one by one, the bonded forces and the reaction
-// coordinate (CV and its finaliser) run on a second stream once the atoms
-// have their slots (they read positions through slot_of) and join before
-// anything that follows: the list build and the pair kernel write nothing
-// they read, and pair and bonded forces meet only in order-independent
-// fixed-point sums, so both orders give bit-identical states.
-void forces(sim_handle *h, FinMode mode, bool with_rebuild) {
-  if (with_rebuild) rebuild_cols(h);
+constexpr int NO_REQUEST = -2;  // forces(): no forced list rebuild
+
+// forces of the current positions.  The rebuild kernels run every time and
+// rebuild the lists that are due (a displacement beyond the buffer, the
+// longest interval, or a forced request: request = a trial, -1 for all, or
+// NO_REQUEST).  Unless kernels are being timed one by one, the bonded forces
+// and the reaction coordinate (CV and its finaliser) run on a second stream
+// once the atoms have their slots (they read positions through slot_of) and
+// join before anything that follows: the list build and the pair kernel write
+// nothing they read, and pair and bonded forces meet only in
+// order-independent fixed-point sums, so both orders give bit-identical states.
+void forces(sim_handle *h, FinMode mode, int request) {
+  if (request != NO_REQUEST) launch_rebuild_request(h->d, request, h->stream);
+  rebuild_cols(h);
   if (h->side && !h->timing) {
     cudaEventRecord(h->ev_fork, h->stream);
     cudaStreamWaitEvent(h->side, h->ev_fork, 0);
     cv_forces(h, mode, h->side);
     cudaEventRecord(h->ev_join, h->side);
-    if (with_rebuild) rebuild_list(h);
+    rebuild_list(h);
     pair_forces(h);
     cudaStreamWaitEvent(h->stream, h->ev_join, 0);
   } else {
-    if (with_rebuild) rebuild_list(h);
+    rebuild_list(h);
     pair_forces(h);
     cv_forces(h, mode, h->stream);
   }
   after_forces(h, mode);
 }
 
-void one_step(sim_handle *h, bool with_rebuild) {
+void one_step(sim_handle *h) {
   timed(h, "update", [&] { launch_update(h->d, h->c, UPD_DRIFT, h->stream); });
-  forces(h, FIN_STEP, with_rebuild);
+  forces(h, FIN_STEP, NO_REQUEST);
 }
 
 int check_flags(sim_handle *h) {
   int flags = 0;
   CK(cudaMemcpyAsync(&flags, h->d.err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
-  if (flags & ERR_NONFINITE) return fail(h, SIM_ENONFINITE, "non-finite position, velocity or reaction coordinate");
+  if (flags & ERR_NONFINITE)
+    return fail(h, SIM_ENONFINITE,
+                "non-finite position, velocity or reaction coordinate, a force beyond 2^30 kJ/mol/nm or an atom "
+                "faster than a box per step");
   if (flags & (ERR_LIST | ERR_COL | ERR_CAPACITY))
     return fail(h, SIM_ELIST_OVERFLOW, "cluster list, grid column or cluster capacity exceeded");
-  if (flags & ERR_SKIN) return fail(h, SIM_ESKIN, "an atom moved more than skin/2 between list rebuilds");
+  if (flags & ERR_SKIN)
+    return fail(h, SIM_ESKIN, "an atom moved more than skin/2 between fixed-interval list rebuilds");
   return SIM_OK;
 }
 
@@ -304,14 +313,13 @@ int capture_chunk(sim_handle *h) {
     h->gev.resize(2 * (size_t)h->params.nstlist);
     for (auto &e : h->gev) CK(cudaEventCreate(&e));
   }
-  // the chunk is steps n = m nst + 1 .. (m + 1) nst: nst - 1 plain steps and
-  // the step that rebuilds the lists, so that calls of nst steps from a
-  // list step replay it
+  // the chunk is nst steps; every step decides on the device which lists
+  // to rebuild, so a chunk replays from any step
   const int nst = h->params.nstlist;
   CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
   for (int k = 0; k < nst; ++k) {
     h->cap_k = k;
-    one_step(h, k == nst - 1);
+    one_step(h);
   }
   h->cap_k = -1;
   CK(cudaStreamEndCapture(h->stream, &g));
@@ -398,6 +406,8 @@ VP_API int sim_create(const sim_system *systems, int32_t n_systems, const int32_
   h->n_trials = total_trials;
   h->use_graph = !(p.flags & SIM_NO_GRAPH);
   h->strict_skin = (p.flags & SIM_STRICT_SKIN) ? 1 : 0;
+  if (h->strict_skin && !(p.flags & SIM_FIXED_INTERVAL))
+    return bail(fail(h, SIM_EINVAL, "SIM_STRICT_SKIN applies to fixed-interval lists (SIM_FIXED_INTERVAL)"));
 
   // ---- constants -------------------------------------------------------------
   const double kT = KB * p.temperature;
@@ -451,6 +461,12 @@ VP_API int sim_create(const sim_system *systems, int32_t n_systems, const int32_
   }
   h->rl2_bbox = (float)((rl + 1e-3) * (rl + 1e-3));
   h->half_skin2 = (float)(0.25 * p.skin * p.skin);
+  c.nstlist = p.nstlist;
+  c.list_fixed = (p.flags & SIM_FIXED_INTERVAL) ? 1 : 0;
+  {
+    const double trig = std::max(0.0, 0.5 * p.skin - 1e-5);  // 1e-5 nm cover FP32 rounding
+    c.trig2 = (float)(trig * trig);
+  }
 
   // ---- LJ types: de-duplicate (sigma, epsilon) over all systems -------------
   std::vector<std::pair<double, double>> gtypes;
@@ -683,6 +699,8 @@ VP_API int sim_create(const sim_system *systems, int32_t n_systems, const int32_
     }
   }
   Dev &d = h->d;
+  if ((long long)slot0 / CJ + 1 >= (1LL << J_BITS))
+    return bail(fail(h, SIM_EINVAL, "batch too large: list entries address at most 2^25 half clusters"));
   d.n_trials = total_trials;
   d.n_sys = n_systems;
   d.total_slots = slot0;
@@ -691,11 +709,12 @@ VP_API int sim_create(const sim_system *systems, int32_t n_systems, const int32_
   d.total_work = (int)work.size();
   const int total_atoms = atom0, total_cv = cv0;
 
-  // ---- initial slot contents (caller order, padded) --------------------------------
-  std::vector<float4> pos(slot0), vel(slot0);
+  // ---- initial slot contents (caller order, padded; the idle half cluster past the end) ----
+  std::vector<float4> pos(slot0 + CJ), vel(slot0);
   for (int k = 0; k < slot0; ++k) pos[k] = pad_pos(k);
-  std::vector<int32_t> orig(slot0, -1), type(slot0, 0), slot_of(total_atoms > 0 ? total_atoms : 1);
-  std::vector<float4> ref(total_atoms > 0 ? total_atoms : 1);
+  for (int k = slot0; k < slot0 + CJ; ++k) pos[k] = idle_pos();
+  d.idle_entry = make_uint2((uint32_t)(slot0 / CJ) | (NO_SHIFT << J_BITS), 0u);
+  std::vector<int32_t> orig(slot0, -1), type(slot0 + CJ, 0), slot_of(total_atoms > 0 ? total_atoms : 1);
   std::vector<TrialState> tstate(total_trials);
   std::vector<int32_t> need_vel(total_trials, 0);
   for (int t = 0; t < total_trials; ++t) {
@@ -711,7 +730,6 @@ VP_API int sim_create(const sim_system *systems, int32_t n_systems, const int32_
       orig[sl] = o;
       type[sl] = tmap[T.sys][S.lj_type[o]];
       slot_of[T.atom0 + o] = sl;
-      ref[T.atom0 + o] = make_float4(pp.x, pp.y, pp.z, 0.f);
     }
     tstate[t].n_clus = (S.n_atoms + CL - 1) / CL;
     need_vel[t] = S.vel ? 0 : 1;
@@ -732,9 +750,9 @@ VP_API int sim_create(const sim_system *systems, int32_t n_systems, const int32_
   r |= dalloc(h, &d.type_b, slot0);
   r |= upload(h, &d.slot_trial, slot_trial);
   r |= dalloc(h, &d.slot_col, slot0);
-  r |= dalloc(h, &d.fx, slot0);
-  r |= dalloc(h, &d.fy, slot0);
-  r |= dalloc(h, &d.fz, slot0);
+  r |= dalloc(h, &d.fx, slot0 + CJ);
+  r |= dalloc(h, &d.fy, slot0 + CJ);
+  r |= dalloc(h, &d.fz, slot0 + CJ);
   r |= upload(h, &d.clus_trial, clus_trial);
   r |= dalloc(h, &d.bb_lo, 2 * (size_t)d.total_clus);  // per 4-atom half cluster
   r |= dalloc(h, &d.bb_hi, 2 * (size_t)d.total_clus);
@@ -748,7 +766,7 @@ VP_API int sim_create(const sim_system *systems, int32_t n_systems, const int32_
   r |= dalloc(h, &d.col_ztab, (size_t)col0 * (ZBINS + 1));
   r |= dalloc(h, &d.bucket, total_atoms);
   r |= upload(h, &d.slot_of, slot_of);
-  r |= upload(h, &d.ref_pos, ref);
+  r |= dalloc(h, &d.ref_slot, slot0);
   r |= dalloc(h, &d.gx, total_cv);
   r |= dalloc(h, &d.gy, total_cv);
   r |= dalloc(h, &d.gz, total_cv);
@@ -792,7 +810,11 @@ VP_API int sim_create(const sim_system *systems, int32_t n_systems, const int32_
   r |= dalloc(h, &d.kick, 1);
   r |= dalloc(h, &d.done, 1);
   r |= dalloc(h, &d.energy, (size_t)total_trials * 5);
-  r |= dalloc(h, &d.skin_count, 1);
+  r |= dalloc(h, &d.diag, 4);
+  r |= dalloc(h, &d.cur_step, 1);
+  r |= dalloc(h, &d.rb, 3 * (size_t)total_trials);
+  r |= dalloc(h, &d.last_rb, total_trials);
+  r |= dalloc(h, &d.gdirty, d.total_clus);
   r |= dalloc(h, &h->d_argmin, 1);
   r |= dalloc(h, &h->d_count, 1);
   r |= dalloc(h, &h->d_flag, 1);
@@ -806,6 +828,10 @@ VP_API int sim_create(const sim_system *systems, int32_t n_systems, const int32_
   float half = 0.5f;
   if (cudaMemcpy(d.kick, &half, sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess)
     return bail(fail(h, SIM_ECUDA, "cudaMemcpy kick"));
+  // no rebuild requested for any step yet (a step number's low 32 bits never
+  // equal this value within 2^32 steps of creation)
+  if (cudaMemset(d.rb, 0xff, 3 * sizeof(uint32_t) * (size_t)total_trials) != cudaSuccess)
+    return bail(fail(h, SIM_ECUDA, "cudaMemset rebuild requests"));
 
   // ---- native contact map, velocities, first lists and forces -------------------------
   int32_t *d_need = nullptr, *d_nat0 = nullptr, *d_tsys = nullptr, *d_st0 = nullptr, *d_snt = nullptr;
@@ -825,7 +851,7 @@ VP_API int sim_create(const sim_system *systems, int32_t n_systems, const int32_
   launch_cnat(d, c, d_native, d_nat0, (int)tiles.size(), d_tsys, st);
   launch_zconst(d, d_st0, d_snt, st);
   launch_init_vel(d, (float)kT, d_need, st);
-  forces(h, FIN_INIT, true);
+  forces(h, FIN_INIT, -1);
   if (cudaStreamSynchronize(st) != cudaSuccess || cudaGetLastError() != cudaSuccess)
     return bail(fail(h, SIM_ECUDA, std::string("initialisation kernels failed: ") +
                                        cudaGetErrorString(cudaGetLastError())));
@@ -845,7 +871,7 @@ VP_API int sim_step_batch(sim_handle *h, int32_t n_steps) {
   int left = n_steps;
   bool pending = false;  // a replay whose in-graph timing events are not read yet
   while (left > 0) {
-    if (h->use_graph && !h->timing && h->step % nst == 0 && left >= nst) {
+    if (h->use_graph && !h->timing && left >= nst) {
       r = capture_chunk(h);
       if (r) return r;
       if (pending) {  // read the previous replay's events before this one records them again
@@ -858,8 +884,7 @@ VP_API int sim_step_batch(sim_handle *h, int32_t n_steps) {
       left -= nst;
       pending = h->gtiming;
     } else {
-      const long long next = h->step + 1;
-      one_step(h, next % nst == 0);
+      one_step(h);
       h->step += 1;
       left -= 1;
     }
@@ -984,10 +1009,44 @@ VP_API int sim_set_state(sim_handle *h, int32_t trial, const double *pos, const 
   CK(cudaMemsetAsync(d.err, 0, sizeof(int), h->stream));
   float half = 0.5f;
   CK(cudaMemcpyAsync(d.kick, &half, sizeof(float), cudaMemcpyHostToDevice, h->stream));
-  forces(h, FIN_RESTORE, true);
+  forces(h, FIN_RESTORE, trial);
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(h->stream));
   return check_flags(h);
+}
+
+VP_API int sim_rebuild(sim_handle *h) {
+  int r = enter(h);
+  if (r) return r;
+  const Dev &d = h->d;
+  CK(cudaMemsetAsync(d.err, 0, sizeof(int), h->stream));
+  CK(cudaMemsetAsync(d.fx, 0, sizeof(long long) * d.total_slots, h->stream));
+  CK(cudaMemsetAsync(d.fy, 0, sizeof(long long) * d.total_slots, h->stream));
+  CK(cudaMemsetAsync(d.fz, 0, sizeof(long long) * d.total_slots, h->stream));
+  size_t ncv = 0;
+  for (auto &T : h->tinfo) ncv += T.n_cv;
+  if (ncv) {
+    CK(cudaMemsetAsync(d.gx, 0, sizeof(long long) * ncv, h->stream));
+    CK(cudaMemsetAsync(d.gy, 0, sizeof(long long) * ncv, h->stream));
+    CK(cudaMemsetAsync(d.gz, 0, sizeof(long long) * ncv, h->stream));
+  }
+  forces(h, FIN_KEEP, -1);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(h->stream));
+  return check_flags(h);
+}
+
+VP_API int sim_list_positions(sim_handle *h, int32_t trial, double *pos) {
+  int r = enter(h);
+  if (r) return r;
+  if (trial < 0 || trial >= h->n_trials || !pos) return fail(h, SIM_EINVAL, "trial out of range or pos is NULL");
+  const int n = h->tinfo[trial].n_atoms;
+  r = ensure_dbuf(h, (size_t)3 * n);
+  if (r) return r;
+  launch_list_positions(h->d, trial, h->dbuf, n, h->stream);
+  CK(cudaMemcpyAsync(pos, h->dbuf, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return SIM_OK;
 }
 
 VP_API int64_t sim_step_count(const sim_handle *h) { return h ? h->step : -1; }
@@ -998,6 +1057,7 @@ VP_API int sim_set_step_count(sim_handle *h, int64_t step) {
   if (step < 0) return fail(h, SIM_EINVAL, "negative step");
   long long s = step;
   CK(cudaMemcpyAsync(h->d.step, &s, sizeof(s), cudaMemcpyHostToDevice, h->stream));
+  CK(cudaMemcpyAsync(h->d.cur_step, &s, sizeof(s), cudaMemcpyHostToDevice, h->stream));
   CK(cudaStreamSynchronize(h->stream));
   h->step = step;
   return SIM_OK;
@@ -1242,7 +1302,7 @@ VP_API int sim_autotune(sim_handle *h, int32_t reps, const char *cache_path, int
   if (!tune_lookup(cache_path, key, pv, cv)) {
     // scratch accumulators: the timed launches must not touch the state
     Dev scratch = h->d;
-    const size_t ns = (size_t)h->d.total_slots;
+    const size_t ns = (size_t)h->d.total_slots + CJ;  // with the idle half cluster
     size_t ncv = 0;
     for (auto &T : h->tinfo) ncv += T.n_cv;
     long long *buf = nullptr;
@@ -1333,10 +1393,10 @@ VP_API int sim_diagnostics(sim_handle *h, int64_t *out) {
   int r = enter(h);
   if (r) return r;
   if (!out) return fail(h, SIM_EINVAL, "out is NULL");
-  long long skin = 0;
+  long long dg[4] = {0, 0, 0, 0};
   std::vector<int32_t> ln(h->d.total_clus);
   std::vector<TrialState> S(h->n_trials);
-  CK(cudaMemcpyAsync(&skin, h->d.skin_count, sizeof(skin), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaMemcpyAsync(dg, h->d.diag, sizeof(dg), cudaMemcpyDeviceToHost, h->stream));
   CK(cudaMemcpyAsync(ln.data(), h->d.list_n, sizeof(int32_t) * ln.size(), cudaMemcpyDeviceToHost, h->stream));
   CK(cudaMemcpyAsync(S.data(), h->d.tstate, sizeof(TrialState) * S.size(), cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
@@ -1345,11 +1405,13 @@ VP_API int sim_diagnostics(sim_handle *h, int64_t *out) {
   long long used = 0, entries = 0;
   for (auto &s : S) used += s.n_clus;
   for (int v : ln) entries += v;
-  out[0] = skin;
+  out[0] = dg[0];
   out[1] = mx;
   out[2] = h->c.list_cap;
   out[3] = used;
   out[4] = entries;
+  out[5] = dg[1];
+  out[6] = dg[2];
   return SIM_OK;
 }
 

@@ -236,7 +236,7 @@ __global__ void __launch_bounds__(CVFIN_THREADS) k_cvfin(Dev d, SimConst c) {
     S.a = a;
     S.phi = phi;
     if (!isfinite(z)) atomicOr(d.err, ERR_NONFINITE);
-    if (c.rec_cap > 0) {
+    if (c.rec_cap > 0 && MODE != FIN_KEEP) {
       long long n = MODE == FIN_STEP ? step_now + 1 : step_now;
       double *r = d.rec + ((size_t)t * c.rec_cap + (size_t)(n % c.rec_cap)) * 5;
       r[0] = z; r[1] = S.zm; r[2] = a; r[3] = phi; r[4] = Q;
@@ -299,7 +299,8 @@ void launch_cv(const Dev &d, const SimConst &c, cudaStream_t s, int variant) {
 void launch_cvfin(const Dev &d, const SimConst &c, FinMode mode, cudaStream_t s) {
   if (mode == FIN_STEP) k_cvfin<FIN_STEP><<<d.n_trials, CVFIN_THREADS, 0, s>>>(d, c);
   else if (mode == FIN_INIT) k_cvfin<FIN_INIT><<<d.n_trials, CVFIN_THREADS, 0, s>>>(d, c);
-  else k_cvfin<FIN_RESTORE><<<d.n_trials, CVFIN_THREADS, 0, s>>>(d, c);
+  else if (mode == FIN_RESTORE) k_cvfin<FIN_RESTORE><<<d.n_trials, CVFIN_THREADS, 0, s>>>(d, c);
+  else k_cvfin<FIN_KEEP><<<d.n_trials, CVFIN_THREADS, 0, s>>>(d, c);
 }
 
 }  // namespace vp

@@ -8,6 +8,11 @@ namespace vp {
 struct Dev {
   int32_t n_trials, n_sys;
   int32_t total_slots, total_clus, total_cols, total_work;
+  // one 4-atom half cluster past the last slot (pos, type and force arrays
+  // hold total_slots + 4 entries) sits at idle_pos(): the entry of a lane
+  // with no list entry to work on points there, so its pairs fall outside
+  // the cut-off with or without the pair masks
+  uint2 idle_entry;
   TrialInfo *tinfo;
   TrialState *tstate;
   // slots (cluster order); *_b are the targets of the re-sort at a rebuild
@@ -28,7 +33,7 @@ struct Dev {
   int32_t *bucket;                     // [total trial atoms]
   // per trial, caller-ordered
   int32_t *slot_of;                    // [total trial atoms]
-  float4 *ref_pos;                     // positions at the last rebuild
+  float4 *ref_slot;                    // [slots] the positions the trial's current list was built from
   long long *gx, *gy, *gz;             // CV gradient, fixed point, [total CV atoms]
   double *z_part;                      // [total_work] per-tile partial sums of z
   // per system, caller-ordered
@@ -57,21 +62,36 @@ struct Dev {
   float *kick;
   unsigned int *done;                  // block ticket of the per-trial finaliser
   long long *energy;                   // [n_trials * 5] fixed point (2^24): LJ, RF, bond, angle, kin
-  long long *skin_count;
+  long long *diag;                     // [4]: skin violations (fixed-interval lists), trial rebuilds,
+                                       // rebuilds triggered by a displacement, spare
+  // list rebuilds: a trial's list is rebuilt in the step whose number (low
+  // 32 bits) its decision entry holds
+  unsigned long long *cur_step;        // number of the step being computed (or of the state held)
+  uint32_t *rb;                        // [3 n_trials]: displacement request, forced request, decision
+  uint32_t *last_rb;                   // [n_trials] step of the trial's last rebuild
+  uint32_t *gdirty;                    // [clusters] bit k < 31: entries 8k..8k+7 hold exclusions, the
+                                       // cluster itself or mixed images (the pair kernels then apply the
+                                       // pair masks); bit 31: some group from the 31st on does
   double *rec;                         // [n_trials * rec_cap * 5]: z, z_m, a, phi, Q
   unsigned *pair_next;                 // work counter of the persistent pair kernel
   int32_t n_sm;                        // multiprocessors of the device
 };
 
 enum UpdateMode { UPD_DRIFT = 0, UPD_FINAL = 1 };
-enum FinMode { FIN_STEP = 0, FIN_INIT = 1, FIN_RESTORE = 2 };
+// FIN_STEP: a step (Phi accumulates, the step counter advances); FIN_INIT:
+// z_m = z; FIN_RESTORE: a new state (z and a from the stored z_m, the record
+// entry of the current step rewritten); FIN_KEEP: the same state again after a
+// forced list rebuild (nothing recorded)
+enum FinMode { FIN_STEP = 0, FIN_INIT = 1, FIN_RESTORE = 2, FIN_KEEP = 3 };
 
 // rebuild (vp_rebuild.cu)
+void launch_rebuild_request(const Dev &d, int32_t trial, cudaStream_t s);
 void launch_bin(const Dev &d, const SimConst &c, float half_skin2, int strict_skin, cudaStream_t s);
-void launch_colscan(const Dev &d, cudaStream_t s);
+void launch_colscan(const Dev &d, const SimConst &c, cudaStream_t s);
 void launch_colfill(const Dev &d, cudaStream_t s);
 void launch_colsort(const Dev &d, cudaStream_t s);
 void launch_list(const Dev &d, const SimConst &c, float rl2_bbox, cudaStream_t s);
+void launch_list_positions(const Dev &d, int32_t trial, double *out, int32_t n, cudaStream_t s);
 // forces (vp_pair.cu)
 void launch_pair(const Dev &d, const SimConst &c, bool energy, int32_t only_trial, cudaStream_t s, int variant = 0);
 void launch_bonded(const Dev &d, cudaStream_t s);

@@ -42,6 +42,8 @@ constexpr int ERR_SKIN = 16;
 constexpr uint32_t J_BITS = 25;
 constexpr uint32_t J_MASK = (1u << J_BITS) - 1u;
 constexpr uint32_t E_EXACT = 1u << 31;
+// image code of no shift ((0+1) | (0+1) << 2 | (0+1) << 4)
+constexpr uint32_t NO_SHIFT = 21u;
 
 // Padding slots sit far outside every box, on distinct points 64 nm apart,
 // so that no pair involving one can fall inside the cut-off (boxes < 60 nm).
@@ -123,7 +125,23 @@ struct SimConst {
   int32_t rec_cap;
   int32_t uniform_gamma;      // every atom of every system has the same friction
   float c1_u, c2sqkT_u;       // then exp(-gamma dt) and sqrt((1 - c1^2) kT)
+  // list rebuilds: at most nstlist steps apart; unless list_fixed, also in
+  // the first step in which an atom of the trial has moved farther than
+  // skin/2 - 1e-5 nm (squared: trig2) from where its list was built
+  int32_t nstlist, list_fixed;
+  float trig2;
 };
+
+// whether trial t rebuilds its list in step n: a displacement or forced
+// request for this step, or the longest interval reached (fixed-interval
+// lists: steps that are multiples of nstlist)
+__device__ __forceinline__ bool rebuild_due(const uint32_t *rb, const uint32_t *last_rb, int n_trials,
+                                            const SimConst &c, int t, unsigned long long n) {
+  const uint32_t n32 = (uint32_t)n;
+  if (rb[t] == n32 || rb[n_trials + t] == n32) return true;
+  if (c.list_fixed) return n % (unsigned long long)c.nstlist == 0ull;
+  return n32 - last_rb[t] >= (uint32_t)c.nstlist;
+}
 
 // ---------------------------------------------------------------------------
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11)

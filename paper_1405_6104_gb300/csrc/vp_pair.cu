@@ -11,6 +11,7 @@
 // share of every bond and angle it is part of) come from k_bonded; the
 // energy kernel k_pair computes the bonded energies itself.
 #include <algorithm>
+#include <type_traits>
 
 #include "vp_dev.cuh"
 
@@ -163,12 +164,12 @@ __global__ void __launch_bounds__(128, MINB) k_pair(Dev d, SimConst c, int only_
   // software pipeline: the entry two groups ahead and the j-atom of the next
   // group are in flight while the current group is evaluated; idle lanes get
   // an empty mask
-  uint2 ent = g < n ? seg[g] : make_uint2(0u, 0u);
-  uint2 ent_n = 8 + g < n ? seg[8 + g] : make_uint2(0u, 0u);
+  uint2 ent = g < n ? seg[g] : d.idle_entry;
+  uint2 ent_n = 8 + g < n ? seg[8 + g] : d.idle_entry;
   float4 pj = d.pos[(int)(ent.x & J_MASK) * CJ + b];
   int tj = d.type[(int)(ent.x & J_MASK) * CJ + b];
   for (int e0 = 0; e0 < n; e0 += 8) {
-    const uint2 ent_nn = e0 + 16 + g < n ? seg[e0 + 16 + g] : make_uint2(0u, 0u);
+    const uint2 ent_nn = e0 + 16 + g < n ? seg[e0 + 16 + g] : d.idle_entry;
     const int sj_n = (int)(ent_n.x & J_MASK) * CJ + b;
     const float4 pj_n = d.pos[sj_n];
     const int tj_n = d.type[sj_n];
@@ -303,12 +304,13 @@ __global__ void __launch_bounds__(PF_WARPS * 32, MINB) k_pair_f(Dev d, SimConst 
 
   const int n = d.list_n[I];
   const uint2 *seg = d.list + (size_t)I * c.list_cap;
-  uint2 ent = g < n ? seg[g] : make_uint2(0u, 0u);
-  uint2 ent_n = 8 + g < n ? seg[8 + g] : make_uint2(0u, 0u);
+  const uint32_t gd = d.gdirty[I];
+  uint2 ent = g < n ? seg[g] : d.idle_entry;
+  uint2 ent_n = 8 + g < n ? seg[8 + g] : d.idle_entry;
   float4 pj = d.pos[(int)(ent.x & J_MASK) * CJ + b];
   int tj = d.type[(int)(ent.x & J_MASK) * CJ + b];
   for (int e0 = 0; e0 < n; e0 += 8) {
-    const uint2 ent_nn = e0 + 16 + g < n ? seg[e0 + 16 + g] : make_uint2(0u, 0u);
+    const uint2 ent_nn = e0 + 16 + g < n ? seg[e0 + 16 + g] : d.idle_entry;
     const int sj_n = (int)(ent_n.x & J_MASK) * CJ + b;
     const float4 pj_n = d.pos[sj_n];
     const int tj_n = d.type[sj_n];
@@ -320,11 +322,16 @@ __global__ void __launch_bounds__(PF_WARPS * 32, MINB) k_pair_f(Dev d, SimConst 
     const float2 *row = &s_cij[wib][0][tj];
     // j-force: even and odd i-atoms in two partial sums (the packed variant's order)
     float fjx[2] = {0.f, 0.f}, fjy[2] = {0.f, 0.f}, fjz[2] = {0.f, 0.f};
-    if (!__any_sync(0xffffffffu, exact)) {
+    // one image per entry; MASKED: the pair masks apply (a group with
+    // exclusions or the cluster itself); else the cut-off alone decides, which
+    // gives the same forces: a listed pair that failed the list rule is still
+    // beyond the cut-off (lists are rebuilt before any atom has moved skin/2)
+    auto one_image = [&](auto mtag) {
+      constexpr bool MASKED = decltype(mtag)::value;
 #pragma unroll
       for (int a = 0; a < CL; ++a) {
         const float4 ia = SHI ? s_i[wib][a] : make_float4(xi[a], yi[a], zi[a], qi[a]);
-        const float pen = (mb & (1u << (4 * a))) ? 0.0f : MASK_PEN;
+        const float pen = MASKED ? ((mb & (1u << (4 * a))) ? 0.0f : MASK_PEN) : 0.0f;
         const float dx = __fsub_rn(xj, ia.x), dy = __fsub_rn(yj, ia.y), dz = __fsub_rn(zj, ia.z);
         const float r2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmaf_rn(dx, dx, pen)));
         const float rinv = rsqrtf(r2);
@@ -345,6 +352,12 @@ __global__ void __launch_bounds__(PF_WARPS * 32, MINB) k_pair_f(Dev d, SimConst 
         fjy[a & 1] = __fmaf_rn(f, dy, fjy[a & 1]);
         fjz[a & 1] = __fmaf_rn(f, dz, fjz[a & 1]);
       }
+    };
+    const bool masked = (gd >> min(e0 >> 3, 31)) & 1u;
+    if (!masked) {
+      one_image(std::false_type{});
+    } else if (!__any_sync(0xffffffffu, exact)) {
+      one_image(std::true_type{});
     } else {
       // some entry of this group needs pair-by-pair minimum images
 #pragma unroll
@@ -464,13 +477,14 @@ __global__ void __launch_bounds__(PF_WARPS * 32, MINB) k_pair_f2(Dev d, SimConst
 
   const int n = d.list_n[I];
   const uint2 *seg = d.list + (size_t)I * c.list_cap;
+  const uint32_t gd = d.gdirty[I];
   // list entries are fetched two groups ahead; the j-atom itself at the top
   // of its iteration (fewer live registers: a higher block count per SM hides
   // that load better than a prefetch does)
-  uint2 ent = g < n ? seg[g] : make_uint2(0u, 0u);
-  uint2 ent_n = 8 + g < n ? seg[8 + g] : make_uint2(0u, 0u);
+  uint2 ent = g < n ? seg[g] : d.idle_entry;
+  uint2 ent_n = 8 + g < n ? seg[8 + g] : d.idle_entry;
   for (int e0 = 0; e0 < n; e0 += 8) {
-    const uint2 ent_nn = e0 + 16 + g < n ? seg[e0 + 16 + g] : make_uint2(0u, 0u);
+    const uint2 ent_nn = e0 + 16 + g < n ? seg[e0 + 16 + g] : d.idle_entry;
     const int sj = (int)(ent.x & J_MASK) * CJ + b;
     const float4 pj = d.pos[sj];
     const int tj = d.type[sj];
@@ -480,7 +494,12 @@ __global__ void __launch_bounds__(PF_WARPS * 32, MINB) k_pair_f2(Dev d, SimConst
     const bool exact = (ent.x & E_EXACT) != 0u;
     const float4 *row = &s_c4[wib][0][tj];
     float fjx, fjy, fjz;
-    if (!__any_sync(0xffffffffu, exact)) {
+    // one image per entry; MASKED: the pair masks apply (a group with
+    // exclusions or the cluster itself); else the cut-off alone decides, which
+    // gives the same forces: a listed pair that failed the list rule is still
+    // beyond the cut-off (lists are rebuilt before any atom has moved skin/2)
+    auto one_image = [&](auto mtag) {
+      constexpr bool MASKED = decltype(mtag)::value;
       const float2 xj2 = make_float2(xj, xj), yj2 = make_float2(yj, yj), zj2 = make_float2(zj, zj);
       const float2 qj2 = make_float2(qj, qj);
       float2 gx = make_float2(0.f, 0.f), gy = gx, gz = gx;
@@ -502,8 +521,8 @@ __global__ void __launch_bounds__(PF_WARPS * 32, MINB) k_pair_f2(Dev d, SimConst
         tt = __ffma2_rn(qq, rinv, tt);
         tt = __fmul2_rn(tt, rinv2);
         float2 f = __ffma2_rn(qq, m2krf, tt);
-        f.x = ((mb & (1u << (8 * p))) && r2.x < rc2) ? f.x : 0.0f;
-        f.y = ((mb & (1u << (8 * p + 4))) && r2.y < rc2) ? f.y : 0.0f;
+        f.x = ((!MASKED || (mb & (1u << (8 * p)))) && r2.x < rc2) ? f.x : 0.0f;
+        f.y = ((!MASKED || (mb & (1u << (8 * p + 4)))) && r2.y < rc2) ? f.y : 0.0f;
         fx[p] = __ffma2_rn(f, dx, fx[p]);
         fy[p] = __ffma2_rn(f, dy, fy[p]);
         fz[p] = __ffma2_rn(f, dz, fz[p]);
@@ -514,6 +533,12 @@ __global__ void __launch_bounds__(PF_WARPS * 32, MINB) k_pair_f2(Dev d, SimConst
       fjx = gx.x + gx.y;
       fjy = gy.x + gy.y;
       fjz = gz.x + gz.y;
+    };
+    const bool masked = (gd >> min(e0 >> 3, 31)) & 1u;
+    if (!masked) {
+      one_image(std::false_type{});
+    } else if (!__any_sync(0xffffffffu, exact)) {
+      one_image(std::true_type{});
     } else {
       // some entry of this group needs pair-by-pair minimum images
       float2 gx = make_float2(0.f, 0.f), gy = gx, gz = gx;

@@ -1,5 +1,15 @@
 // vp_rebuild.cu -- cell binning, spatial sort into 8-atom clusters and the
-// cluster-pair Verlet list (every nstlist steps).
+// cluster-pair Verlet list of the trials whose list is due.
+//
+// Every kernel here runs in every step and works only on the trials whose
+// list is due in that step (the decision of k_bin, kept in d.rb); the others
+// return at once.  A trial's list is due when one of its atoms has moved
+// farther than skin/2 - 1e-5 nm from where its list was built (the update
+// kernel requests it), after nstlist steps, or on request from the host
+// (creation, a new state).  The first rule keeps every pair closer than r_cut
+// in the list at every force evaluation: two atoms that were at least
+// r_cut + skin apart when the list was built are still farther apart than
+// r_cut (the 1e-5 nm cover FP32 rounding).
 //
 // Layout: per trial the box is cut into ncol x ncol columns along x and y;
 // atoms are sorted by (column, z) and cut into clusters of 8 (the last
@@ -15,31 +25,45 @@ namespace vp {
 // ---------------------------------------------------------------------------
 // binning: wrap into the box, pick the column, count, skin check
 // ---------------------------------------------------------------------------
-__global__ void k_bin(Dev d, float half_skin2, int strict) {
+// forced rebuild of one trial (trial >= 0) or of all, in the step held now
+__global__ void k_rebuild_request(Dev d, int trial) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= d.n_trials || (trial >= 0 && t != trial)) return;
+  d.rb[d.n_trials + t] = (uint32_t)*d.cur_step;
+}
+
+// the rebuild decision of trial t in the current step, taken by k_bin
+__device__ __forceinline__ bool rebuilding(const Dev &d, int t) { return d.rb[2 * d.n_trials + t] == (uint32_t)*d.cur_step; }
+
+__global__ void k_bin(Dev d, SimConst c, float half_skin2, int strict) {
   int slot = blockIdx.x * blockDim.x + threadIdx.x;
   if (slot >= d.total_slots) return;
   int t = d.slot_trial[slot];
+  const unsigned long long n = *d.cur_step;
+  if (!rebuild_due(d.rb, d.last_rb, d.n_trials, c, t, n)) return;
   const TrialInfo T = d.tinfo[t];
   int local = slot - T.slot0;
+  if (local == 0) d.rb[2 * d.n_trials + t] = (uint32_t)n;  // the decision the other rebuild kernels read
   int o = d.orig[slot];
   if (local >= d.tstate[t].n_clus * CL || o < 0) { d.slot_col[slot] = -1; return; }
   float4 p = d.pos[slot];
   const float L = T.box, iL = T.inv_box;
+  if (c.list_fixed && d.rb[d.n_trials + t] != (uint32_t)n) {
+    // fixed-interval lists: an atom farther than skin/2 from where the list
+    // was built may have left pairs out (the slot is the one it had then;
+    // a forced rebuild follows a new state, not a list interval)
+    const float4 r = d.ref_slot[slot];
+    const float ddx = p.x - r.x, ddy = p.y - r.y, ddz = p.z - r.z;
+    if (ddx * ddx + ddy * ddy + ddz * ddz > half_skin2) {
+      atomicAdd(reinterpret_cast<unsigned long long *>(d.diag), 1ull);
+      if (strict) atomicOr(d.err, ERR_SKIN);
+    }
+  }
   float x = p.x - L * floorf(p.x * iL), y = p.y - L * floorf(p.y * iL), z = p.z - L * floorf(p.z * iL);
   x = x >= L ? x - L : (x < 0.0f ? x + L : x);
   y = y >= L ? y - L : (y < 0.0f ? y + L : y);
   z = z >= L ? z - L : (z < 0.0f ? z + L : z);
   z += 0.0f;  // no negative zero in the sort key
-  // displacement since the last rebuild (minimum image)
-  float4 r = d.ref_pos[T.atom0 + o];
-  float ddx = x - r.x, ddy = y - r.y, ddz = z - r.z;
-  ddx -= L * rintf(ddx * iL);
-  ddy -= L * rintf(ddy * iL);
-  ddz -= L * rintf(ddz * iL);
-  if (ddx * ddx + ddy * ddy + ddz * ddz > half_skin2) {
-    atomicAdd(reinterpret_cast<unsigned long long *>(d.skin_count), 1ull);
-    if (strict) atomicOr(d.err, ERR_SKIN);
-  }
   // a coordinate that is not finite, or so large that one wrap cannot bring
   // it into the box (a run that has blown up), is an error; the atom is put
   // at the origin so that every index below stays inside the grid
@@ -47,15 +71,14 @@ __global__ void k_bin(Dev d, float half_skin2, int strict) {
     atomicOr(d.err, ERR_NONFINITE);
     x = y = z = 0.0f;
   }
-  d.ref_pos[T.atom0 + o] = make_float4(x, y, z, 0.0f);
   d.pos[slot] = make_float4(x, y, z, p.w);
   int cx = max(0, min((int)(x * T.inv_col_w), T.ncol - 1));
   int cy = max(0, min((int)(y * T.inv_col_w), T.ncol - 1));
-  int c = cx * T.ncol + cy;
-  d.slot_col[slot] = c;
+  const int col = cx * T.ncol + cy;
+  d.slot_col[slot] = col;
   // slots are in column order from the last rebuild, so a warp's atoms fall
   // into one or two columns: one atomic per column and warp
-  const int cg = T.col0 + c;
+  const int cg = T.col0 + col;
   const unsigned peers = __match_any_sync(__activemask(), cg);
   if ((threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&d.col_count[cg], __popc(peers));
 }
@@ -67,6 +90,7 @@ __global__ void k_colscan(Dev d) {
   constexpr int NT = 256;
   __shared__ int s_a[NT], s_c[NT];
   int t = blockIdx.x;
+  if (!rebuilding(d, t)) return;
   const TrialInfo T = d.tinfo[t];
   int nc = T.ncol * T.ncol;
   int per = (nc + NT - 1) / NT;
@@ -105,7 +129,13 @@ __global__ void k_colscan(Dev d) {
     if (threadIdx.x == 0) atomicOr(d.err, ERR_CAPACITY);
     total = T.max_clus;
   }
-  if (threadIdx.x == NT - 1) d.tstate[t].n_clus = total;
+  if (threadIdx.x == NT - 1) {
+    d.tstate[t].n_clus = total;
+    const uint32_t n32 = (uint32_t)*d.cur_step;
+    d.last_rb[t] = n32;
+    atomicAdd(reinterpret_cast<unsigned long long *>(d.diag + 1), 1ull);
+    if (d.rb[t] == n32) atomicAdd(reinterpret_cast<unsigned long long *>(d.diag + 2), 1ull);
+  }
   // slots past the new clusters become empty (the re-sorted layout is copied
   // over the current one after k_colsort)
   for (int sl = T.slot0 + total * CL + threadIdx.x; sl < T.slot0 + T.max_clus * CL; sl += NT) {
@@ -122,9 +152,10 @@ __global__ void k_colscan(Dev d) {
 __global__ void k_colfill(Dev d) {
   int slot = blockIdx.x * blockDim.x + threadIdx.x;
   if (slot >= d.total_slots) return;
+  int t = d.slot_trial[slot];
+  if (!rebuilding(d, t)) return;
   int c = d.slot_col[slot];
   if (c < 0) return;
-  int t = d.slot_trial[slot];
   const TrialInfo &T = d.tinfo[t];
   int cg = T.col0 + c;
   // one atomic per column and warp; the lanes of a column take consecutive
@@ -149,8 +180,12 @@ __global__ void __launch_bounds__(128) k_colsort(Dev d) {
   __shared__ float s_zlo[COL_CAP / CJ + 2];  // lower z-bound of every half
   int cg = blockIdx.x;
   int t = d.col_trial[cg];
+  if (!rebuilding(d, t)) return;
   const TrialInfo T = d.tinfo[t];
   int n = d.col_count[cg];
+  __syncthreads();
+  // the count is consumed: the column starts from zero at the trial's next rebuild
+  if (threadIdx.x == 0) d.col_count[cg] = 0;
   if (n > COL_CAP) return;  // flagged by k_colscan
   int start = d.col_start[cg], cstart = d.col_cstart[cg];
   if (cstart + (n + CL - 1) / CL > T.max_clus) return;  // flagged by k_colscan
@@ -302,10 +337,12 @@ __global__ void __launch_bounds__(LIST_WARPS * 32, 8) k_list(Dev d, SimConst c, 
   __shared__ int s_nex[LIST_WARPS][CL];
   __shared__ float4 s_xp[LIST_WARPS][CL / 2][2];  // i-atom pairs (2p, 2p+1): {-x, -x', -y, -y'} {-z, -z', 0, 0}
   const int wib = threadIdx.x >> 5;
+  __shared__ unsigned s_dirty[LIST_WARPS];  // groups of 8 entries that need the pair masks
   const int I = blockIdx.x * LIST_WARPS + wib;
   const int lane = threadIdx.x & 31;
   if (I >= d.total_clus) return;
   const int t = d.clus_trial[I];
+  if (!rebuilding(d, t)) return;
   const TrialInfo T = d.tinfo[t];
   const int Il = I - T.clus0;
   if (Il >= d.tstate[t].n_clus) {
@@ -336,9 +373,8 @@ __global__ void __launch_bounds__(LIST_WARPS * 32, 8) k_list(Dev d, SimConst c, 
     // wider on each side than needed (every half in them is still tested)
     int a1 = 0, n1 = 0, a2 = 0, n2 = 0;
     if (cc < nc2) {
-      const int n = d.col_count[T.col0 + cc];
       const int ccs = d.col_cstart[T.col0 + cc];
-      const int ncl = (n + CL - 1) / CL;
+      const int ncl = max(0, (cc + 1 < nc2 ? d.col_cstart[T.col0 + cc + 1] : d.tstate[t].n_clus) - ccs);
       const int jlo = max(ccs, Il);
       if (ccs + ncl > jlo) {
         const int cx = cc / T.ncol, cy = cc - cx * T.ncol;
@@ -441,6 +477,7 @@ __global__ void __launch_bounds__(LIST_WARPS * 32, 8) k_list(Dev d, SimConst c, 
     for (int k = 0; k < n; ++k) s_excl[wib][lane][k] = d.excl[(size_t)sa * MAX_EXCL + k];
     s_nex[wib][lane] = n;
   }
+  if (lane == 0) s_dirty[wib] = c.list_fixed ? ~0u : 0u;  // fixed-interval lists: masks everywhere
   __syncwarp();
   // ---- phase 2: one candidate 4-atom j-cluster per lane ----
   // Image counts: q = rint(fl(d * invL)) is monotone in d = fl(xj - xi), so
@@ -508,7 +545,12 @@ __global__ void __launch_bounds__(LIST_WARPS * 32, 8) k_list(Dev d, SimConst c, 
     }
     const unsigned bal = __ballot_sync(0xffffffffu, mask != 0u);
     const int pos = cnt + __popc(bal & ((1u << lane) - 1u));
-    if (mask != 0u && pos < c.list_cap) seg[pos] = make_uint2(w0, mask);
+    if (mask != 0u && pos < c.list_cap) {
+      seg[pos] = make_uint2(w0, mask);
+      // the cluster with itself (pairs below the diagonal masked) and entries
+      // whose pairs take images one by one need the masks in the pair kernel
+      if ((int)((w0 & J_MASK) >> 1) == I || (w0 & E_EXACT)) atomicOr(&s_dirty[wib], 1u << min(pos >> 3, 31));
+    }
     cnt += __popc(bal);
   }
   const int n_ent = min(cnt, c.list_cap);
@@ -530,35 +572,65 @@ __global__ void __launch_bounds__(LIST_WARPS * 32, 8) k_list(Dev d, SimConst c, 
         const int mid = (lo_e + hi_e) >> 1;
         if ((seg[mid].x & J_MASK) < j4) lo_e = mid + 1; else hi_e = mid;
       }
-      if (lo_e < n_ent && (seg[lo_e].x & J_MASK) == j4)
+      if (lo_e < n_ent && (seg[lo_e].x & J_MASK) == j4) {
         atomicAnd(&seg[lo_e].y, ~(1u << (lane * CJ + (sj & 3))));
+        atomicOr(&s_dirty[wib], 1u << min(lo_e >> 3, 31));
+      }
     }
   }
+  __syncwarp();
   if (lane == 0) {
+    d.gdirty[I] = s_dirty[wib];
     d.list_n[I] = n_ent;
     if (cnt > c.list_cap || overflow) atomicOr(d.err, ERR_LIST);
   }
 }
 
+// the re-sorted layout replaces the current one (slots of rebuilding trials),
+// and its positions are the ones the new list is built from
+__global__ void k_copyback(Dev d) {
+  const int slot = blockIdx.x * blockDim.x + threadIdx.x;
+  if (slot >= d.total_slots || !rebuilding(d, d.slot_trial[slot])) return;
+  const float4 p = d.pos_b[slot];
+  d.pos[slot] = p;
+  d.ref_slot[slot] = p;
+  d.vel[slot] = d.vel_b[slot];
+  d.orig[slot] = d.orig_b[slot];
+  d.type[slot] = d.type_b[slot];
+}
+
+// positions the current list of one trial was built from, caller order
+__global__ void k_list_positions(Dev d, int trial, double *out, int n) {
+  const int o = blockIdx.x * blockDim.x + threadIdx.x;
+  if (o >= n) return;
+  const float4 p = d.ref_slot[d.slot_of[d.tinfo[trial].atom0 + o]];
+  out[3 * o] = p.x;
+  out[3 * o + 1] = p.y;
+  out[3 * o + 2] = p.z;
+}
+
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
-void launch_bin(const Dev &d, const SimConst &c, float half_skin2, int strict_skin, cudaStream_t s) {
-  (void)c;
-  cudaMemsetAsync(d.col_count, 0, sizeof(int32_t) * (size_t)d.total_cols, s);
-  k_bin<<<(d.total_slots + 255) / 256, 256, 0, s>>>(d, half_skin2, strict_skin);
+void launch_rebuild_request(const Dev &d, int32_t trial, cudaStream_t s) {
+  k_rebuild_request<<<(d.n_trials + 255) / 256, 256, 0, s>>>(d, trial);
 }
-void launch_colscan(const Dev &d, cudaStream_t s) { k_colscan<<<d.n_trials, 256, 0, s>>>(d); }
+void launch_bin(const Dev &d, const SimConst &c, float half_skin2, int strict_skin, cudaStream_t s) {
+  k_bin<<<(d.total_slots + 255) / 256, 256, 0, s>>>(d, c, half_skin2, strict_skin);
+}
+void launch_colscan(const Dev &d, const SimConst &c, cudaStream_t s) {
+  (void)c;
+  k_colscan<<<d.n_trials, 256, 0, s>>>(d);
+}
+void launch_list_positions(const Dev &d, int32_t trial, double *out, int32_t n, cudaStream_t s) {
+  if (n > 0) k_list_positions<<<(n + 255) / 256, 256, 0, s>>>(d, trial, out, n);
+}
 void launch_colfill(const Dev &d, cudaStream_t s) {
   k_colfill<<<(d.total_slots + 255) / 256, 256, 0, s>>>(d);
 }
 void launch_colsort(const Dev &d, cudaStream_t s) {
   k_colsort<<<d.total_cols, 128, 0, s>>>(d);  // columns hold about 100 atoms: 128 threads keep every thread busy in the sort
-  size_t n = (size_t)d.total_slots;
-  cudaMemcpyAsync(d.pos, d.pos_b, n * sizeof(float4), cudaMemcpyDeviceToDevice, s);
-  cudaMemcpyAsync(d.vel, d.vel_b, n * sizeof(float4), cudaMemcpyDeviceToDevice, s);
-  cudaMemcpyAsync(d.orig, d.orig_b, n * sizeof(int32_t), cudaMemcpyDeviceToDevice, s);
-  cudaMemcpyAsync(d.type, d.type_b, n * sizeof(int32_t), cudaMemcpyDeviceToDevice, s);
+  k_copyback<<<(d.total_slots + 255) / 256, 256, 0, s>>>(d);
 }
 void launch_list(const Dev &d, const SimConst &c, float rl2_bbox, cudaStream_t s) {
   k_list<<<(unsigned)((d.total_clus + LIST_WARPS - 1) / LIST_WARPS), LIST_WARPS * 32, 0, s>>>(d, c, rl2_bbox);

@@ -11,10 +11,11 @@
 
 namespace vp {
 
-// eight blocks per SM (32 registers): the kernel waits on memory round trips
-// and needs every resident warp it can get
+// six blocks per SM (40 registers: with 32 the list buffer's reference
+// position, one more early load, spills): the kernel waits on memory round
+// trips and needs every resident warp it can get
 template <int MODE>
-__global__ void __launch_bounds__(256, 8) k_update(Dev d, SimConst c) {
+__global__ void __launch_bounds__(256, 6) k_update(Dev d, SimConst c) {
   const int slot = blockIdx.x * blockDim.x + threadIdx.x;
   if (slot >= d.total_slots) return;
   if (MODE == UPD_FINAL && slot == 0) *d.kick = 0.5f;
@@ -25,9 +26,11 @@ __global__ void __launch_bounds__(256, 8) k_update(Dev d, SimConst c) {
   const int o = __ldg(d.orig + slot);
   const int t = __ldg(d.slot_trial + slot);
   float4 p = d.pos[slot], v = d.vel[slot];
+  const float4 ref = MODE == UPD_DRIFT && !c.list_fixed ? d.ref_slot[slot] : make_float4(0.f, 0.f, 0.f, 0.f);
   const long long fxi = d.fx[slot], fyi = d.fy[slot], fzi = d.fz[slot];
   const float kick = MODE == UPD_DRIFT ? *d.kick : 0.5f;
   const unsigned long long step = MODE == UPD_DRIFT ? (unsigned long long)(*d.step) + 1ull : 0ull;
+  if (MODE == UPD_DRIFT && slot == 0) *d.cur_step = step;  // the step the rebuild kernels decide for
   if (o < 0) return;
   const int n_cv = __ldg(&d.tinfo[t].n_cv), cv0 = __ldg(&d.tinfo[t].cv0);
   const uint32_t key0 = __ldg(&d.tinfo[t].key0), key1 = __ldg(&d.tinfo[t].key1);
@@ -63,9 +66,24 @@ __global__ void __launch_bounds__(256, 8) k_update(Dev d, SimConst c) {
     v.y = c1 * v.y + c2sd * xi.y;
     v.z = c1 * v.z + c2sd * xi.z;
     p.x += c.half_dt * v.x; p.y += c.half_dt * v.y; p.z += c.half_dt * v.z;
-    if (!(isfinite(p.x) && isfinite(p.y) && isfinite(p.z) && isfinite(v.x) && isfinite(v.y) && isfinite(v.z)))
+    // a run that has blown up: a non-finite state, a force beyond 2^30
+    // kJ/mol/nm (the 64-bit fixed-point sums, 2^32 units per kJ/mol/nm, are
+    // no longer trustworthy) or an atom that crosses the box in one step
+    // (positions are wrapped at every rebuild, so a blown-up run would
+    // otherwise stay finite)
+    const float vlim = __ldg(&d.tinfo[t].box) / c.dt;
+    if (!(isfinite(p.x) && isfinite(p.y) && isfinite(p.z) && isfinite(v.x) && isfinite(v.y) && isfinite(v.z)) ||
+        fmaxf(fabsf(v.x), fmaxf(fabsf(v.y), fabsf(v.z))) > vlim ||
+        fmaxf(fabsf(Fx), fmaxf(fabsf(Fy), fabsf(Fz))) > 1073741824.0f)
       atomicOr(d.err, ERR_NONFINITE);
     d.pos[slot] = p;
+    // moved beyond the list buffer: the trial's list is rebuilt in this step,
+    // before the forces (positions are not wrapped between rebuilds, so this
+    // is the displacement itself)
+    if (!c.list_fixed) {
+      const float ddx = p.x - ref.x, ddy = p.y - ref.y, ddz = p.z - ref.z;
+      if (ddx * ddx + ddy * ddy + ddz * ddz > c.trig2) d.rb[t] = (uint32_t)step;
+    }
   }
   d.vel[slot] = v;
 }
@@ -127,7 +145,6 @@ __global__ void k_scatter_state(Dev d, int trial, const double *pos, const doubl
   v.x = (float)vel[q]; v.y = (float)vel[q + 1]; v.z = (float)vel[q + 2];
   d.pos[s] = p;
   d.vel[s] = v;
-  d.ref_pos[T.atom0 + o] = make_float4(p.x, p.y, p.z, 0.f);
 }
 
 // flag = 1 if any of the n values is not finite (the caller's state is

@@ -154,17 +154,24 @@ def _rand_unit(rng):
     return v / np.linalg.norm(v)
 
 
-def _chain_walk(rng, n, bond, angle, centre, radius, min_dist, max_tries=200):
+def _chain_walk(rng, n, bond, angle, centre, radius, min_dist, max_tries=200, max_backtracks=0):
     """Self-avoiding chain with fixed bond length and bond angle, random
-    dihedrals, kept inside a sphere of the given radius."""
+    dihedrals, kept inside a sphere of the given radius.  When no trial
+    position of an atom keeps min_dist from the chain, the best one is taken;
+    with max_backtracks > 0 only if it keeps at least 0.8 min_dist, otherwise
+    (a dense walk that has trapped itself) the walk backs up 8 atoms and
+    continues from there, up to max_backtracks times (the starting coil of a
+    solvated system, whose atoms interact)."""
     pts = np.zeros((n, 3))
     pts[0] = np.asarray(centre, dtype=np.float64)
     if n == 1:
         return pts
     d = _rand_unit(rng)
     pts[1] = pts[0] + bond * d
-    for i in range(2, n):
-        best, best_score = None, -np.inf
+    backtracks = 0
+    i = 2
+    while i < n:
+        best, best_score, best_md = None, -np.inf, np.inf
         a, b = pts[i - 2], pts[i - 1]
         u = (b - a) / np.linalg.norm(b - a)
         perp = np.cross(u, _rand_unit(rng))
@@ -184,11 +191,16 @@ def _chain_walk(rng, n, bond, angle, centre, radius, min_dist, max_tries=200):
             md = np.sqrt(((prev - c) ** 2).sum(1)).min() if len(prev) else np.inf
             score = min(md - min_dist, 0.0) * 10.0 - max(r_out, 0.0)
             if md >= min_dist and r_out <= 0:
-                best = c
+                best, best_md = c, md
                 break
             if score > best_score:
-                best, best_score = c, score
+                best, best_score, best_md = c, score, md
+        if best_md < 0.8 * min_dist and backtracks < max_backtracks and i > 2:
+            backtracks += 1
+            i = max(2, i - 8)
+            continue
         pts[i] = best
+        i += 1
     return pts
 
 
@@ -318,7 +330,8 @@ def solvated_heteropolymer(n_solute: int = 540, n_water: int = 3500, box: Option
         coil_radius = min(1.8 * scale, 0.42 * L)
     centre = np.full(3, L / 2)
     native = _chain_walk(rng, n_solute, POLY_BOND["r0"], POLY_ANGLE["t0"], centre, native_radius, 0.18)
-    coil = _chain_walk(rng, n_solute, POLY_BOND["r0"], POLY_ANGLE["t0"], centre, coil_radius, 0.28)
+    coil = _chain_walk(rng, n_solute, POLY_BOND["r0"], POLY_ANGLE["t0"], centre, coil_radius, 0.28,
+                       max_backtracks=5000)
     coil %= L
     cls = rng.integers(0, 4, size=n_solute)
     q = rng.normal(0.0, 0.25, size=n_solute)

@@ -42,7 +42,7 @@ def test_uneven_batch_sampled_parity_and_invariance(uneven):
     seeds = [2000 + k for k in range(len(systems))]
     with B.TrialBatch(systems, p, [1] * len(systems), trial_seeds=seeds) as b:
         assert b.n_trials == len(systems)
-        b.step(20)  # two list intervals; ends on a rebuild
+        b.step(20)
         diag = B.sim_diagnostics(b.h)
         assert diag["max_list_entries"] < diag["list_capacity"]
         phi, best = b.bias_functional()
@@ -60,7 +60,7 @@ def test_uneven_batch_sampled_parity_and_invariance(uneven):
             assert cv[0] == pytest.approx(z, rel=1e-10, abs=1e-10)
         for k in (smallest, median):
             s = systems[k]
-            pos = states[k][0]
+            pos = B.sim_list_positions(b.h, k)  # the positions the current list was built from
             gpu = {tuple(x) for x in B.sim_pairlist(b.h, k).tolist()}
             ref = {tuple(x) for x in O.pairlist(s, pos.astype(np.float32), p.r_cut + p.skin).tolist()}
             assert gpu == ref, (k, s.n_atoms)

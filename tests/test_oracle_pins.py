@@ -294,6 +294,28 @@ def test_energy_conservation_without_friction_and_bias():
     assert drift < 1e-3  # kJ/mol/ps per atom
 
 
+def test_displacement_triggered_lists_give_the_cut_off_model():
+    """U of Eq. Lang is the cut-off potential: every pair closer than r_cut
+    interacts.  With lists rebuilt once an atom has moved skin/2 (minus
+    1e-5 nm), a thin buffer of 0.02 nm must give the same trajectory as a
+    0.4 nm buffer (whose lists, rebuilt every 10 steps, cover every pair that
+    can come within r_cut), up to rounding; fixed 20-step intervals with the
+    thin buffer miss pairs and do not."""
+    s, p = S.tiny_chain(0)
+    p.k_ratchet = 0.0
+    n = 300
+    thick = S.Params(**{**p.__dict__, "skin": 0.4, "nstlist": 10, "flags": 4})
+    ref = O.run(s, thick, 5, n)
+    thin = O.run(s, S.Params(**{**p.__dict__, "skin": 0.02, "nstlist": 20}), 5, n)
+    fixed = O.run(s, S.Params(**{**p.__dict__, "skin": 0.02, "nstlist": 20, "flags": 4}), 5, n)
+    L = s.box
+    dev = lambda r: np.abs((r["pos"] - ref["pos"]) - L * np.round((r["pos"] - ref["pos"]) / L)).max()
+    # the thick buffer itself: 10 steps of 2 fs move no atom 0.2 nm at 300 K
+    assert all(r["status"] == 0 for r in (ref, thin, fixed))
+    assert dev(thin) < 1e-8
+    assert dev(fixed) > 1e-6
+
+
 def test_thermostat_equipartition():
     s, p = S.tiny_chain(0)
     p.gamma, p.k_ratchet = 10.0, 0.0
