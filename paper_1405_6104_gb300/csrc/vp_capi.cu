@@ -248,7 +248,7 @@ constexpr int NO_REQUEST = -2;  // forces(): no forced list rebuild
 // nothing they read, and pair and bonded forces meet only in
 // order-independent fixed-point sums, so both orders give bit-identical states.
 void forces(sim_handle *h, FinMode mode, int request) {
-  if (request != NO_REQUEST) launch_rebuild_request(h->d, request, h->stream);
+  if (request != NO_REQUEST) launch_rebuild_request(h->d, h->c, request, h->stream);
   rebuild_cols(h);
   if (h->side && !h->timing) {
     cudaEventRecord(h->ev_fork, h->stream);
@@ -812,8 +812,15 @@ VP_API int sim_create(const sim_system *systems, int32_t n_systems, const int32_
   r |= dalloc(h, &d.energy, (size_t)total_trials * 5);
   r |= dalloc(h, &d.diag, 4);
   r |= dalloc(h, &d.cur_step, 1);
-  r |= dalloc(h, &d.rb, 3 * (size_t)total_trials);
+  r |= dalloc(h, &d.rb, 2 * (size_t)total_trials);
   r |= dalloc(h, &d.last_rb, total_trials);
+  r |= dalloc(h, &d.rb_list, total_trials);
+  r |= dalloc(h, &d.rb_cnt, 4);
+  for (const auto &T : h->tinfo) {
+    d.max_trial_slots = std::max(d.max_trial_slots, T.max_clus * CL);
+    d.max_trial_clus = std::max(d.max_trial_clus, T.max_clus);
+    d.max_trial_cols = std::max(d.max_trial_cols, T.ncol * T.ncol);
+  }
   r |= dalloc(h, &d.gdirty, d.total_clus);
   r |= dalloc(h, &h->d_argmin, 1);
   r |= dalloc(h, &h->d_count, 1);
@@ -830,7 +837,7 @@ VP_API int sim_create(const sim_system *systems, int32_t n_systems, const int32_
     return bail(fail(h, SIM_ECUDA, "cudaMemcpy kick"));
   // no rebuild requested for any step yet (a step number's low 32 bits never
   // equal this value within 2^32 steps of creation)
-  if (cudaMemset(d.rb, 0xff, 3 * sizeof(uint32_t) * (size_t)total_trials) != cudaSuccess)
+  if (cudaMemset(d.rb, 0xff, 2 * sizeof(uint32_t) * (size_t)total_trials) != cudaSuccess)
     return bail(fail(h, SIM_ECUDA, "cudaMemset rebuild requests"));
 
   // ---- native contact map, velocities, first lists and forces -------------------------

@@ -67,8 +67,11 @@ struct Dev {
   // list rebuilds: a trial's list is rebuilt in the step whose number (low
   // 32 bits) its decision entry holds
   unsigned long long *cur_step;        // number of the step being computed (or of the state held)
-  uint32_t *rb;                        // [3 n_trials]: displacement request, forced request, decision
+  uint32_t *rb;                        // [2 n_trials]: displacement request, forced request
   uint32_t *last_rb;                   // [n_trials] step of the trial's last rebuild
+  int32_t *rb_list;                    // [n_trials] the trials rebuilding in this step (any order) ...
+  uint32_t *rb_cnt;                    // [4]: ... their number, the list kernel's work counter, spare
+  int32_t max_trial_slots, max_trial_cols, max_trial_clus;  // largest of any trial
   uint32_t *gdirty;                    // [clusters] bit k < 31: entries 8k..8k+7 hold exclusions, the
                                        // cluster itself or mixed images (the pair kernels then apply the
                                        // pair masks); bit 31: some group from the 31st on does
@@ -76,6 +79,31 @@ struct Dev {
   unsigned *pair_next;                 // work counter of the persistent pair kernel
   int32_t n_sm;                        // multiprocessors of the device
 };
+
+// Which trials rebuild their lists in step n (executed by one whole block,
+// in a kernel of its own after the update kernel): a displacement or forced
+// request for this step, or the longest interval reached (fixed-interval
+// lists: steps that are multiples of nstlist); forced_only: the forced
+// requests alone (a new state between steps).  The chosen trials go to
+// rb_list.
+__device__ __forceinline__ void decide_rebuilds(const Dev &d, const SimConst &c, unsigned long long n,
+                                                bool forced_only) {
+  const uint32_t n32 = (uint32_t)n;
+  if (threadIdx.x == 0) {
+    d.rb_cnt[0] = 0u;
+    d.rb_cnt[1] = 0u;
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < d.n_trials; t += blockDim.x) {
+    bool go = d.rb[d.n_trials + t] == n32;
+    if (!forced_only && !go) {
+      if (d.rb[t] == n32) go = true;
+      else if (c.list_fixed) go = n % (unsigned long long)c.nstlist == 0ull;
+      else go = n32 - d.last_rb[t] >= (uint32_t)c.nstlist;
+    }
+    if (go) d.rb_list[atomicAdd(d.rb_cnt, 1u)] = t;
+  }
+}
 
 enum UpdateMode { UPD_DRIFT = 0, UPD_FINAL = 1 };
 // FIN_STEP: a step (Phi accumulates, the step counter advances); FIN_INIT:
@@ -85,7 +113,7 @@ enum UpdateMode { UPD_DRIFT = 0, UPD_FINAL = 1 };
 enum FinMode { FIN_STEP = 0, FIN_INIT = 1, FIN_RESTORE = 2, FIN_KEEP = 3 };
 
 // rebuild (vp_rebuild.cu)
-void launch_rebuild_request(const Dev &d, int32_t trial, cudaStream_t s);
+void launch_rebuild_request(const Dev &d, const SimConst &c, int32_t trial, cudaStream_t s);
 void launch_bin(const Dev &d, const SimConst &c, float half_skin2, int strict_skin, cudaStream_t s);
 void launch_colscan(const Dev &d, const SimConst &c, cudaStream_t s);
 void launch_colfill(const Dev &d, cudaStream_t s);

@@ -132,16 +132,7 @@ struct SimConst {
   float trig2;
 };
 
-// whether trial t rebuilds its list in step n: a displacement or forced
-// request for this step, or the longest interval reached (fixed-interval
-// lists: steps that are multiples of nstlist)
-__device__ __forceinline__ bool rebuild_due(const uint32_t *rb, const uint32_t *last_rb, int n_trials,
-                                            const SimConst &c, int t, unsigned long long n) {
-  const uint32_t n32 = (uint32_t)n;
-  if (rb[t] == n32 || rb[n_trials + t] == n32) return true;
-  if (c.list_fixed) return n % (unsigned long long)c.nstlist == 0ull;
-  return n32 - last_rb[t] >= (uint32_t)c.nstlist;
-}
+
 
 // ---------------------------------------------------------------------------
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11)

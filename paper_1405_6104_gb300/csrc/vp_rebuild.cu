@@ -2,8 +2,9 @@
 // cluster-pair Verlet list of the trials whose list is due.
 //
 // Every kernel here runs in every step and works only on the trials whose
-// list is due in that step (the decision of k_bin, kept in d.rb); the others
-// return at once.  A trial's list is due when one of its atoms has moved
+// list is due in that step: the update kernel's last block (or, for a new
+// state, k_rebuild_request) lists them in d.rb_list, and the kernels take
+// their work items (slot chunks, columns, clusters) from that list.  A trial's list is due when one of its atoms has moved
 // farther than skin/2 - 1e-5 nm from where its list was built (the update
 // kernel requests it), after nstlist steps, or on request from the host
 // (creation, a new state).  The first rule keeps every pair closer than r_cut
@@ -18,6 +19,8 @@
 // the atom pairs that satisfy the FP32 list rule and are not excluded; the
 // half list keeps j-clusters whose parent cluster index is >= the i-cluster
 // (upper triangle inside a cluster).
+#include <algorithm>
+
 #include "vp_dev.cuh"
 
 namespace vp {
@@ -26,24 +29,27 @@ namespace vp {
 // binning: wrap into the box, pick the column, count, skin check
 // ---------------------------------------------------------------------------
 // forced rebuild of one trial (trial >= 0) or of all, in the step held now
-__global__ void k_rebuild_request(Dev d, int trial) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= d.n_trials || (trial >= 0 && t != trial)) return;
-  d.rb[d.n_trials + t] = (uint32_t)*d.cur_step;
+// (one block)
+__global__ void k_rebuild_request(Dev d, SimConst c, int trial) {
+  const unsigned long long n = *d.cur_step;
+  for (int t = threadIdx.x; t < d.n_trials; t += blockDim.x)
+    if (trial < 0 || t == trial) d.rb[d.n_trials + t] = (uint32_t)n;
+  __syncthreads();
+  decide_rebuilds(d, c, n, true);
 }
 
-// the rebuild decision of trial t in the current step, taken by k_bin
-__device__ __forceinline__ bool rebuilding(const Dev &d, int t) { return d.rb[2 * d.n_trials + t] == (uint32_t)*d.cur_step; }
+// work items of the rebuilding trials: each trial cut into `per` pieces,
+// items taken in grid-stride order by whole blocks
+#define FOR_REBUILD_ITEMS(per, t, piece)                                                  \
+  for (int item_ = blockIdx.x, n_items_ = (int)d.rb_cnt[0] * (per); item_ < n_items_;     \
+       item_ += gridDim.x)                                                                 \
+    if (const int t = d.rb_list[item_ / (per)], piece = item_ % (per); true)
 
-__global__ void k_bin(Dev d, SimConst c, float half_skin2, int strict) {
-  int slot = blockIdx.x * blockDim.x + threadIdx.x;
-  if (slot >= d.total_slots) return;
-  int t = d.slot_trial[slot];
-  const unsigned long long n = *d.cur_step;
-  if (!rebuild_due(d.rb, d.last_rb, d.n_trials, c, t, n)) return;
+__device__ __forceinline__ void bin_slot(const Dev &d, const SimConst &c, float half_skin2, int strict, int t,
+                                         int local, unsigned long long n) {
   const TrialInfo T = d.tinfo[t];
-  int local = slot - T.slot0;
-  if (local == 0) d.rb[2 * d.n_trials + t] = (uint32_t)n;  // the decision the other rebuild kernels read
+  if (local >= T.max_clus * CL) return;
+  const int slot = T.slot0 + local;
   int o = d.orig[slot];
   if (local >= d.tstate[t].n_clus * CL || o < 0) { d.slot_col[slot] = -1; return; }
   float4 p = d.pos[slot];
@@ -83,14 +89,20 @@ __global__ void k_bin(Dev d, SimConst c, float half_skin2, int strict) {
   if ((threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&d.col_count[cg], __popc(peers));
 }
 
+__global__ void k_bin(Dev d, SimConst c, float half_skin2, int strict) {
+  const unsigned long long n = *d.cur_step;
+  const int per = (d.max_trial_slots + 255) / 256;
+  FOR_REBUILD_ITEMS(per, t, piece) bin_slot(d, c, half_skin2, strict, t, piece * 256 + threadIdx.x, n);
+}
+
 // ---------------------------------------------------------------------------
 // per trial: exclusive scans of column atom counts and cluster counts
 // ---------------------------------------------------------------------------
 __global__ void k_colscan(Dev d) {
   constexpr int NT = 256;
   __shared__ int s_a[NT], s_c[NT];
-  int t = blockIdx.x;
-  if (!rebuilding(d, t)) return;
+  if (blockIdx.x >= d.rb_cnt[0]) return;
+  int t = d.rb_list[blockIdx.x];
   const TrialInfo T = d.tinfo[t];
   int nc = T.ncol * T.ncol;
   int per = (nc + NT - 1) / NT;
@@ -149,14 +161,12 @@ __global__ void k_colscan(Dev d) {
 // ---------------------------------------------------------------------------
 // scatter slot indices into their column buckets (unordered)
 // ---------------------------------------------------------------------------
-__global__ void k_colfill(Dev d) {
-  int slot = blockIdx.x * blockDim.x + threadIdx.x;
-  if (slot >= d.total_slots) return;
-  int t = d.slot_trial[slot];
-  if (!rebuilding(d, t)) return;
+__device__ __forceinline__ void colfill_slot(const Dev &d, int t, int local) {
+  const TrialInfo &T = d.tinfo[t];
+  if (local >= T.max_clus * CL) return;
+  const int slot = T.slot0 + local;
   int c = d.slot_col[slot];
   if (c < 0) return;
-  const TrialInfo &T = d.tinfo[t];
   int cg = T.col0 + c;
   // one atomic per column and warp; the lanes of a column take consecutive
   // places (the order inside a bucket is irrelevant: the column sort orders it)
@@ -170,18 +180,28 @@ __global__ void k_colfill(Dev d) {
   if (p < COL_CAP && d.col_count[cg] <= COL_CAP) d.bucket[T.atom0 + d.col_start[cg] + p] = slot;
 }
 
+__global__ void k_colfill(Dev d) {
+  const int per = (d.max_trial_slots + 255) / 256;
+  FOR_REBUILD_ITEMS(per, t, piece) colfill_slot(d, t, piece * 256 + threadIdx.x);
+}
+
 // ---------------------------------------------------------------------------
 // per column: sort by (z, atom index), write the new cluster layout, update
 // slot_of, pad the last cluster and compute cluster bounding boxes
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(128) k_colsort(Dev d) {
-  __shared__ unsigned long long key[COL_CAP];
-  __shared__ int s_old[COL_CAP];
-  __shared__ float s_zlo[COL_CAP / CJ + 2];  // lower z-bound of every half
-  int cg = blockIdx.x;
-  int t = d.col_trial[cg];
-  if (!rebuilding(d, t)) return;
+struct ColsortShared {
+  unsigned long long key[COL_CAP];
+  int s_old[COL_CAP];
+  float s_zlo[COL_CAP / CJ + 2];  // lower z-bound of every half
+};
+
+__device__ __forceinline__ void colsort_column(const Dev &d, ColsortShared &sh, int t, int c) {
+  unsigned long long *key = sh.key;
+  int *s_old = sh.s_old;
+  float *s_zlo = sh.s_zlo;
   const TrialInfo T = d.tinfo[t];
+  if (c >= T.ncol * T.ncol) return;
+  const int cg = T.col0 + c;
   int n = d.col_count[cg];
   __syncthreads();
   // the count is consumed: the column starts from zero at the trial's next rebuild
@@ -266,6 +286,14 @@ __global__ void __launch_bounds__(128) k_colsort(Dev d) {
   }
 }
 
+__global__ void __launch_bounds__(128) k_colsort(Dev d) {
+  __shared__ ColsortShared sh;
+  FOR_REBUILD_ITEMS(d.max_trial_cols, t, piece) {
+    __syncthreads();  // the previous column's shared arrays are no longer read
+    colsort_column(d, sh, t, piece);
+  }
+}
+
 // ---------------------------------------------------------------------------
 // cluster-pair list
 // ---------------------------------------------------------------------------
@@ -331,20 +359,28 @@ constexpr int CAND_MAX = 1024;  // candidate 4-atom j-clusters per i-cluster (bo
 // the entry's mask, image code and exact flag; entries are written in
 // candidate order (deterministic).  Phase 3: the i-atoms' exclusions clear
 // their bits in the written entries (found by binary search).
-__global__ void __launch_bounds__(LIST_WARPS * 32, 8) k_list(Dev d, SimConst c, float rl2_bbox) {
-  __shared__ int s_cand[LIST_WARPS][CAND_MAX];
-  __shared__ int s_excl[LIST_WARPS][CL][MAX_EXCL];
-  __shared__ int s_nex[LIST_WARPS][CL];
-  __shared__ float4 s_xp[LIST_WARPS][CL / 2][2];  // i-atom pairs (2p, 2p+1): {-x, -x', -y, -y'} {-z, -z', 0, 0}
+struct ListShared {
+  int s_cand[LIST_WARPS][CAND_MAX];
+  int s_excl[LIST_WARPS][CL][MAX_EXCL];
+  int s_nex[LIST_WARPS][CL];
+  float4 s_xp[LIST_WARPS][CL / 2][2];  // i-atom pairs (2p, 2p+1): {-x, -x', -y, -y'} {-z, -z', 0, 0}
+  unsigned s_dirty[LIST_WARPS];        // groups of 8 entries that need the pair masks
+  unsigned s_mask[LIST_WARPS][512];    // masks of the entries (their first words overwrite s_cand)
+};
+
+__device__ __forceinline__ void list_cluster(const Dev &d, const SimConst &c, float rl2_bbox, ListShared &sh, int t,
+                                             int Il) {
+  auto &s_cand = sh.s_cand;
+  auto &s_excl = sh.s_excl;
+  auto &s_nex = sh.s_nex;
+  auto &s_xp = sh.s_xp;
+  auto &s_dirty = sh.s_dirty;
+  auto &s_mask = sh.s_mask;
   const int wib = threadIdx.x >> 5;
-  __shared__ unsigned s_dirty[LIST_WARPS];  // groups of 8 entries that need the pair masks
-  const int I = blockIdx.x * LIST_WARPS + wib;
   const int lane = threadIdx.x & 31;
-  if (I >= d.total_clus) return;
-  const int t = d.clus_trial[I];
-  if (!rebuilding(d, t)) return;
   const TrialInfo T = d.tinfo[t];
-  const int Il = I - T.clus0;
+  if (Il >= T.max_clus) return;
+  const int I = T.clus0 + Il;
   if (Il >= d.tstate[t].n_clus) {
     if (lane == 0) d.list_n[I] = 0;
     return;
@@ -472,13 +508,18 @@ __global__ void __launch_bounds__(LIST_WARPS * 32, 8) k_list(Dev d, SimConst c, 
   }
   if (lane < CL) {
     const int o = d.orig[I * CL + lane];
-    const int sa = T.sysatom0 + (o < 0 ? 0 : o);
-    const int n = o < 0 ? 0 : d.excl_n[sa];
-    for (int k = 0; k < n; ++k) s_excl[wib][lane][k] = d.excl[(size_t)sa * MAX_EXCL + k];
-    s_nex[wib][lane] = n;
+    s_nex[wib][lane] = o < 0 ? 0 : d.excl_n[T.sysatom0 + o];
   }
   if (lane == 0) s_dirty[wib] = c.list_fixed ? ~0u : 0u;  // fixed-interval lists: masks everywhere
   __syncwarp();
+  // the slots of the i-atoms' excluded partners, all loads of the warp in flight together
+  for (int k = lane; k < CL * MAX_EXCL; k += 32) {
+    const int a = k / MAX_EXCL, q = k - a * MAX_EXCL;
+    if (q < s_nex[wib][a]) {
+      const int o = d.orig[I * CL + a];
+      s_excl[wib][a][q] = d.slot_of[T.atom0 + d.excl[(size_t)(T.sysatom0 + o) * MAX_EXCL + q]];
+    }
+  }
   // ---- phase 2: one candidate 4-atom j-cluster per lane ----
   // Image counts: q = rint(fl(d * invL)) is monotone in d = fl(xj - xi), so
   // when the two bounding-box extremes of d give the same q in a dimension,
@@ -545,8 +586,12 @@ __global__ void __launch_bounds__(LIST_WARPS * 32, 8) k_list(Dev d, SimConst c, 
     }
     const unsigned bal = __ballot_sync(0xffffffffu, mask != 0u);
     const int pos = cnt + __popc(bal & ((1u << lane) - 1u));
+    __syncwarp();  // every lane has read its candidate before entries overwrite them
     if (mask != 0u && pos < c.list_cap) {
-      seg[pos] = make_uint2(w0, mask);
+      // entries are kept in shared memory until the exclusions are cleared:
+      // the first word over the consumed candidates, the mask beside
+      cand[pos] = (int)w0;
+      s_mask[wib][pos] = mask;
       // the cluster with itself (pairs below the diagonal masked) and entries
       // whose pairs take images one by one need the masks in the pair kernel
       if ((int)((w0 & J_MASK) >> 1) == I || (w0 & E_EXACT)) atomicOr(&s_dirty[wib], 1u << min(pos >> 3, 31));
@@ -560,25 +605,25 @@ __global__ void __launch_bounds__(LIST_WARPS * 32, 8) k_list(Dev d, SimConst c, 
   // (entries ascend in j-cluster index; a pair inside the i-cluster belongs
   // to the entry with the higher slot as j)
   __syncwarp();
-  if (lane < CL) {
-    const int si = I * CL + lane;
-    const int ne = s_nex[wib][lane];
-    for (int q = 0; q < ne; ++q) {
-      const int sj = d.slot_of[T.atom0 + s_excl[wib][lane][q]];
-      if ((sj >> 3) < I || ((sj >> 3) == I && sj <= si)) continue;  // listed from the other side, or not at all
-      const unsigned j4 = (unsigned)(sj >> 2);
-      int lo_e = 0, hi_e = n_ent;  // first entry with j-cluster >= j4
-      while (lo_e < hi_e) {
-        const int mid = (lo_e + hi_e) >> 1;
-        if ((seg[mid].x & J_MASK) < j4) lo_e = mid + 1; else hi_e = mid;
-      }
-      if (lo_e < n_ent && (seg[lo_e].x & J_MASK) == j4) {
-        atomicAnd(&seg[lo_e].y, ~(1u << (lane * CJ + (sj & 3))));
-        atomicOr(&s_dirty[wib], 1u << min(lo_e >> 3, 31));
-      }
+  for (int k = lane; k < CL * MAX_EXCL; k += 32) {
+    const int a = k / MAX_EXCL, q = k - a * MAX_EXCL;
+    if (q >= s_nex[wib][a]) continue;
+    const int si = I * CL + a;
+    const int sj = s_excl[wib][a][q];
+    if ((sj >> 3) < I || ((sj >> 3) == I && sj <= si)) continue;  // listed from the other side, or not at all
+    const unsigned j4 = (unsigned)(sj >> 2);
+    int lo_e = 0, hi_e = n_ent;  // first entry with j-cluster >= j4
+    while (lo_e < hi_e) {
+      const int mid = (lo_e + hi_e) >> 1;
+      if (((unsigned)cand[mid] & J_MASK) < j4) lo_e = mid + 1; else hi_e = mid;
+    }
+    if (lo_e < n_ent && ((unsigned)cand[lo_e] & J_MASK) == j4) {
+      atomicAnd(&s_mask[wib][lo_e], ~(1u << (a * CJ + (sj & 3))));
+      atomicOr(&s_dirty[wib], 1u << min(lo_e >> 3, 31));
     }
   }
   __syncwarp();
+  for (int e = lane; e < n_ent; e += 32) seg[e] = make_uint2((unsigned)cand[e], s_mask[wib][e]);
   if (lane == 0) {
     d.gdirty[I] = s_dirty[wib];
     d.list_n[I] = n_ent;
@@ -586,17 +631,39 @@ __global__ void __launch_bounds__(LIST_WARPS * 32, 8) k_list(Dev d, SimConst c, 
   }
 }
 
+// one warp per cluster of a rebuilding trial, clusters handed out by a
+// counter (their lists differ in length)
+__global__ void __launch_bounds__(LIST_WARPS * 32, 8) k_list(Dev d, SimConst c, float rl2_bbox) {
+  __shared__ ListShared sh;
+  const int lane = threadIdx.x & 31;
+  const int n_items = (int)d.rb_cnt[0] * d.max_trial_clus;
+  for (;;) {
+    __syncwarp();  // the warp's shared arrays of its previous cluster are no longer read
+    unsigned got = 0u;
+    if (lane == 0) got = atomicAdd(d.rb_cnt + 1, 1u);
+    const int item = (int)__shfl_sync(0xffffffffu, got, 0);
+    if (item >= n_items) return;
+    list_cluster(d, c, rl2_bbox, sh, d.rb_list[item / d.max_trial_clus], item % d.max_trial_clus);
+  }
+}
+
 // the re-sorted layout replaces the current one (slots of rebuilding trials),
 // and its positions are the ones the new list is built from
-__global__ void k_copyback(Dev d) {
-  const int slot = blockIdx.x * blockDim.x + threadIdx.x;
-  if (slot >= d.total_slots || !rebuilding(d, d.slot_trial[slot])) return;
+__device__ __forceinline__ void copyback_slot(const Dev &d, int t, int local) {
+  const TrialInfo &T = d.tinfo[t];
+  if (local >= T.max_clus * CL) return;
+  const int slot = T.slot0 + local;
   const float4 p = d.pos_b[slot];
   d.pos[slot] = p;
   d.ref_slot[slot] = p;
   d.vel[slot] = d.vel_b[slot];
   d.orig[slot] = d.orig_b[slot];
   d.type[slot] = d.type_b[slot];
+}
+
+__global__ void k_copyback(Dev d) {
+  const int per = (d.max_trial_slots + 255) / 256;
+  FOR_REBUILD_ITEMS(per, t, piece) copyback_slot(d, t, piece * 256 + threadIdx.x);
 }
 
 // positions the current list of one trial was built from, caller order
@@ -612,11 +679,19 @@ __global__ void k_list_positions(Dev d, int trial, double *out, int n) {
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
-void launch_rebuild_request(const Dev &d, int32_t trial, cudaStream_t s) {
-  k_rebuild_request<<<(d.n_trials + 255) / 256, 256, 0, s>>>(d, trial);
+// The grids are fixed (they are captured in graphs) and sized from the SM
+// count; their blocks and warps walk the work items of the trials that
+// rebuild in the step, so a step in which few trials rebuild costs little.
+// (no more blocks than items in the largest possible step: all trials rebuilding)
+static unsigned rebuild_grid(const Dev &d, int per_sm, long long per_trial) {
+  return (unsigned)std::max(1LL, std::min((long long)d.n_sm * per_sm, per_trial * d.n_trials));
+}
+
+void launch_rebuild_request(const Dev &d, const SimConst &c, int32_t trial, cudaStream_t s) {
+  k_rebuild_request<<<1, 1024, 0, s>>>(d, c, trial);
 }
 void launch_bin(const Dev &d, const SimConst &c, float half_skin2, int strict_skin, cudaStream_t s) {
-  k_bin<<<(d.total_slots + 255) / 256, 256, 0, s>>>(d, c, half_skin2, strict_skin);
+  k_bin<<<rebuild_grid(d, 4, (d.max_trial_slots + 255) / 256), 256, 0, s>>>(d, c, half_skin2, strict_skin);
 }
 void launch_colscan(const Dev &d, const SimConst &c, cudaStream_t s) {
   (void)c;
@@ -626,14 +701,15 @@ void launch_list_positions(const Dev &d, int32_t trial, double *out, int32_t n, 
   if (n > 0) k_list_positions<<<(n + 255) / 256, 256, 0, s>>>(d, trial, out, n);
 }
 void launch_colfill(const Dev &d, cudaStream_t s) {
-  k_colfill<<<(d.total_slots + 255) / 256, 256, 0, s>>>(d);
+  k_colfill<<<rebuild_grid(d, 4, (d.max_trial_slots + 255) / 256), 256, 0, s>>>(d);
 }
 void launch_colsort(const Dev &d, cudaStream_t s) {
-  k_colsort<<<d.total_cols, 128, 0, s>>>(d);  // columns hold about 100 atoms: 128 threads keep every thread busy in the sort
-  k_copyback<<<(d.total_slots + 255) / 256, 256, 0, s>>>(d);
+  // columns hold about 100 atoms: 128 threads keep every thread busy in the sort
+  k_colsort<<<rebuild_grid(d, 8, d.max_trial_cols), 128, 0, s>>>(d);
+  k_copyback<<<rebuild_grid(d, 4, (d.max_trial_slots + 255) / 256), 256, 0, s>>>(d);
 }
 void launch_list(const Dev &d, const SimConst &c, float rl2_bbox, cudaStream_t s) {
-  k_list<<<(unsigned)((d.total_clus + LIST_WARPS - 1) / LIST_WARPS), LIST_WARPS * 32, 0, s>>>(d, c, rl2_bbox);
+  k_list<<<rebuild_grid(d, 8, (d.max_trial_clus + LIST_WARPS - 1) / LIST_WARPS), LIST_WARPS * 32, 0, s>>>(d, c, rl2_bbox);
 }
 
 }  // namespace vp

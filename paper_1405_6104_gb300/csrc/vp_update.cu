@@ -11,13 +11,11 @@
 
 namespace vp {
 
-// six blocks per SM (40 registers: with 32 the list buffer's reference
-// position, one more early load, spills): the kernel waits on memory round
-// trips and needs every resident warp it can get
+// One slot; returns whether it requested a list rebuild of its trial.
 template <int MODE>
-__global__ void __launch_bounds__(256, 6) k_update(Dev d, SimConst c) {
-  const int slot = blockIdx.x * blockDim.x + threadIdx.x;
-  if (slot >= d.total_slots) return;
+__device__ __forceinline__ bool update_slot(const Dev &d, const SimConst &c, int slot) {
+  if (slot >= d.total_slots) return false;
+  bool req = false;
   if (MODE == UPD_FINAL && slot == 0) *d.kick = 0.5f;
   // every load that does not depend on another is issued before any store
   // (the stores could alias them as far as the compiler knows), so a thread
@@ -30,8 +28,8 @@ __global__ void __launch_bounds__(256, 6) k_update(Dev d, SimConst c) {
   const long long fxi = d.fx[slot], fyi = d.fy[slot], fzi = d.fz[slot];
   const float kick = MODE == UPD_DRIFT ? *d.kick : 0.5f;
   const unsigned long long step = MODE == UPD_DRIFT ? (unsigned long long)(*d.step) + 1ull : 0ull;
-  if (MODE == UPD_DRIFT && slot == 0) *d.cur_step = step;  // the step the rebuild kernels decide for
-  if (o < 0) return;
+  if (MODE == UPD_DRIFT && slot == 0) *d.cur_step = step;  // the step the rebuild kernels work on
+  if (o < 0) return false;
   const int n_cv = __ldg(&d.tinfo[t].n_cv), cv0 = __ldg(&d.tinfo[t].cv0);
   const uint32_t key0 = __ldg(&d.tinfo[t].key0), key1 = __ldg(&d.tinfo[t].key1);
   const unsigned long long nstep = step + (unsigned long long)__ldg(&d.tinfo[t].noise_off);
@@ -82,10 +80,28 @@ __global__ void __launch_bounds__(256, 6) k_update(Dev d, SimConst c) {
     // is the displacement itself)
     if (!c.list_fixed) {
       const float ddx = p.x - ref.x, ddy = p.y - ref.y, ddz = p.z - ref.z;
-      if (ddx * ddx + ddy * ddy + ddz * ddz > c.trig2) d.rb[t] = (uint32_t)step;
+      if (ddx * ddx + ddy * ddy + ddz * ddz > c.trig2) {
+        d.rb[t] = (uint32_t)step;
+        req = true;
+      }
     }
   }
   d.vel[slot] = v;
+  return req;
+}
+
+
+// Six blocks per SM (40 registers: with 32 the list buffer's reference
+// position, one more early load, spills): the kernel waits on memory round
+// trips and needs every resident warp it can get.
+template <int MODE>
+__global__ void __launch_bounds__(256, 6) k_update(Dev d, SimConst c) {
+  update_slot<MODE>(d, c, blockIdx.x * blockDim.x + threadIdx.x);
+}
+
+// which trials rebuild their lists in this step (one block, after the update)
+__global__ void __launch_bounds__(1024) k_decide(Dev d, SimConst c) {
+  decide_rebuilds(d, c, *d.cur_step, false);
 }
 
 // Maxwell-Boltzmann velocities (Philox stream 1, step 0) with the centre of
@@ -257,8 +273,12 @@ void launch_philox_normals(uint64_t seed, unsigned long long step, uint32_t stre
 
 void launch_update(const Dev &d, const SimConst &c, UpdateMode mode, cudaStream_t s) {
   unsigned blocks = (unsigned)((d.total_slots + 255) / 256);
-  if (mode == UPD_DRIFT) k_update<UPD_DRIFT><<<blocks, 256, 0, s>>>(d, c);
-  else k_update<UPD_FINAL><<<blocks, 256, 0, s>>>(d, c);
+  if (mode == UPD_DRIFT) {
+    k_update<UPD_DRIFT><<<blocks, 256, 0, s>>>(d, c);
+    k_decide<<<1, 1024, 0, s>>>(d, c);
+  } else {
+    k_update<UPD_FINAL><<<blocks, 256, 0, s>>>(d, c);
+  }
 }
 void launch_init_vel(const Dev &d, float kT, const int32_t *need, cudaStream_t s) {
   k_init_vel<<<d.n_trials, 256, 0, s>>>(d, kT, need);
