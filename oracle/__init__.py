@@ -358,7 +358,9 @@ def refine_frames(s, p, frames, n_iter, step):
     """Descent on Phi over the inner frames of a path, end frames fixed, with
     Armijo backtracking (first trial step 2x the last accepted one, halved
     until Phi drops by 1e-4 eta |g|^2): FP64 restatement of the refinement.
-    Returns (frames, Phi history [n_iter + 1], accepted iterations)."""
+    A trial point's moved coordinates are rounded to FP32, the precision the
+    path's frames are held in, so that the path returned is exactly the one
+    scored.  Returns (frames, Phi history [n_iter + 1], accepted iterations)."""
     X = np.array(frames, dtype=np.float64)[:, : s.n_cv, :].copy()
     phi, G = phi_frames_grad(s, p, X)
     G[0] = 0.0
@@ -371,7 +373,8 @@ def refine_frames(s, p, frames, n_iter, step):
         for _ in range(40):
             if gg <= 0.0:
                 break
-            Y = X - eta * G
+            Y = X.copy()
+            Y[1:-1] = (X[1:-1] - eta * G[1:-1]).astype(np.float32).astype(np.float64)
             phi_y = phi_frames(s, p, Y)[0]
             if phi_y <= phi - 1e-4 * eta * gg:
                 X, phi, ok = Y, phi_y, True

@@ -49,3 +49,30 @@ def test_refinement_matches_the_oracle(name):
     # the refined path re-scored by the oracle
     assert O.phi_frames(s, p, X)[0] == pytest.approx(hist[-1], rel=1e-6)
     assert hist[-1] == pytest.approx(hist_o[-1], rel=0.1)
+
+
+@pytest.mark.parametrize("name", ["tiny", "small"])
+def test_refinement_iterations_on_shared_paths(name):
+    """Iteration by iteration from the same path (the GPU's path after the
+    previous iteration, on both sides): each iteration's Phi and moved frames
+    agree with the oracle's restatement, the Phi history to 1e-5 relative
+    (the GPU gradient carries a 1e-4 relative error, which moves the trial
+    point by that fraction of one step)."""
+    s, p = S.tiny_chain(0) if name == "tiny" else S.small_solvated()
+    b, X = gpu_path(s, p, 91, 40)
+    try:
+        step = 1e-3
+        for it in range(8):
+            Xg, hg, ag = B.phi_frames_refine(b.h, 0, X, 1, step)
+            Xo, ho, ao = O.refine_frames(s, p, X, 1, step)
+            assert hg[0] == pytest.approx(ho[0], rel=1e-6), it
+            assert ag == ao, it
+            if not ag:
+                break
+            assert hg[1] == pytest.approx(ho[1], rel=1e-5), it
+            # the step (eta g) agrees to the gradient's 1e-4; then one FP32 rounding
+            assert np.abs(Xg - Xo).max() <= 1e-3 * np.abs(Xo - X).max() + 5e-7, it
+            X = Xg
+        assert it >= 3
+    finally:
+        b.close()

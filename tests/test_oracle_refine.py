@@ -44,3 +44,14 @@ def test_monotone_path_has_nothing_to_refine():
     Fm = F[order]
     X, hist, acc = O.refine_frames(s, p, Fm, 5, 1e-3)
     assert hist[0] == 0.0 and acc == 0 and np.array_equal(X, Fm)
+
+
+def test_refined_frames_are_fp32_values():
+    """The moved coordinates are FP32 values (the precision of the frames the
+    path is recorded in), the end frames the input's."""
+    s, p, F = _path()
+    F = F.astype(np.float32).astype(np.float64)
+    X, hist, acc = O.refine_frames(s, p, F, 6, 1e-3)
+    assert acc > 0
+    assert np.array_equal(X.astype(np.float32).astype(np.float64), X)
+    assert not np.array_equal(X[1:-1], F[1:-1])
