@@ -163,6 +163,26 @@ int sim_set_state(sim_handle *h, int32_t trial, const double *pos, const double 
  * restored there with sim_set_state continue bit-identically. */
 int sim_rebuild(sim_handle *h);
 
+/* The potential U(X, Y) of Eq. Lang (Lennard-Jones + reaction field + bonds
+ * + angles, no bias) and its forces -grad U for one configuration per trial,
+ * entirely on the device: no host copy, no synchronisation of the host.
+ *   d_pos: DEVICE array, every trial's positions [n_atoms][3] (nm, FP64,
+ *     caller order), trials concatenated in trial order; the trials' positions
+ *     are replaced by them (stored as FP32; velocities and the functional's
+ *     bookkeeping are left as they are: call sim_set_state before stepping
+ *     such a trial);
+ *   d_energy: DEVICE array [n_trials] (FP64, kJ/mol) or NULL; NaN for every
+ *     trial when a device error flag was raised in the evaluation (a list
+ *     overflow, a non-finite coordinate);
+ *   d_forces: DEVICE array shaped like d_pos (kJ/mol/nm) or NULL;
+ *   cuda_stream: the caller's stream; the work is ordered after the work
+ *     queued on it before the call, and work queued on it after the call
+ *     waits for the results.
+ * A trial's list is rebuilt only when one of its atoms lies farther than
+ * skin/2 - 1e-5 nm from where the list was built (so repeated evaluations near
+ * one configuration reuse it).  SIM_EINVAL without d_pos or any output. */
+int sim_potential_device(sim_handle *h, const double *d_pos, double *d_energy, double *d_forces, void *cuda_stream);
+
 /* Steps taken since creation (the Philox counter of the next step is this + 1). */
 int64_t sim_step_count(const sim_handle *h);
 /* Sets the step counter (resume from a checkpoint; with SIM_FIXED_INTERVAL

@@ -96,6 +96,7 @@ _SIGS = {
     "sim_diagnostics": ([C.c_void_p, C.c_void_p], C.c_int),
     "sim_list_positions": ([C.c_void_p, C.c_int32, C.c_void_p], C.c_int),
     "sim_rebuild": ([C.c_void_p], C.c_int),
+    "sim_potential_device": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
     "sim_autotune": ([C.c_void_p, C.c_int32, C.c_char_p, C.c_void_p], C.c_int),
     "sim_set_timing": ([C.c_void_p, C.c_int32], C.c_int),
     "sim_kernel_times": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32], C.c_int),
@@ -351,6 +352,13 @@ def sim_list_positions(h, trial: int):
     out = np.zeros((n, 3))
     _check(h, load().sim_list_positions(h, int(trial), out.ctypes.data))
     return out
+
+
+def sim_potential_device(h, d_pos: int, d_energy: int, d_forces: int, cuda_stream: int = 0):
+    """U and -grad U of one configuration per trial, device pointers in and
+    out (e.g. ``tensor.data_ptr()``), ordered on the given stream."""
+    _check(h, load().sim_potential_device(h, C.c_void_p(d_pos or None), C.c_void_p(d_energy or None),
+                                          C.c_void_p(d_forces or None), C.c_void_p(cuda_stream or None)))
 
 
 def sim_rebuild(h):

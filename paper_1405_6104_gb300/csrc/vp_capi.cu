@@ -34,7 +34,7 @@ struct sim_handle {
   int device = 0;
   cudaStream_t stream = nullptr;
   cudaStream_t caller = nullptr;
-  cudaEvent_t entry_ev = nullptr;
+  cudaEvent_t entry_ev = nullptr, exit_ev = nullptr;
   // second stream of the captured chunk: the reaction coordinate (CV and its
   // finaliser) reads only positions, so it runs beside the list build and the
   // pair forces, joined before the next update
@@ -397,6 +397,7 @@ VP_API int sim_create(const sim_system *systems, int32_t n_systems, const int32_
   if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess)
     return bail(fail(h, SIM_ECUDA, "cudaStreamCreate failed"));
   cudaEventCreateWithFlags(&h->entry_ev, cudaEventDisableTiming);
+  cudaEventCreateWithFlags(&h->exit_ev, cudaEventDisableTiming);
   if (cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) != cudaSuccess)
@@ -1043,6 +1044,38 @@ VP_API int sim_rebuild(sim_handle *h) {
   return check_flags(h);
 }
 
+VP_API int sim_potential_device(sim_handle *h, const double *d_pos, double *d_energy, double *d_forces,
+                                void *cuda_stream) {
+  if (!h) return SIM_EINVAL;
+  if (!d_pos || (!d_energy && !d_forces)) return fail(h, SIM_EINVAL, "d_pos and an output are required");
+  CK(cudaSetDevice(h->device));
+  cudaStream_t cs = (cudaStream_t)cuda_stream, s = h->stream;
+  CK(cudaEventRecord(h->entry_ev, cs));
+  CK(cudaStreamWaitEvent(s, h->entry_ev, 0));
+  const Dev &d = h->d;
+  int n = 0;
+  for (const auto &T : h->tinfo) n += T.n_atoms;
+  // requests of earlier calls at this step number must not count again
+  CK(cudaMemsetAsync(d.rb, 0xff, 2 * sizeof(uint32_t) * (size_t)h->n_trials, s));
+  CK(cudaMemsetAsync(d.err, 0, sizeof(int), s));
+  CK(cudaMemsetAsync(d.fx, 0, sizeof(long long) * d.total_slots, s));
+  CK(cudaMemsetAsync(d.fy, 0, sizeof(long long) * d.total_slots, s));
+  CK(cudaMemsetAsync(d.fz, 0, sizeof(long long) * d.total_slots, s));
+  CK(cudaMemsetAsync(d.energy, 0, sizeof(long long) * 5 * (size_t)h->n_trials, s));
+  launch_scatter_positions(d, h->c, d_pos, n, s);
+  launch_decide(d, h->c, s);
+  rebuild_cols(h);
+  rebuild_list(h);
+  launch_pair(d, h->c, false, -1, s, h->pair_variant);
+  launch_bonded(d, s);
+  launch_pair(d, h->c, true, -1, s);
+  launch_potential_out(d, d_energy, d_forces, n, s);
+  CK(cudaGetLastError());
+  CK(cudaEventRecord(h->exit_ev, s));
+  CK(cudaStreamWaitEvent(cs, h->exit_ev, 0));
+  return SIM_OK;
+}
+
 VP_API int sim_list_positions(sim_handle *h, int32_t trial, double *pos) {
   int r = enter(h);
   if (r) return r;
@@ -1614,6 +1647,7 @@ VP_API void sim_destroy(sim_handle *h) {
   for (auto &t : h->timers)
     for (auto &pr : t.ev) { cudaEventDestroy(pr.first); cudaEventDestroy(pr.second); }
   if (h->entry_ev) cudaEventDestroy(h->entry_ev);
+  if (h->exit_ev) cudaEventDestroy(h->exit_ev);
   if (h->ev_fork) cudaEventDestroy(h->ev_fork);
   if (h->ev_join) cudaEventDestroy(h->ev_join);
   if (h->side) cudaStreamDestroy(h->side);

@@ -140,6 +140,9 @@ void launch_gather_state(const Dev &d, int32_t trial, double *pos, double *vel, 
 void launch_check_finite(const double *x, size_t n, int *flag, cudaStream_t s);
 void launch_forces_out(const Dev &d, const SimConst &c, int32_t trial, double *out, int32_t n, cudaStream_t s);
 void launch_kinetic(const Dev &d, int32_t trial, cudaStream_t s);
+void launch_scatter_positions(const Dev &d, const SimConst &c, const double *pos, int32_t n, cudaStream_t s);
+void launch_potential_out(const Dev &d, double *energy, double *forces, int32_t n, cudaStream_t s);
+void launch_decide(const Dev &d, const SimConst &c, cudaStream_t s);
 void launch_extract_pairs(const Dev &d, int32_t list_cap, int32_t trial, int32_t n_clus, int32_t *pairs,
                           long long cap, unsigned long long *count, cudaStream_t s);
 void launch_philox_normals(uint64_t seed, unsigned long long step, uint32_t stream, int n, uint32_t *raw,

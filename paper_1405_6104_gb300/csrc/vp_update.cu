@@ -199,6 +199,49 @@ __global__ void k_forces_out(Dev d, SimConst c, int trial, double *out, int n) {
   out[3 * o] = F[0]; out[3 * o + 1] = F[1]; out[3 * o + 2] = F[2];
 }
 
+// Positions of every trial from a device array (trials concatenated, caller
+// order, FP64; velocities untouched).  An atom farther than the list buffer
+// allows from where its trial's list was built requests a rebuild of that
+// list in the current step.
+__global__ void k_scatter_positions(Dev d, SimConst c, const double *pos, int n) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  int lo = 0, hi = d.n_trials - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (d.tinfo[mid].atom0 <= k) lo = mid; else hi = mid - 1;
+  }
+  const int t = lo;
+  const int s = d.slot_of[k];
+  float4 p = d.pos[s];
+  p.x = (float)pos[3 * (size_t)k];
+  p.y = (float)pos[3 * (size_t)k + 1];
+  p.z = (float)pos[3 * (size_t)k + 2];
+  d.pos[s] = p;
+  const float4 r = d.ref_slot[s];
+  const float dx = p.x - r.x, dy = p.y - r.y, dz = p.z - r.z;
+  if (c.list_fixed || !(dx * dx + dy * dy + dz * dz <= c.trig2)) d.rb[t] = (uint32_t)*d.cur_step;
+}
+
+// potential energy (LJ + RF + bonds + angles) and -grad U of every trial into
+// device arrays: energy[t], forces [trials concatenated][3] (FP64)
+// (NaN energies when a device error flag is up: a list overflow or a
+// non-finite state in the evaluation)
+__global__ void k_potential_out(Dev d, double *energy, double *forces, int n) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < d.n_trials && energy) {
+    const long long *e = d.energy + (size_t)k * 5;
+    energy[k] = *d.err ? __longlong_as_double(0x7ff8000000000000LL)
+                       : ((double)e[0] + (double)e[1] + (double)e[2] + (double)e[3]) / E_SCALE;
+  }
+  if (k >= n || !forces) return;
+  const int s = d.slot_of[k];
+  const double sc = 2.3283064365386963e-10;
+  forces[3 * (size_t)k] = (double)d.fx[s] * sc;
+  forces[3 * (size_t)k + 1] = (double)d.fy[s] * sc;
+  forces[3 * (size_t)k + 2] = (double)d.fz[s] * sc;
+}
+
 __global__ void k_kinetic(Dev d, int trial) {
   __shared__ double red[256];
   const TrialInfo T = d.tinfo[trial];
@@ -297,6 +340,14 @@ void launch_forces_out(const Dev &d, const SimConst &c, int32_t trial, double *o
   if (n > 0) k_forces_out<<<(n + 255) / 256, 256, 0, s>>>(d, c, trial, out, n);
 }
 void launch_kinetic(const Dev &d, int32_t trial, cudaStream_t s) { k_kinetic<<<1, 256, 0, s>>>(d, trial); }
+void launch_scatter_positions(const Dev &d, const SimConst &c, const double *pos, int32_t n, cudaStream_t s) {
+  if (n > 0) k_scatter_positions<<<(n + 255) / 256, 256, 0, s>>>(d, c, pos, n);
+}
+void launch_potential_out(const Dev &d, double *energy, double *forces, int32_t n, cudaStream_t s) {
+  const int m = n > d.n_trials ? n : d.n_trials;
+  if (m > 0) k_potential_out<<<(m + 255) / 256, 256, 0, s>>>(d, energy, forces, n);
+}
+void launch_decide(const Dev &d, const SimConst &c, cudaStream_t s) { k_decide<<<1, 1024, 0, s>>>(d, c); }
 void launch_extract_pairs(const Dev &d, int32_t list_cap, int32_t trial, int32_t n_clus, int32_t *pairs,
                           long long cap, unsigned long long *count, cudaStream_t s) {
   if (n_clus > 0) k_extract_pairs<<<(n_clus + 3) / 4, 128, 0, s>>>(d, list_cap, trial, pairs, cap, count);

@@ -5,7 +5,8 @@ and exchanges one double per trial at the end (no collective on the data
 path).
 
 ``shard_trials`` assigns global trial indices to ranks (contiguous blocks,
-balanced to within one trial); ``global_selection`` gathers (Phi, trial) of
+balanced to within one trial); ``shard_by_cost`` balances trials of uneven
+cost (atoms x steps) instead; ``global_selection`` gathers (Phi, trial) of
 every rank on the host and returns the global argmin, ties going to the
 lowest trial index as in ``bias_functional``.  Both run on CPU; the process
 group may use gloo or NCCL (CPU tensors then travel through gloo only)."""
@@ -22,6 +23,26 @@ def shard_trials(n_trials: int, world: int, rank: int) -> np.ndarray:
     lo = rank * base + min(rank, extra)
     hi = lo + base + (1 if rank < extra else 0)
     return np.arange(lo, hi, dtype=np.int64)
+
+
+def shard_by_cost(costs, world: int, rank: int) -> np.ndarray:
+    """Global trial indices of `rank` when trial k costs costs[k] (e.g. its
+    atoms x steps): trials in decreasing cost, ties by index, each to the
+    rank with the least cost so far (ties to the lower rank).  Every rank's
+    total is within the largest single cost of every other rank's; the
+    indices come back ascending.  Deterministic: every rank computes the
+    same assignment."""
+    c = np.asarray(costs, np.float64)
+    if world < 1 or not 0 <= rank < world or c.ndim != 1 or np.any(c < 0):
+        raise ValueError("bad shard arguments")
+    order = sorted(range(len(c)), key=lambda k: (-c[k], k))
+    load = np.zeros(world)
+    owner = np.empty(len(c), np.int64)
+    for k in order:
+        r = int(np.argmin(load))  # the first of equal loads
+        owner[k] = r
+        load[r] += c[k]
+    return np.nonzero(owner == rank)[0].astype(np.int64)
 
 
 def global_selection(phi_local, trials_local, group=None, z_ok_local=None):
