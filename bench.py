@@ -644,17 +644,192 @@ def run_similarity(args):
     return 0
 
 
+def equilibrate_batch(B, S, systems, p, steps: int, gamma: float = 20.0):
+    """Relaxes every system of a batch together (strong friction, no bias);
+    returns copies of the systems with the relaxed FP32 positions."""
+    pe = S.Params(**{**p.__dict__, "gamma": gamma, "k_ratchet": 0.0})
+    out = []
+    with B.TrialBatch(systems, pe, [1] * len(systems), trial_seeds=[7 + k for k in range(len(systems))]) as b:
+        b.step(steps)
+        for k, s in enumerate(systems):
+            pos, _, _ = b.get_state(k)
+            c = s.copy()
+            c.pos = pos.astype(np.float32).astype(np.float64)
+            c.vel = None
+            out.append(c)
+    return out
+
+
+def _timed_batch(B, batch, n_calls: int, nst: int, stream):
+    """CUDA-event milliseconds of n_calls calls of nst steps on the batch's stream."""
+    import torch
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(n_calls):
+        batch.step(nst)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    return ev0.elapsed_time(ev1)
+
+
+def run_uneven(args):
+    """BASELINE configuration of the uneven batch: 32 systems of 5 000 to
+    60 000 atoms (solutes of 200 to 2000 atoms, boxes at 33 water-equivalents
+    per nm^3), one trial each, 5 000 MD steps (500 bench steps of 10) after a
+    relaxation; launch shapes from the autotuner, chosen per size class."""
+    import torch
+    rank, world, local = rank_info()
+    torch.cuda.set_device(local)
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1405_6104_gb300 import binding as B
+    from paper_1405_6104_gb300 import systems as S
+    steps = args.steps if args.steps is not None else 500
+    systems, p = S.uneven_32(2)
+    if args.prep_steps > 0:
+        systems = equilibrate_batch(B, S, systems, p, min(args.prep_steps, 1000))
+    atoms = int(sum(s.n_atoms for s in systems))
+    nst = p.nstlist
+    seeds = [2000 + k for k in range(len(systems))]
+    with B.TrialBatch(systems, p, [1] * len(systems), trial_seeds=seeds) as b:
+        tuned = B.sim_autotune(b.h, 5, None)
+        classes = B.sim_tune_classes(b.h)
+        stream = torch.cuda.ExternalStream(b.stream)
+        clocks = ClockSampler(local) if rank == 0 else None
+        B.sim_set_timing(b.h, 2)
+        for _ in range(args.warmup):
+            b.step(nst)
+        torch.cuda.synchronize()
+        B.sim_kernel_times(b.h)
+        diag0 = B.sim_diagnostics(b.h)
+        t_begin = time.time()
+        ms = _timed_batch(B, b, steps, nst, stream)
+        t_end = time.time()
+        diag1 = B.sim_diagnostics(b.h)
+        pair_ms, pair_n = B.sim_kernel_times(b.h).get("pair_in_graph", (float("nan"), 0))
+        B.sim_set_timing(b.h, 0)
+        clk = clocks.stop(t_begin, t_end) if clocks else None
+        phi, best = b.bias_functional()
+        # end to end with host buffers, as the default line
+        P = np.concatenate([b.get_state(k)[0] for k in range(len(systems))])
+        V = np.concatenate([b.get_state(k)[1] for k in range(len(systems))])
+        e2e_calls = 10
+        t0 = time.perf_counter()
+        for _ in range(e2e_calls):
+            b.set_state(-1, P, V)
+            b.step(nst)
+            phi_e, _ = b.bias_functional()
+        t1 = time.perf_counter()
+        B.sim_set_timing(b.h, 1)
+        B.sim_kernel_times(b.h)
+        for _ in range(3):
+            b.step(nst)
+        kt = B.sim_kernel_times(b.h)
+        B.sim_set_timing(b.h, 0)
+    value = atoms * nst * steps / (ms * 1e-3)
+    pk, src = peaks()
+    sm_mhz = pk.get("sm_max_mhz", 2070.0)
+    fp32_peak = 152 * 128 * 2 * sm_mhz * 1e6
+    pair_avg_s = pair_ms / max(pair_n, 1) * 1e-3
+    flops = atoms * PAIRS_PER_ATOM_STEP * FLOPS_PER_PAIR  # the same water density in every system
+    # the oracle on the host cores: a bounded sample (the smallest system, a few steps)
+    import oracle as O
+    small = min(range(len(systems)), key=lambda k: systems[k].n_atoms)
+    O.run(systems[small], p, seeds[small], 1)
+    tc = time.perf_counter()
+    r = O.run(systems[small], p, seeds[small], 20)
+    t_or = time.perf_counter() - tc
+    line = {
+        "metric": METRIC, "value": value, "unit": "atom-steps/s", "n_gpus": 1, "steps": steps,
+        "warmup": args.warmup, "ms_per_step": ms / steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+i64-fixed+ff-cv", "data": "synthetic",
+        "config": {"workload": f"uneven batch: 32 systems of {min(s.n_atoms for s in systems)} to "
+                               f"{max(s.n_atoms for s in systems)} atoms ({atoms} in all), one trial each, "
+                               f"{steps * nst} MD steps timed", "md_steps_per_bench_step": nst,
+                   "start": f"generated, relaxed {min(args.prep_steps, 1000)} steps at gamma 20/ps (untimed)",
+                   "autotuned": {"pair_variant": tuned[0], "cv_variant": tuned[1], "size_classes": classes},
+                   "l2": "working set > L2"},
+        "roofline": {"bound": "alu", "kernel": "pair", "achieved": flops / pair_avg_s / 1e12,
+                     "peak": fp32_peak / 1e12, "unit": "TFLOP/s", "frac": flops / pair_avg_s / fp32_peak,
+                     "traffic": None, "launch_ms": pair_avg_s * 1e3, "launches_timed": pair_n,
+                     "launch_timing": "event-record nodes around the pair launches of each step in the replayed graphs",
+                     "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz",
+                     "work": f"{PAIRS_PER_ATOM_STEP:.0f} half pairs x {FLOPS_PER_PAIR:.0f} flops per atom-step"},
+        "kernel_ms": {k: v[0] / v[1] for k, v in kt.items() if v[1] > 0},
+        "cpu_baseline": {"value": systems[small].n_atoms * 20 / t_or, "unit": "atom-steps/s", "cores": O.num_threads(),
+                         "kind": "oracle", "sample": f"the smallest system ({systems[small].n_atoms} atoms), 20 MD steps"},
+        "e2e": {"value": atoms * nst * e2e_calls / (t1 - t0), "unit": "atom-steps/s",
+                "h2d_bytes_per_step": int(P.nbytes + V.nbytes), "d2h_bytes_per_step": int(phi_e.nbytes + 8)},
+        "gpu_launches": int(round(steps * sum(v[1] for v in kt.values()) / 3)),
+        "clocks": clk,
+        "diagnostics": {"skin_violations": diag1["skin_violations"] - diag0["skin_violations"],
+                        "trial_rebuilds": diag1["trial_rebuilds"] - diag0["trial_rebuilds"],
+                        "trial_steps": len(systems) * nst * steps},
+        "selection": {"trial": int(best), "phi": float(phi[best]), "phi_per_trial": [float(x) for x in phi]},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def run_long(args):
+    """The stated run lengths: the 64-trial batch for 10 000 MD steps (each
+    trial's functional, the selected trial, error flags and list statistics)
+    and one trial of the same system for 20 000 MD steps, from the relaxed
+    start; timed as a whole (one bench step = the whole run)."""
+    import torch
+    rank, world, local = rank_info()
+    torch.cuda.set_device(local)
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1405_6104_gb300 import binding as B
+    from paper_1405_6104_gb300 import systems as S
+    s, p, seeds = S.batched_64(1)
+    s = equilibrate(B, S, s, p, steps=args.prep_steps) if args.prep_steps > 0 else s
+    out = {}
+    clocks = ClockSampler(local) if rank == 0 else None
+    t_begin = time.time()
+    for name, n_trials, n_md in (("batch64_10000", 64, 10000), ("single_20000", 1, 20000)):
+        with B.TrialBatch(s, p, [n_trials], trial_seeds=seeds[:n_trials]) as b:
+            B.sim_autotune(b.h, 3, None)
+            stream = torch.cuda.ExternalStream(b.stream)
+            b.step(p.nstlist)  # captures the chunk graph
+            ms = _timed_batch(B, b, (n_md - p.nstlist) // p.nstlist, p.nstlist, stream)
+            phi, best = b.bias_functional()
+            zs = [b.get_state(k)[2] for k in range(n_trials)]
+            diag = B.sim_diagnostics(b.h)
+        steps_timed = n_md - p.nstlist
+        out[name] = {
+            "trials": n_trials, "md_steps": n_md, "atom_steps_per_s": n_trials * s.n_atoms * steps_timed / (ms * 1e-3),
+            "ms": ms, "status": "ok (no error flag)", "phi": [float(x) for x in phi], "argmin": int(best),
+            "phi_min": float(phi[best]), "z_final": [float(z[0]) for z in zs], "z_min": [float(z[1]) for z in zs],
+            "skin_violations": diag["skin_violations"], "trial_rebuilds": diag["trial_rebuilds"],
+            "mean_steps_between_rebuilds": round(n_trials * n_md / max(diag["trial_rebuilds"], 1), 2)}
+    t_end = time.time()
+    clk = clocks.stop(t_begin, t_end) if clocks else None
+    line = {"metric": METRIC, "value": out["batch64_10000"]["atom_steps_per_s"], "unit": "atom-steps/s",
+            "n_gpus": 1, "steps": 1, "warmup": 1, "ms_per_step": out["batch64_10000"]["ms"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+i64-fixed+ff-cv", "data": "synthetic",
+            "config": {"workload": "64 trials x 11040 atoms for 10 000 MD steps (10 ps), and 1 trial for 20 000",
+                       "start": f"generated, relaxed {args.prep_steps} steps at gamma 20/ps (untimed)"},
+            "runs": out, "clocks": clk}
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=60,
-                    help="timed bench steps (60 x 10 MD steps keep the clock sampler inside the timed region)")
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed bench steps (default 60: 60 x 10 MD steps keep the clock sampler inside the timed "
+                         "region; uneven: 500, i.e. the configuration's 5 000 MD steps)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
-    ap.add_argument("--workload", default="batched64", choices=["batched64", "toy2d", "adjoint30k", "similarity"],
-                    help="batched64: the 64 x 11 040-atom trial batch (default); toy2d: the 2-D toy model's K_R "
-                         "scan; adjoint30k: the functional's gradient along a 500-frame path of 30 000 atoms; "
-                         "similarity: path similarity over 64 trial paths")
+    ap.add_argument("--workload", default="batched64",
+                    choices=["batched64", "uneven", "long", "toy2d", "adjoint30k", "similarity"],
+                    help="batched64: the 64 x 11 040-atom trial batch (default); uneven: 32 systems of 5k-60k atoms, "
+                         "5 000 steps; long: the stated run lengths (64 trials x 10 000 steps, 1 trial x 20 000); "
+                         "toy2d: the 2-D toy model's K_R scan; adjoint30k: the functional's gradient along a "
+                         "500-frame path of 30 000 atoms; similarity: path similarity over 64 trial paths")
     ap.add_argument("--pair-variant", type=int, default=None, help="fix the pair-kernel variant (skip autotuning)")
     ap.add_argument("--cv-variant", type=int, default=None, help="fix the reaction-coordinate kernel variant")
     ap.add_argument("--prep-steps", type=int, default=3000,
@@ -662,6 +837,10 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    if args.workload == "uneven":
+        return run_uneven(args)
+    if args.steps is None:
+        args.steps = 60
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "toy2d":
@@ -670,6 +849,8 @@ def main():
         return run_adjoint(args)
     if args.workload == "similarity":
         return run_similarity(args)
+    if args.workload == "long":
+        return run_long(args)
     return run_gpu(args)
 
 

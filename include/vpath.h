@@ -289,10 +289,22 @@ int sim_diagnostics(sim_handle *h, int64_t *out);
  * forces) and of the reaction-coordinate kernel
  * (2, 4 or 8 warps per block) on this batch, reps launches each, into scratch
  * accumulators (the state is untouched), and uses the fastest from then on.
+ * Size classes: the trials are grouped by round(log2 atoms) and density; when
+ * a batch holds more than one class, the pair variants are also timed on each
+ * class's clusters alone, and one launch per class with its own variant is
+ * used instead of the single launch when that sequence is faster.
  * cache_path (may be NULL): a text file of "size-class variant variant" lines
- * consulted first and appended to.  choice[2] (may be NULL) receives the
- * picked variants. */
+ * consulted first and appended to (batches of one class).  choice[2] (may be
+ * NULL) receives the picked variants (the single launch's pair variant). */
 int sim_autotune(sim_handle *h, int32_t reps, const char *cache_path, int32_t *choice);
+/* The batch's size classes: returns their number and writes, for k < cap,
+ * info[5k .. 5k+4] = {round(log2 atoms per trial), trials, clusters (slot
+ * capacity / 8), pair variant used for it, 1 if the class has a launch of its
+ * own (0: one launch for the batch)}. */
+int32_t sim_tune_classes(sim_handle *h, int32_t *info, int32_t cap);
+/* One pair launch per size class from now on, class k with variants[k]
+ * (n = the number of classes).  SIM_EINVAL for a wrong n or variant. */
+int sim_set_class_variants(sim_handle *h, const int32_t *variants, int32_t n);
 /* Sets the launch shapes directly (the numbering of sim_autotune), e.g. to
  * test one of them.  SIM_EINVAL for a variant out of range. */
 int sim_set_variants(sim_handle *h, int32_t pair_variant, int32_t cv_variant);

@@ -99,6 +99,8 @@ _SIGS = {
     "sim_potential_device": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
     "sim_autotune": ([C.c_void_p, C.c_int32, C.c_char_p, C.c_void_p], C.c_int),
     "sim_set_timing": ([C.c_void_p, C.c_int32], C.c_int),
+    "sim_tune_classes": ([C.c_void_p, C.c_void_p, C.c_int32], C.c_int32),
+    "sim_set_class_variants": ([C.c_void_p, C.c_void_p, C.c_int32], C.c_int),
     "sim_kernel_times": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32], C.c_int),
     "sim_philox_normals": ([C.c_uint64, C.c_int64, C.c_uint32, C.c_int32, C.c_void_p, C.c_void_p], C.c_int),
     "cv_eval_noalloc": ([C.c_void_p, C.c_void_p, C.c_int32, C.c_double, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
@@ -371,6 +373,24 @@ def sim_autotune(h, reps: int = 5, cache_path: Optional[str] = None):
     ch = np.zeros(2, np.int32)
     _check(h, load().sim_autotune(h, int(reps), None if cache_path is None else cache_path.encode(), ch.ctypes.data))
     return int(ch[0]), int(ch[1])
+
+
+def sim_tune_classes(h):
+    """The batch's size classes: a list of dicts (log2 atoms, trials, clusters,
+    pair variant, whether the class has its own pair launch)."""
+    n = load().sim_tune_classes(h, None, 0)
+    if n < 0:
+        raise SimError(n, sim_last_error(h))
+    info = np.zeros(5 * max(n, 1), np.int32)
+    load().sim_tune_classes(h, info.ctypes.data, n)
+    return [dict(lg_atoms=int(info[5 * k]), trials=int(info[5 * k + 1]), clusters=int(info[5 * k + 2]),
+                 pair_variant=int(info[5 * k + 3]), own_launch=bool(info[5 * k + 4])) for k in range(n)]
+
+
+def sim_set_class_variants(h, variants):
+    """One pair launch per size class, class k with variants[k]."""
+    v = np.ascontiguousarray(np.asarray(variants, np.int32))
+    _check(h, load().sim_set_class_variants(h, v.ctypes.data, len(v)))
 
 
 def sim_set_timing(h, on):

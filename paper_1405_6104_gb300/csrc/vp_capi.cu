@@ -63,6 +63,15 @@ struct sim_handle {
   std::string err;
   int rec_cap = 0;
   int pair_variant = 0, cv_variant = 0;  // launch shapes picked by the autotuner
+  // size classes of the batch (trials grouped by atom count, density and
+  // type count) and, when the autotuner found it faster, one pair launch per
+  // class over its clusters with the class's own variant
+  struct SizeClass {
+    int lg_atoms = 0, n_trials = 0, n_clus = 0, variant = 0;
+    int *clist = nullptr;
+  };
+  std::vector<SizeClass> classes;
+  bool per_class = false;
   // CV-frame recorder (one trial)
   int frame_trial = -1, frame_cap = 0;
   float *frames = nullptr;
@@ -199,14 +208,24 @@ void rebuild_list(sim_handle *h) {
   timed(h, "list", [&] { launch_list(h->d, h->c, h->rl2_bbox, h->stream); });
 }
 
+// the nonbonded forces of every trial: one launch over all clusters, or one
+// per size class with the class's variant
+void launch_pair_hot(const sim_handle *h, const Dev &d, cudaStream_t s) {
+  if (!h->per_class) {
+    launch_pair(d, h->c, false, -1, s, h->pair_variant);
+    return;
+  }
+  for (const auto &k : h->classes) launch_pair(d, h->c, false, -1, s, k.variant, k.clist, k.n_clus);
+}
+
 void pair_forces(sim_handle *h) {
   cudaStream_t s = h->stream;
   if (h->gtiming && h->cap_k >= 0) {
     cudaEventRecordWithFlags(h->gev[2 * h->cap_k], s, cudaEventRecordExternal);  // a failure ends the capture
-    launch_pair(h->d, h->c, false, -1, s, h->pair_variant);
+    launch_pair_hot(h, h->d, s);
     cudaEventRecordWithFlags(h->gev[2 * h->cap_k + 1], s, cudaEventRecordExternal);
   } else {
-    timed(h, "pair", [&] { launch_pair(h->d, h->c, false, -1, s, h->pair_variant); });
+    timed(h, "pair", [&] { launch_pair_hot(h, h->d, s); });
   }
 }
 
@@ -1066,7 +1085,7 @@ VP_API int sim_potential_device(sim_handle *h, const double *d_pos, double *d_en
   launch_decide(d, h->c, s);
   rebuild_cols(h);
   rebuild_list(h);
-  launch_pair(d, h->c, false, -1, s, h->pair_variant);
+  launch_pair_hot(h, d, s);
   launch_bonded(d, s);
   launch_pair(d, h->c, true, -1, s);
   launch_potential_out(d, d_energy, d_forces, n, s);
@@ -1333,13 +1352,46 @@ void tune_store(const char *path, const std::string &key, int pv, int cv) {
 
 }  // namespace
 
+namespace {
+// size classes: trials grouped by round(log2 atoms), density (per 10 atoms/nm^3)
+// and the batch's type count; device cluster lists of each class
+int build_classes(sim_handle *h) {
+  if (!h->classes.empty()) return SIM_OK;
+  std::map<std::pair<int, int>, std::vector<int>> groups;
+  for (int t = 0; t < h->n_trials; ++t) {
+    const TrialInfo &T = h->tinfo[t];
+    const double vol = (double)T.box * T.box * T.box;
+    const int lg = (int)std::lround(std::log2((double)std::max(1, T.n_atoms)));
+    const int dens = (int)std::lround(T.n_atoms / std::max(vol, 1e-9) / 10.0);
+    groups[{lg, dens}].push_back(t);
+  }
+  for (const auto &g : groups) {
+    sim_handle::SizeClass k;
+    k.lg_atoms = g.first.first;
+    k.n_trials = (int)g.second.size();
+    std::vector<int32_t> cl;
+    for (int t : g.second)
+      for (int q = 0; q < h->tinfo[t].max_clus; ++q) cl.push_back(h->tinfo[t].clus0 + q);
+    k.n_clus = (int)cl.size();
+    int r = upload(h, &k.clist, cl);
+    if (r) return r;
+    h->classes.push_back(k);
+  }
+  return SIM_OK;
+}
+}  // namespace
+
 VP_API int sim_autotune(sim_handle *h, int32_t reps, const char *cache_path, int32_t *choice) {
   int r = enter(h);
   if (r) return r;
   if (reps < 1) reps = 5;
+  r = build_classes(h);
+  if (r) return r;
   const std::string key = tune_key(h);
   int pv = 0, cv = 0;
-  if (!tune_lookup(cache_path, key, pv, cv)) {
+  bool per_class = false;
+  const bool multi = h->classes.size() > 1;
+  if (multi || !tune_lookup(cache_path, key, pv, cv)) {
     // scratch accumulators: the timed launches must not touch the state
     Dev scratch = h->d;
     const size_t ns = (size_t)h->d.total_slots + CJ;  // with the idle half cluster
@@ -1370,20 +1422,37 @@ VP_API int sim_autotune(sim_handle *h, int32_t reps, const char *cache_path, int
       float ms = time_it([&] { launch_pair(scratch, h->c, false, -1, h->stream, v); });
       if (ms < best) { best = ms; pv = v; }
     }
-    best = 3e38f;
+    if (multi) {
+      // each class on its own, then the classes one after another with their
+      // own variants against the best single launch over the whole batch
+      for (auto &k : h->classes) {
+        float bk = 3e38f;
+        for (int v = 0; v < PAIR_VARIANTS; ++v) {
+          float ms = time_it([&] { launch_pair(scratch, h->c, false, -1, h->stream, v, k.clist, k.n_clus); });
+          if (ms < bk) { bk = ms; k.variant = v; }
+        }
+      }
+      const float t_classes = time_it([&] {
+        for (const auto &k : h->classes) launch_pair(scratch, h->c, false, -1, h->stream, k.variant, k.clist, k.n_clus);
+      });
+      per_class = t_classes < best;
+    }
+    float bc = 3e38f;
     for (int v = 0; v < CV_VARIANTS; ++v) {
       float ms = time_it([&] { launch_cv(scratch, h->c, h->stream, v); });
-      if (ms < best) { best = ms; cv = v; }
+      if (ms < bc) { bc = ms; cv = v; }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cudaFree(buf);
     cudaFree(zp);
     CK(cudaGetLastError());
-    tune_store(cache_path, key, pv, cv);
+    if (!multi) tune_store(cache_path, key, pv, cv);
   }
   h->pair_variant = pv;
   h->cv_variant = cv;
+  h->per_class = per_class;
+  if (!multi && !h->classes.empty()) h->classes[0].variant = pv;
   if (h->chunk) {
     cudaGraphExecDestroy(h->chunk);
     h->chunk = nullptr;
@@ -1392,12 +1461,41 @@ VP_API int sim_autotune(sim_handle *h, int32_t reps, const char *cache_path, int
   return SIM_OK;
 }
 
+VP_API int sim_set_class_variants(sim_handle *h, const int32_t *variants, int32_t n) {
+  if (!h) return SIM_EINVAL;
+  if (build_classes(h)) return SIM_ECUDA;
+  if (!variants || n != (int32_t)h->classes.size()) return fail(h, SIM_EINVAL, "one variant per size class");
+  for (int k = 0; k < n; ++k)
+    if (variants[k] < 0 || variants[k] >= PAIR_VARIANTS) return fail(h, SIM_EINVAL, "variant out of range");
+  for (int k = 0; k < n; ++k) h->classes[k].variant = variants[k];
+  h->per_class = true;
+  if (h->chunk) {
+    cudaGraphExecDestroy(h->chunk);
+    h->chunk = nullptr;
+  }
+  return SIM_OK;
+}
+
+VP_API int32_t sim_tune_classes(sim_handle *h, int32_t *info, int32_t cap) {
+  if (!h) return SIM_EINVAL;
+  if (build_classes(h)) return SIM_ECUDA;
+  const int n = (int)h->classes.size();
+  for (int k = 0; k < n && k < cap && info; ++k) {
+    const auto &c = h->classes[k];
+    int32_t *o = info + 5 * k;
+    o[0] = c.lg_atoms; o[1] = c.n_trials; o[2] = c.n_clus; o[3] = h->per_class ? c.variant : h->pair_variant;
+    o[4] = h->per_class ? 1 : 0;
+  }
+  return n;
+}
+
 VP_API int sim_set_variants(sim_handle *h, int32_t pair_variant, int32_t cv_variant) {
   if (!h) return SIM_EINVAL;
   if (pair_variant < 0 || pair_variant >= PAIR_VARIANTS || cv_variant < 0 || cv_variant >= CV_VARIANTS)
     return fail(h, SIM_EINVAL, "variant out of range");
   h->pair_variant = pair_variant;
   h->cv_variant = cv_variant;
+  h->per_class = false;
   if (h->chunk) {
     cudaGraphExecDestroy(h->chunk);
     h->chunk = nullptr;

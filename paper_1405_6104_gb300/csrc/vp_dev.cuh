@@ -121,7 +121,9 @@ void launch_colsort(const Dev &d, cudaStream_t s);
 void launch_list(const Dev &d, const SimConst &c, float rl2_bbox, cudaStream_t s);
 void launch_list_positions(const Dev &d, int32_t trial, double *out, int32_t n, cudaStream_t s);
 // forces (vp_pair.cu)
-void launch_pair(const Dev &d, const SimConst &c, bool energy, int32_t only_trial, cudaStream_t s, int variant = 0);
+// clist (optional): the i-clusters to work on (n_items of them), else all
+void launch_pair(const Dev &d, const SimConst &c, bool energy, int32_t only_trial, cudaStream_t s, int variant = 0,
+                 const int *clist = nullptr, int n_items = 0);
 void launch_bonded(const Dev &d, cudaStream_t s);
 constexpr int PAIR_VARIANTS = 9;
 // reaction coordinate and functional (vp_cv.cu)

@@ -259,15 +259,16 @@ constexpr float MASK_PEN = 1.0e30f;
 // pair) instead of being held in 32 registers, which lets more warps reside.
 // TS is the row stride of the per-warp LJ table (at least the number of types).
 template <int MINB, bool SHI, int TS>
-__global__ void __launch_bounds__(PF_WARPS * 32, MINB) k_pair_f(Dev d, SimConst c) {
+__global__ void __launch_bounds__(PF_WARPS * 32, MINB) k_pair_f(Dev d, SimConst c, const int *clist, int n_items) {
   __shared__ float2 s_cij[PF_WARPS][CL][TS];
   __shared__ float4 s_sh[PF_WARPS][64];
   __shared__ float4 s_i[PF_WARPS][CL];
   __shared__ float s_red[PF_WARPS][3 * CL * 33];
   const int wib = threadIdx.x >> 5;
-  const int I = blockIdx.x * PF_WARPS + wib;
+  const int item = blockIdx.x * PF_WARPS + wib;
   const int lane = threadIdx.x & 31;
-  if (I >= d.total_clus) return;
+  if (item >= n_items) return;
+  const int I = clist ? clist[item] : item;
   const int t = d.clus_trial[I];
   const TrialInfo T = d.tinfo[t];
   if (I - T.clus0 >= d.tstate[t].n_clus) return;
@@ -429,7 +430,8 @@ __global__ void __launch_bounds__(PF_WARPS * 32, MINB) k_pair_f(Dev d, SimConst 
 // sums even and odd i-atoms in two partials, as the scalar variants do, so
 // all variants give bit-identical forces.
 template <int MINB>
-__global__ void __launch_bounds__(PF_WARPS * 32, MINB) k_pair_f2(Dev d, SimConst c, unsigned *next) {
+__global__ void __launch_bounds__(PF_WARPS * 32, MINB) k_pair_f2(Dev d, SimConst c, unsigned *next, const int *clist,
+                                                                   int n_items) {
   constexpr int TS = SMALL_TYPES;
   __shared__ float4 s_c4[PF_WARPS][CL / 2][TS];
   __shared__ float4 s_sh[PF_WARPS][64];
@@ -443,8 +445,9 @@ __global__ void __launch_bounds__(PF_WARPS * 32, MINB) k_pair_f2(Dev d, SimConst
   __syncwarp();  // the warp's tables of its previous cluster are no longer read
   unsigned got = 0u;
   if (lane == 0) got = atomicAdd(next, 1u);
-  const int I = (int)__shfl_sync(0xffffffffu, got, 0);
-  if (I >= d.total_clus) return;
+  const int item = (int)__shfl_sync(0xffffffffu, got, 0);
+  if (item >= n_items) return;
+  const int I = clist ? clist[item] : item;
   const int t = d.clus_trial[I];
   const TrialInfo T = d.tinfo[t];
   if (I - T.clus0 >= d.tstate[t].n_clus) continue;
@@ -703,7 +706,8 @@ void launch_bonded(const Dev &d, cudaStream_t s) {
 // shared memory and an LJ table for at most SMALL_TYPES types (less shared
 // memory per block), 6/7/8 blocks (larger type sets fall back to variant 0).
 // All variants do the same arithmetic in the same order (bit-identical forces).
-void launch_pair(const Dev &d, const SimConst &c, bool energy, int32_t only_trial, cudaStream_t s, int variant) {
+void launch_pair(const Dev &d, const SimConst &c, bool energy, int32_t only_trial, cudaStream_t s, int variant,
+                 const int *clist, int n_items) {
   long long threads = (long long)d.total_clus * 32;
   unsigned blocks = (unsigned)((threads + 127) / 128);
   const size_t nt2 = (size_t)c.n_types * c.n_types;
@@ -711,26 +715,28 @@ void launch_pair(const Dev &d, const SimConst &c, bool energy, int32_t only_tria
     k_pair<true, 4><<<blocks, 128, nt2 * (sizeof(float2) + sizeof(float)), s>>>(d, c, only_trial);
     return;
   }
-  const unsigned fb = (unsigned)((d.total_clus + PF_WARPS - 1) / PF_WARPS);
+  if (!clist) n_items = d.total_clus;
+  if (n_items <= 0) return;
+  const unsigned fb = (unsigned)((n_items + PF_WARPS - 1) / PF_WARPS);
   if (variant >= 3 && c.n_types > SMALL_TYPES) variant = 0;
   switch (variant) {
-    case 1: k_pair_f<5, false, MAX_TYPES><<<fb, PF_WARPS * 32, 0, s>>>(d, c); break;
-    case 2: k_pair_f<6, false, MAX_TYPES><<<fb, PF_WARPS * 32, 0, s>>>(d, c); break;
-    case 3: k_pair_f<6, true, SMALL_TYPES><<<fb, PF_WARPS * 32, 0, s>>>(d, c); break;
-    case 4: k_pair_f<7, true, SMALL_TYPES><<<fb, PF_WARPS * 32, 0, s>>>(d, c); break;
-    case 5: k_pair_f<8, true, SMALL_TYPES><<<fb, PF_WARPS * 32, 0, s>>>(d, c); break;
+    case 1: k_pair_f<5, false, MAX_TYPES><<<fb, PF_WARPS * 32, 0, s>>>(d, c, clist, n_items); break;
+    case 2: k_pair_f<6, false, MAX_TYPES><<<fb, PF_WARPS * 32, 0, s>>>(d, c, clist, n_items); break;
+    case 3: k_pair_f<6, true, SMALL_TYPES><<<fb, PF_WARPS * 32, 0, s>>>(d, c, clist, n_items); break;
+    case 4: k_pair_f<7, true, SMALL_TYPES><<<fb, PF_WARPS * 32, 0, s>>>(d, c, clist, n_items); break;
+    case 5: k_pair_f<8, true, SMALL_TYPES><<<fb, PF_WARPS * 32, 0, s>>>(d, c, clist, n_items); break;
     case 6: case 7: case 8: {
       // persistent grid: as many blocks as can be resident, sized from the SM
       // count; the counter hands out the i-clusters
       const int minb = variant - 1;
       const unsigned pb = std::min(fb, (unsigned)(d.n_sm * minb));
       cudaMemsetAsync(d.pair_next, 0, sizeof(unsigned), s);
-      if (variant == 6) k_pair_f2<5><<<pb, PF_WARPS * 32, 0, s>>>(d, c, d.pair_next);
-      else if (variant == 7) k_pair_f2<6><<<pb, PF_WARPS * 32, 0, s>>>(d, c, d.pair_next);
-      else k_pair_f2<7><<<pb, PF_WARPS * 32, 0, s>>>(d, c, d.pair_next);
+      if (variant == 6) k_pair_f2<5><<<pb, PF_WARPS * 32, 0, s>>>(d, c, d.pair_next, clist, n_items);
+      else if (variant == 7) k_pair_f2<6><<<pb, PF_WARPS * 32, 0, s>>>(d, c, d.pair_next, clist, n_items);
+      else k_pair_f2<7><<<pb, PF_WARPS * 32, 0, s>>>(d, c, d.pair_next, clist, n_items);
       break;
     }
-    default: k_pair_f<4, false, MAX_TYPES><<<fb, PF_WARPS * 32, 0, s>>>(d, c); break;
+    default: k_pair_f<4, false, MAX_TYPES><<<fb, PF_WARPS * 32, 0, s>>>(d, c, clist, n_items); break;
   }
 }
 

@@ -397,18 +397,40 @@ __device__ __forceinline__ void list_cluster(const Dev &d, const SimConst &c, fl
   int n_cand = 0;
   bool overflow = false;
   // ---- phase 1: candidate 4-atom j-clusters ----
-  // lanes test 32 columns; the halves (of clusters with index >= Il) of the
-  // passing columns are then enumerated as one flat range, 32 per step, so
-  // that the bounding-box loads of a whole step are in flight together
-  for (int cb = 0; cb < nc2; cb += 32) {
-    const int cc = cb + lane;
+  // Only the grid columns within reach of the i-cluster's bounding box (one
+  // column more on each side for the rounding of the binning) are visited,
+  // in ascending column index: the window's x and y column indices, wrapped
+  // periodically, are enumerated in sorted order (so the candidates, and the
+  // entries, ascend in j-cluster index).  Lanes test 32 columns; the halves
+  // (of clusters with index >= Il) of the passing columns are then
+  // enumerated as one flat range, 32 per step, so that the bounding-box loads
+  // of a whole step are in flight together.
+  const float reach = sqrtf(rl2_bbox);
+  int wx0, wnx, wy0, wny;  // first column (mod ncol) and count of the window in x and in y
+  {
+    const int ax = (int)floorf((lo.x - reach) * T.inv_col_w) - 1, bx = (int)floorf((hi.x + reach) * T.inv_col_w) + 1;
+    const int ay = (int)floorf((lo.y - reach) * T.inv_col_w) - 1, by = (int)floorf((hi.y + reach) * T.inv_col_w) + 1;
+    wnx = min(T.ncol, bx - ax + 1);
+    wny = min(T.ncol, by - ay + 1);
+    wx0 = wnx == T.ncol ? 0 : ((ax % T.ncol) + T.ncol) % T.ncol;
+    wy0 = wny == T.ncol ? 0 : ((ay % T.ncol) + T.ncol) % T.ncol;
+  }
+  // k-th smallest of {a, a + 1, ..., a + m - 1} mod ncol
+  auto kth = [&](int a, int m, int k) {
+    const int e = a + m - T.ncol;  // the part that wraps to [0, e)
+    return e <= 0 ? a + k : (k < e ? k : a + (k - e));
+  };
+  const int nwin = wnx * wny;
+  for (int cb = 0; cb < nwin; cb += 32) {
+    const int wi = cb + lane;
     // this lane's column: up to two ranges [a1, a1 + n1), [a2, a2 + n2) of
     // half indices (relative to the trial's first half) whose z-extent can
     // reach the i-cluster: the z-window (and its periodic image) comes from
     // the column's xy gap, the ranges from the column's z-bin table, one bin
     // wider on each side than needed (every half in them is still tested)
     int a1 = 0, n1 = 0, a2 = 0, n2 = 0;
-    if (cc < nc2) {
+    const int cc = wi < nwin ? kth(wx0, wnx, wi / wny) * T.ncol + kth(wy0, wny, wi % wny) : 0;
+    if (wi < nwin) {
       const int ccs = d.col_cstart[T.col0 + cc];
       const int ncl = max(0, (cc + 1 < nc2 ? d.col_cstart[T.col0 + cc + 1] : d.tstate[t].n_clus) - ccs);
       const int jlo = max(ccs, Il);

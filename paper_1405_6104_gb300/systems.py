@@ -88,7 +88,10 @@ class Params:
 # force-field constants of the synthetic models (fixed once here so both sides
 # read identical data)
 WATER_O = dict(mass=15.9994, charge=-0.834, sigma=0.315061, epsilon=0.636386)
-WATER_H = dict(mass=1.008, charge=0.417, sigma=0.0, epsilon=0.0)
+# the hydrogen's small Lennard-Jones sphere (CHARMM's variant of TIP3P) keeps
+# a hydrogen of this flexible water from collapsing onto an atom that attracts
+# it (without it a hot start of the solvated systems can blow up)
+WATER_H = dict(mass=1.008, charge=0.417, sigma=0.0400013, epsilon=0.192464)
 WATER_OH = dict(r0=0.09572, k=462750.0)
 WATER_HOH = dict(t0=math.radians(104.52), k=836.8)
 POLY_CLASSES = dict(sigma=[0.25, 0.30, 0.34, 0.37], epsilon=[0.1, 0.4, 0.5, 0.8],

@@ -71,3 +71,28 @@ def test_uneven_batch_sampled_parity_and_invariance(uneven):
         pos, vel, cv = b.get_state(0)
     assert np.array_equal(pos, states[smallest][0]) and np.array_equal(vel, states[smallest][1])
     assert cv[3] == states[smallest][2][3]
+
+
+def test_per_class_launches_are_bit_identical(uneven):
+    """The size classes of the uneven batch: one pair launch per class, each
+    with its own variant (the autotuner's per-class picks, and a fixed mix),
+    gives the same trajectories, bit for bit, as one launch over the whole
+    batch with variant 0."""
+    systems, p = uneven
+    sub = [systems[k] for k in np.argsort([s.n_atoms for s in systems])[::6]]  # six systems across the sizes
+    seeds = [3000 + k for k in range(len(sub))]
+    results = []
+    for mode in ("single", "tuned", "mix"):
+        with B.TrialBatch(sub, p, [1] * len(sub), trial_seeds=seeds) as b:
+            classes = B.sim_tune_classes(b.h)
+            assert len(classes) >= 3 and sum(c["trials"] for c in classes) == len(sub)
+            if mode == "tuned":
+                B.sim_autotune(b.h, 1, None)
+            elif mode == "mix":
+                B.sim_set_class_variants(b.h, [(0, 8, 3, 6, 1)[k % 5] for k in range(len(classes))])
+                assert all(c["own_launch"] for c in B.sim_tune_classes(b.h))
+            b.step(15)
+            results.append([b.get_state(k) for k in range(len(sub))])
+    for other in results[1:]:
+        for x, y in zip(results[0], other):
+            assert np.array_equal(x[0], y[0]) and np.array_equal(x[1], y[1]) and x[2][3] == y[2][3]
