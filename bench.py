@@ -230,6 +230,7 @@ def run_gpu(args):
     # or fixed from the command line (through the autotuner's cache format)
     if args.pair_variant is None and args.cv_variant is None:
         tuned = B.sim_autotune(batch.h, 5, None)
+        step_form = B.sim_autotune_step(batch.h, 2)
     else:
         probe = tempfile.mktemp(suffix=".txt")
         picked = B.sim_autotune(batch.h, 1, probe)
@@ -239,6 +240,9 @@ def run_gpu(args):
                     f"{args.cv_variant if args.cv_variant is not None else picked[1]}\n")
         tuned = B.sim_autotune(batch.h, 1, probe)
         os.unlink(probe)
+        step_form = 0
+    if step_form != 0:  # the roofline times the pair launches of the kernel-per-phase form
+        B.sim_set_step_mode(batch.h, 0)
     clocks = ClockSampler(local) if rank == 0 else None
     # event-record nodes around the pair kernel inside the chunk graph: the
     # roofline's launch duration is measured over the timed region itself
@@ -328,6 +332,7 @@ def run_gpu(args):
     if rank == 0:
         with B.TrialBatch(s, p, [1], trial_seeds=seeds[:1]) as one:
             B.sim_autotune(one.h, 5, None)
+            plain_form = B.sim_autotune_step(one.h, 3)
             ostream = torch.cuda.ExternalStream(one.stream)
             for _ in range(args.warmup):
                 one.step(nst)
@@ -341,7 +346,8 @@ def run_gpu(args):
             torch.cuda.synchronize()
             pv = s.n_atoms * nst * n_plain / (e0.elapsed_time(e1) * 1e-3)
             plain = {"value": pv, "unit": "atom-steps/s",
-                     "workload": f"1 trial x {s.n_atoms} atoms, same kernels and graph replay, {n_plain} x {nst} MD steps",
+                     "workload": f"1 trial x {s.n_atoms} atoms, same kernels, {n_plain} x {nst} MD steps",
+                     "step_form": "one cooperative kernel per step" if plain_form else "kernel per phase, graph replays",
                      "batching_speedup": value / world / pv}
 
     if rank == 0:
@@ -366,7 +372,9 @@ def run_gpu(args):
             "config": {"workload": WORKLOAD, "global_batch": n_trials * world, "atoms_per_trial": s.n_atoms,
                        "start": f"generated, relaxed {args.prep_steps} steps at gamma 20/ps (untimed)",
                        "md_steps_per_bench_step": nst, "parallelism": f"replicas x{world}",
-                       "autotuned": {"pair_variant": tuned[0], "cv_variant": tuned[1]},
+                       "autotuned": {"pair_variant": tuned[0], "cv_variant": tuned[1],
+                                     "step_form": "one cooperative kernel per step" if step_form else
+                                     "kernel per phase, graph replays"},
                        "l2": "working set > L2 (lists + state ~0.5 GB)"},
             "roofline": {"bound": "alu", "kernel": "pair", "achieved": achieved / 1e12, "peak": fp32_peak / 1e12,
                          "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": pair_traffic(),
@@ -496,6 +504,7 @@ def run_adjoint(args):
     n_frames, every = 500, 50
     with B.TrialBatch(s, p, [1], trial_seeds=[3]) as b:
         B.sim_autotune(b.h, 3, None)
+        fwd_form = B.sim_autotune_step(b.h, 2)
         stream = torch.cuda.ExternalStream(b.stream)
         for _ in range(args.warmup):
             trajectory_adjoint(b, 0, n_frames, every=every)
@@ -516,7 +525,9 @@ def run_adjoint(args):
         # where the time goes: one more run with per-kernel timing on the
         # batch and on the batch that replays the segments side by side
         handles = [b.h] + [rb.h for rb in b.__dict__.get("_replay_batches", {}).values()]
+        forms = [B.sim_step_mode(hh) for hh in handles]
         for hh in handles:
+            B.sim_set_step_mode(hh, 0)  # per-kernel times need the kernel-per-phase form
             B.sim_set_timing(hh, 1)
             B.sim_kernel_times(hh)
         t1 = time.perf_counter()
@@ -530,6 +541,8 @@ def run_adjoint(args):
             if kt_fwd is None:
                 kt_fwd = dict(kt)
             B.sim_set_timing(hh, 0)
+        for hh, f in zip(handles, forms):
+            B.sim_set_step_mode(hh, f)
     md_ms = sum(v[0] for v in kt.values())
     pk, _ = peaks()
     sm_mhz = pk.get("sm_max_mhz", 2070.0)
@@ -544,7 +557,8 @@ def run_adjoint(args):
         "vs_baseline": None, "dtype": "f32+i64-fixed+ff-cv", "data": "synthetic",
         "config": {"workload": f"30 000 atoms (1800-atom solute, 9400 waters), {n_frames} frames (1 per step), "
                                f"checkpoints every {every} steps, k_R 5", "phi": float(phi),
-                   "grad_max": float(np.abs(G).max())},
+                   "grad_max": float(np.abs(G).max()),
+                   "forward_step_form": "one cooperative kernel per step" if fwd_form else "kernel per phase"},
         "wall_s_per_step": wall / args.steps,
         "md_kernels_ms_per_step": md_ms,
         "md_kernel_share": md_ms / (t_kt * 1e3),

@@ -52,7 +52,7 @@ extern "C" {
 #define SIM_ENONFINITE (-5)      /* a position, velocity or z became non-finite, a force exceeded
                                    2^30 kJ/mol/nm or an atom moved more than a box length in one
                                    step (the run has blown up) */
-#define SIM_ETIMEOUT (-6)        /* a bounded device wait gave up */
+#define SIM_ETIMEOUT (-6)        /* a bounded device wait gave up (a grid barrier of the one-kernel step) */
 
 /* sim_params.flags */
 #define SIM_STRICT_SKIN 1        /* with SIM_FIXED_INTERVAL: treat skin violations as errors instead of
@@ -308,6 +308,23 @@ int sim_set_class_variants(sim_handle *h, const int32_t *variants, int32_t n);
 /* Sets the launch shapes directly (the numbering of sim_autotune), e.g. to
  * test one of them.  SIM_EINVAL for a variant out of range. */
 int sim_set_variants(sim_handle *h, int32_t pair_variant, int32_t cv_variant);
+
+/* Form of a step.  mode 0: one kernel per phase (update, rebuild decision,
+ * list rebuilds, pair forces, bonded forces and the reaction coordinate on a
+ * second stream, finaliser), CUDA-graph replays of nstlist-step chunks;
+ * mode 1: one cooperative kernel per step (every phase of every trial; grid
+ * barriers between phases, each polling a bounded number of times: when one
+ * gives up the call returns SIM_ETIMEOUT and the step is incomplete; the
+ * environment variable VPATH_SPIN_LIMIT, read at sim_create, sets the bound
+ * for fault-injection tests), for batches too small to fill the GPU.  Both
+ * forms give bit-identical states.  SIM_EINVAL for another mode.
+ * sim_step_mode returns the current form.  sim_autotune_step times reps
+ * chunks of nstlist steps in each form, keeps the faster (*mode, may be NULL)
+ * and restores the state it started from (positions, velocities, z_m, Phi,
+ * step counter; the lists are rebuilt). */
+int sim_set_step_mode(sim_handle *h, int32_t mode);
+int32_t sim_step_mode(const sim_handle *h);
+int sim_autotune_step(sim_handle *h, int32_t reps, int32_t *mode);
 
 /* Kernel timing.  on = 1: the next sim_step_batch calls launch kernels
  * directly and time each launch with CUDA events on the library stream.

@@ -101,6 +101,9 @@ _SIGS = {
     "sim_set_timing": ([C.c_void_p, C.c_int32], C.c_int),
     "sim_tune_classes": ([C.c_void_p, C.c_void_p, C.c_int32], C.c_int32),
     "sim_set_class_variants": ([C.c_void_p, C.c_void_p, C.c_int32], C.c_int),
+    "sim_set_step_mode": ([C.c_void_p, C.c_int32], C.c_int),
+    "sim_step_mode": ([C.c_void_p], C.c_int32),
+    "sim_autotune_step": ([C.c_void_p, C.c_int32, C.c_void_p], C.c_int),
     "sim_kernel_times": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32], C.c_int),
     "sim_philox_normals": ([C.c_uint64, C.c_int64, C.c_uint32, C.c_int32, C.c_void_p, C.c_void_p], C.c_int),
     "cv_eval_noalloc": ([C.c_void_p, C.c_void_p, C.c_int32, C.c_double, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
@@ -391,6 +394,22 @@ def sim_set_class_variants(h, variants):
     """One pair launch per size class, class k with variants[k]."""
     v = np.ascontiguousarray(np.asarray(variants, np.int32))
     _check(h, load().sim_set_class_variants(h, v.ctypes.data, len(v)))
+
+
+def sim_set_step_mode(h, mode: int):
+    """0: one kernel per phase (graph replays); 1: one cooperative kernel per step."""
+    _check(h, load().sim_set_step_mode(h, int(mode)))
+
+
+def sim_step_mode(h) -> int:
+    return int(load().sim_step_mode(h))
+
+
+def sim_autotune_step(h, reps: int = 3) -> int:
+    """Times both step forms on this batch, keeps the faster; the state is restored."""
+    m = C.c_int32(0)
+    _check(h, load().sim_autotune_step(h, int(reps), C.byref(m)))
+    return int(m.value)
 
 
 def sim_set_timing(h, on):

@@ -11,8 +11,9 @@ SRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libvpath.so")
 SOURCES = ["vp_rebuild.cu", "vp_pair.cu", "vp_cv.cu", "vp_update.cu", "vp_capi.cu", "vp_noalloc.cu", "vp_adjoint.cu",
-           "vp_toy2d.cu", "vp_contacts.cu"]
-HEADERS = ["vp_internal.cuh", "vp_dev.cuh", "vp_cvpair.cuh", "vp_adjoint.cuh", "vp_contacts.cuh", os.path.join("..", "..", "include", "vpath.h")]
+           "vp_toy2d.cu", "vp_contacts.cu", "vp_step.cu"]
+HEADERS = ["vp_internal.cuh", "vp_dev.cuh", "vp_cvpair.cuh", "vp_adjoint.cuh", "vp_contacts.cuh", "vp_pair_dev.cuh",
+           "vp_cv_dev.cuh", "vp_rebuild_dev.cuh", "vp_update_dev.cuh", os.path.join("..", "..", "include", "vpath.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-fvisibility=hidden"]
 # the pair kernel works far from the denormal range: flush-to-zero keeps its

@@ -72,6 +72,10 @@ struct sim_handle {
   };
   std::vector<SizeClass> classes;
   bool per_class = false;
+  // step form: false = one kernel per phase (CUDA-graph replays of chunks),
+  // true = one cooperative kernel per step (replayed in graphs when the
+  // capture succeeds, else launched directly)
+  bool fused = false, fused_no_graph = false;
   // CV-frame recorder (one trial)
   int frame_trial = -1, frame_cap = 0;
   float *frames = nullptr;
@@ -286,6 +290,12 @@ void forces(sim_handle *h, FinMode mode, int request) {
 }
 
 void one_step(sim_handle *h) {
+  if (h->fused) {
+    timed(h, "step_fused",
+          [&] { launch_step_fused(h->d, h->c, h->rl2_bbox, h->half_skin2, h->strict_skin, h->stream); });
+    after_forces(h, FIN_STEP);
+    return;
+  }
   timed(h, "update", [&] { launch_update(h->d, h->c, UPD_DRIFT, h->stream); });
   forces(h, FIN_STEP, NO_REQUEST);
 }
@@ -302,6 +312,12 @@ int check_flags(sim_handle *h) {
     return fail(h, SIM_ELIST_OVERFLOW, "cluster list, grid column or cluster capacity exceeded");
   if (flags & ERR_SKIN)
     return fail(h, SIM_ESKIN, "an atom moved more than skin/2 between fixed-interval list rebuilds");
+  if (flags & ERR_TIMEOUT) {
+    // the barrier is left half counted: start it afresh for the next launch
+    CK(cudaMemsetAsync(h->d.bar, 0, 2 * sizeof(unsigned), h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return fail(h, SIM_ETIMEOUT, "a grid barrier of the one-kernel step gave up waiting (the step is incomplete)");
+  }
   return SIM_OK;
 }
 
@@ -483,6 +499,11 @@ VP_API int sim_create(const sim_system *systems, int32_t n_systems, const int32_
   h->half_skin2 = (float)(0.25 * p.skin * p.skin);
   c.nstlist = p.nstlist;
   c.list_fixed = (p.flags & SIM_FIXED_INTERVAL) ? 1 : 0;
+  // bounded grid barriers of the one-kernel step: 2^20 polls of >= 64 ns; the
+  // debug variable VPATH_SPIN_LIMIT sets another bound (a test makes it run
+  // out with a tiny one)
+  c.spin_limit = 1u << 20;
+  if (const char *e = std::getenv("VPATH_SPIN_LIMIT")) c.spin_limit = (uint32_t)std::strtoul(e, nullptr, 10);
   {
     const double trig = std::max(0.0, 0.5 * p.skin - 1e-5);  // 1e-5 nm cover FP32 rounding
     c.trig2 = (float)(trig * trig);
@@ -845,7 +866,8 @@ VP_API int sim_create(const sim_system *systems, int32_t n_systems, const int32_
   r |= dalloc(h, &h->d_argmin, 1);
   r |= dalloc(h, &h->d_count, 1);
   r |= dalloc(h, &h->d_flag, 1);
-  r |= dalloc(h, &d.pair_next, 1);
+  r |= dalloc(h, &d.pair_next, 3);
+  r |= dalloc(h, &d.bar, 2);
   {
     int nsm = 0;
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device);
@@ -898,8 +920,14 @@ VP_API int sim_step_batch(sim_handle *h, int32_t n_steps) {
   int left = n_steps;
   bool pending = false;  // a replay whose in-graph timing events are not read yet
   while (left > 0) {
-    if (h->use_graph && !h->timing && left >= nst) {
+    if (h->use_graph && !h->timing && left >= nst && !(h->fused && h->fused_no_graph)) {
       r = capture_chunk(h);
+      if (r && h->fused) {
+        // the cooperative step kernel could not be captured: launch it directly from now on
+        cudaGetLastError();
+        h->fused_no_graph = true;
+        continue;
+      }
       if (r) return r;
       if (pending) {  // read the previous replay's events before this one records them again
         CK(cudaStreamSynchronize(h->stream));
@@ -909,7 +937,7 @@ VP_API int sim_step_batch(sim_handle *h, int32_t n_steps) {
       CK(cudaGraphLaunch(h->chunk, h->stream));
       h->step += nst;
       left -= nst;
-      pending = h->gtiming;
+      pending = h->gtiming && !h->fused;  // the one-kernel step has no separate pair launch to time
     } else {
       one_step(h);
       h->step += 1;
@@ -1474,6 +1502,102 @@ VP_API int sim_set_class_variants(sim_handle *h, const int32_t *variants, int32_
     h->chunk = nullptr;
   }
   return SIM_OK;
+}
+
+VP_API int sim_set_step_mode(sim_handle *h, int32_t mode) {
+  if (!h) return SIM_EINVAL;
+  if (mode != 0 && mode != 1) return fail(h, SIM_EINVAL, "step mode must be 0 (kernel per phase) or 1 (one kernel)");
+  h->fused = mode == 1;
+  if (h->chunk) {
+    cudaGraphExecDestroy(h->chunk);
+    h->chunk = nullptr;
+  }
+  return SIM_OK;
+}
+
+VP_API int32_t sim_step_mode(const sim_handle *h) { return h ? (h->fused ? 1 : 0) : SIM_EINVAL; }
+
+VP_API int sim_autotune_step(sim_handle *h, int32_t reps, int32_t *mode) {
+  int r = enter(h);
+  if (r) return r;
+  if (reps < 1) reps = 3;
+  const Dev &d = h->d;
+  const int nst = h->params.nstlist;
+  // the state to come back to: positions and velocities of every trial, the
+  // functional's bookkeeping, the step counter
+  size_t n = 0;
+  for (const auto &T : h->tinfo) n += (size_t)T.n_atoms;
+  double *saved = nullptr;
+  CK(cudaMalloc(&saved, sizeof(double) * 6 * std::max<size_t>(n, 1)));
+  {
+    size_t off = 0;
+    for (int t = 0; t < h->n_trials; ++t) {
+      const size_t m = (size_t)h->tinfo[t].n_atoms;
+      launch_gather_state(d, t, saved + 3 * off, saved + 3 * n + 3 * off, (int)m, h->stream);
+      off += m;
+    }
+  }
+  std::vector<TrialState> S(h->n_trials);
+  CK(cudaMemcpyAsync(S.data(), d.tstate, sizeof(TrialState) * h->n_trials, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  const long long step0 = h->step;
+  auto restore = [&]() -> int {
+    launch_scatter_state(d, -1, saved, saved + 3 * n, (int)n, h->stream);
+    // the functional's bookkeeping comes back; the cluster counts stay those
+    // of the current layout (the rebuild below starts from it)
+    std::vector<TrialState> cur(h->n_trials);
+    CK(cudaMemcpyAsync(cur.data(), d.tstate, sizeof(TrialState) * h->n_trials, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    for (int t = 0; t < h->n_trials; ++t) {
+      cur[t].zm = S[t].zm;
+      cur[t].Phi = S[t].Phi;
+    }
+    CK(cudaMemcpyAsync(d.tstate, cur.data(), sizeof(TrialState) * h->n_trials, cudaMemcpyHostToDevice, h->stream));
+    CK(cudaMemcpyAsync(d.step, &step0, sizeof(step0), cudaMemcpyHostToDevice, h->stream));
+    CK(cudaMemcpyAsync(d.cur_step, &step0, sizeof(step0), cudaMemcpyHostToDevice, h->stream));
+    h->step = step0;
+    const float half = 0.5f;
+    CK(cudaMemcpyAsync(d.kick, &half, sizeof(float), cudaMemcpyHostToDevice, h->stream));
+    CK(cudaMemsetAsync(d.fx, 0, sizeof(long long) * d.total_slots, h->stream));
+    CK(cudaMemsetAsync(d.fy, 0, sizeof(long long) * d.total_slots, h->stream));
+    CK(cudaMemsetAsync(d.fz, 0, sizeof(long long) * d.total_slots, h->stream));
+    size_t ncv = 0;
+    for (auto &T : h->tinfo) ncv += T.n_cv;
+    if (ncv) {
+      CK(cudaMemsetAsync(d.gx, 0, sizeof(long long) * ncv, h->stream));
+      CK(cudaMemsetAsync(d.gy, 0, sizeof(long long) * ncv, h->stream));
+      CK(cudaMemsetAsync(d.gz, 0, sizeof(long long) * ncv, h->stream));
+    }
+    forces(h, FIN_KEEP, -1);
+    CK(cudaStreamSynchronize(h->stream));
+    return check_flags(h);
+  };
+  float best = 3e38f;
+  int pick = h->fused ? 1 : 0;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  for (int m = 0; m < 2 && r == SIM_OK; ++m) {
+    r = sim_set_step_mode(h, m);
+    if (!r) r = sim_step_batch(h, nst);  // captures the chunk graph
+    if (!r) {
+      cudaEventRecord(e0, h->stream);
+      for (int k = 0; k < reps && !r; ++k) r = sim_step_batch(h, nst);
+      cudaEventRecord(e1, h->stream);
+      cudaEventSynchronize(e1);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (!r && ms < best) { best = ms; pick = m; }
+    }
+    if (!r) r = restore();
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(saved);
+  if (r) return r;
+  r = sim_set_step_mode(h, pick);
+  if (mode) *mode = pick;
+  return r;
 }
 
 VP_API int32_t sim_tune_classes(sim_handle *h, int32_t *info, int32_t cap) {

@@ -76,7 +76,9 @@ struct Dev {
                                        // cluster itself or mixed images (the pair kernels then apply the
                                        // pair masks); bit 31: some group from the 31st on does
   double *rec;                         // [n_trials * rec_cap * 5]: z, z_m, a, phi, Q
-  unsigned *pair_next;                 // work counter of the persistent pair kernel
+  unsigned *pair_next;                 // work counters: [0] the persistent pair kernel; [1] the
+                                       // one-kernel step's pair phase, [2] its CV phase
+  unsigned *bar;                       // [2] grid barrier of the one-kernel step: arrivals, generation
   int32_t n_sm;                        // multiprocessors of the device
 };
 
@@ -106,6 +108,23 @@ __device__ __forceinline__ void decide_rebuilds(const Dev &d, const SimConst &c,
 }
 
 enum UpdateMode { UPD_DRIFT = 0, UPD_FINAL = 1 };
+
+// shared memory of one warp's reaction-coordinate tile
+struct CvWarpShared {
+  unsigned short s_near[CV_T * CV_T];
+  float s_x[2 * CV_T][3];
+  // gradient of the tile's 64 atoms: each fixed-point contribution c splits
+  // into c >> 24 (signed) and its low 24 bits, summed in 32-bit shared
+  // atomics (native, unlike 64-bit ones); at most 32 contributions per entry
+  // keep both sums far from overflow, and (hi << 24) + lo is the exact sum
+  int s_ghi[2 * CV_T][3];
+  unsigned s_glo[2 * CV_T][3];
+};
+constexpr int CVFIN_THREADS = 1024;  // the finaliser's reduction width (virtual threads)
+struct CvfinShared {
+  double rz[CVFIN_THREADS], rq[CVFIN_THREADS];
+  bool last;
+};
 // FIN_STEP: a step (Phi accumulates, the step counter advances); FIN_INIT:
 // z_m = z; FIN_RESTORE: a new state (z and a from the stored z_m, the record
 // entry of the current step rewritten); FIN_KEEP: the same state again after a
@@ -150,5 +169,8 @@ void launch_extract_pairs(const Dev &d, int32_t list_cap, int32_t trial, int32_t
 void launch_philox_normals(uint64_t seed, unsigned long long step, uint32_t stream, int n, uint32_t *raw,
                            double *normals, cudaStream_t s);
 void launch_select(const Dev &d, double z_max, double *phi_out, int32_t *argmin_out, cudaStream_t s);
+// one MD step of every trial as one cooperative kernel (vp_step.cu)
+cudaError_t launch_step_fused(const Dev &d, const SimConst &c, float rl2_bbox, float half_skin2, int strict,
+                              cudaStream_t s);
 
 }  // namespace vp

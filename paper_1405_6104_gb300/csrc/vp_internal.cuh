@@ -30,6 +30,7 @@ constexpr int ERR_COL = 2;
 constexpr int ERR_NONFINITE = 4;
 constexpr int ERR_CAPACITY = 8;
 constexpr int ERR_SKIN = 16;
+constexpr int ERR_TIMEOUT = 32;        // a bounded grid barrier of the one-kernel step gave up
 
 // list entry (uint2):
 //   x = 4-atom j-cluster index (bits 0-24) | image shift (bits 25-30: nx+1,
@@ -130,6 +131,7 @@ struct SimConst {
   // skin/2 - 1e-5 nm (squared: trig2) from where its list was built
   int32_t nstlist, list_fixed;
   float trig2;
+  uint32_t spin_limit;        // polls of a grid barrier before it gives up (one-kernel step)
 };
 
 

@@ -14,15 +14,10 @@
 #include <type_traits>
 
 #include "vp_dev.cuh"
+#include "vp_pair_dev.cuh"
 
 namespace vp {
 
-// displacement x_p - x_self under the minimum image, with the image shift
-// subtracted from x_p first (exact when the two are within a box length)
-__device__ __forceinline__ float3 min_disp(float4 self, float4 other, float L, float iL) {
-  float nx = rintf((other.x - self.x) * iL), ny = rintf((other.y - self.y) * iL), nz = rintf((other.z - self.z) * iL);
-  return make_float3((other.x - L * nx) - self.x, (other.y - L * ny) - self.y, (other.z - L * nz) - self.z);
-}
 
 // force on one atom from its bonded terms (bonds: V = k/2 (r - r0)^2, angles
 // V = k/2 (theta - theta0)^2); eb/ea receive this atom's share of the energy
@@ -244,6 +239,7 @@ __global__ void __launch_bounds__(128, MINB) k_pair(Dev d, SimConst c, int only_
   }
 }
 
+
 // Force-only kernel (the hot path).  Per warp, shared memory holds the LJ
 // coefficients of its 8 i-atoms against every type (row a at a fixed stride,
 // so the pair loop addresses them with immediate offsets) and the 27 image
@@ -251,10 +247,6 @@ __global__ void __launch_bounds__(128, MINB) k_pair(Dev d, SimConst c, int only_
 // (0 or 1e30), so a masked pair falls outside the cut-off without any
 // per-pair bit test.  Arithmetic per pair: 3 FADD, 6 FMUL, 12 FFMA, 1 RSQ,
 // 1 LDS, 1 FSETP + FSEL.
-constexpr int PF_WARPS = 4;
-constexpr int SMALL_TYPES = 16;
-constexpr float MASK_PEN = 1.0e30f;
-
 // SHI: the i-atoms are read from shared memory (one broadcast LDS.128 per
 // pair) instead of being held in 32 registers, which lets more warps reside.
 // TS is the row stride of the per-warp LJ table (at least the number of types).
@@ -429,271 +421,27 @@ __global__ void __launch_bounds__(PF_WARPS * 32, MINB) k_pair_f(Dev d, SimConst 
 // (exactly the sum of -f*d: round-to-nearest is sign-symmetric); the j-force
 // sums even and odd i-atoms in two partials, as the scalar variants do, so
 // all variants give bit-identical forces.
+
+
 template <int MINB>
 __global__ void __launch_bounds__(PF_WARPS * 32, MINB) k_pair_f2(Dev d, SimConst c, unsigned *next, const int *clist,
                                                                    int n_items) {
-  constexpr int TS = SMALL_TYPES;
-  __shared__ float4 s_c4[PF_WARPS][CL / 2][TS];
-  __shared__ float4 s_sh[PF_WARPS][64];
-  __shared__ float4 s_ip[PF_WARPS][CL / 2][2];
-  __shared__ float s_red[PF_WARPS][3 * CL * 33];
-  const int wib = threadIdx.x >> 5;
+  __shared__ PairF2Shared sh;
   const int lane = threadIdx.x & 31;
   // persistent warps: each takes the next i-cluster from a counter until none
   // is left, so that short and long lists even out across the SMs
   for (;;) {
-  __syncwarp();  // the warp's tables of its previous cluster are no longer read
-  unsigned got = 0u;
-  if (lane == 0) got = atomicAdd(next, 1u);
-  const int item = (int)__shfl_sync(0xffffffffu, got, 0);
-  if (item >= n_items) return;
-  const int I = clist ? clist[item] : item;
-  const int t = d.clus_trial[I];
-  const TrialInfo T = d.tinfo[t];
-  if (I - T.clus0 >= d.tstate[t].n_clus) continue;
-  const float L = T.box, iL = T.inv_box;
-  const int g = lane >> 2, b = lane & 3;
-  const int NT = c.n_types;
-
-  if (lane < CL / 2) {
-    const float4 a0 = d.pos[I * CL + 2 * lane], a1 = d.pos[I * CL + 2 * lane + 1];
-    // negated coordinates: d = xj + (-xi) in one FADD2 (a packed operand has no negate modifier)
-    s_ip[wib][lane][0] = make_float4(-a0.x, -a1.x, -a0.y, -a1.y);
-    s_ip[wib][lane][1] = make_float4(-a0.z, -a1.z, a0.w, a1.w);
+    __syncwarp();  // the warp's tables of its previous cluster are no longer read
+    unsigned got = 0u;
+    if (lane == 0) got = atomicAdd(next, 1u);
+    const int item = (int)__shfl_sync(0xffffffffu, got, 0);
+    if (item >= n_items) return;
+    pair_cluster_f2(d, c, sh, clist ? clist[item] : item);
   }
-  for (int k = lane; k < (CL / 2) * NT; k += 32) {
-    const int p = k / NT, tj = k - p * NT;
-    const int t0 = d.type[I * CL + 2 * p], t1 = d.type[I * CL + 2 * p + 1];
-    const float2 c0 = d.ljtab[t0 * NT + tj], c1 = d.ljtab[t1 * NT + tj];
-    s_c4[wib][p][tj] = make_float4(c0.y, c1.y, -c0.x, -c1.x);
-  }
-  for (int k = lane; k < 64; k += 32) {
-    const int ix = (k & 3) - 1, iy = ((k >> 2) & 3) - 1, iz = ((k >> 4) & 3) - 1;
-    s_sh[wib][k] = make_float4(L * ix, L * iy, L * iz, 0.f);
-  }
-  __syncwarp();
-  float2 fx[CL / 2], fy[CL / 2], fz[CL / 2];
-#pragma unroll
-  for (int p = 0; p < CL / 2; ++p) fx[p] = fy[p] = fz[p] = make_float2(0.f, 0.f);
-  const float2 m2krf = make_float2(-c.two_krf, -c.two_krf);
-  const float rc2 = c.rc2;
-
-  const int n = d.list_n[I];
-  const uint2 *seg = d.list + (size_t)I * c.list_cap;
-  const uint32_t gd = d.gdirty[I];
-  // list entries are fetched two groups ahead; the j-atom itself at the top
-  // of its iteration (fewer live registers: a higher block count per SM hides
-  // that load better than a prefetch does)
-  uint2 ent = g < n ? seg[g] : d.idle_entry;
-  uint2 ent_n = 8 + g < n ? seg[8 + g] : d.idle_entry;
-  for (int e0 = 0; e0 < n; e0 += 8) {
-    const uint2 ent_nn = e0 + 16 + g < n ? seg[e0 + 16 + g] : d.idle_entry;
-    const int sj = (int)(ent.x & J_MASK) * CJ + b;
-    const float4 pj = d.pos[sj];
-    const int tj = d.type[sj];
-    const float4 shv = s_sh[wib][(ent.x >> J_BITS) & 63u];
-    const float xj = pj.x - shv.x, yj = pj.y - shv.y, zj = pj.z - shv.z, qj = pj.w;
-    const unsigned mb = ent.y >> b;
-    const bool exact = (ent.x & E_EXACT) != 0u;
-    const float4 *row = &s_c4[wib][0][tj];
-    float fjx, fjy, fjz;
-    // one image per entry; MASKED: the pair masks apply (a group with
-    // exclusions or the cluster itself); else the cut-off alone decides, which
-    // gives the same forces: a listed pair that failed the list rule is still
-    // beyond the cut-off (lists are rebuilt before any atom has moved skin/2)
-    auto one_image = [&](auto mtag) {
-      constexpr bool MASKED = decltype(mtag)::value;
-      const float2 xj2 = make_float2(xj, xj), yj2 = make_float2(yj, yj), zj2 = make_float2(zj, zj);
-      const float2 qj2 = make_float2(qj, qj);
-      float2 gx = make_float2(0.f, 0.f), gy = gx, gz = gx;
-#pragma unroll
-      for (int p = 0; p < CL / 2; ++p) {
-        const float4 i0 = s_ip[wib][p][0], i1 = s_ip[wib][p][1];
-        const float2 dx = __fadd2_rn(xj2, make_float2(i0.x, i0.y));
-        const float2 dy = __fadd2_rn(yj2, make_float2(i0.z, i0.w));
-        const float2 dz = __fadd2_rn(zj2, make_float2(i1.x, i1.y));
-        // the mask bit joins the cut-off test (the same forces as the penalty form)
-        const float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
-        const float2 rinv = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
-        const float2 rinv2 = __fmul2_rn(rinv, rinv);
-        const float2 rinv6 = __fmul2_rn(__fmul2_rn(rinv2, rinv2), rinv2);
-        const float4 cc = row[p * TS];
-        const float2 qq = __fmul2_rn(make_float2(i1.z, i1.w), qj2);
-        float2 tt = __ffma2_rn(make_float2(cc.x, cc.y), rinv6, make_float2(cc.z, cc.w));
-        tt = __fmul2_rn(tt, rinv6);
-        tt = __ffma2_rn(qq, rinv, tt);
-        tt = __fmul2_rn(tt, rinv2);
-        float2 f = __ffma2_rn(qq, m2krf, tt);
-        f.x = ((!MASKED || (mb & (1u << (8 * p)))) && r2.x < rc2) ? f.x : 0.0f;
-        f.y = ((!MASKED || (mb & (1u << (8 * p + 4)))) && r2.y < rc2) ? f.y : 0.0f;
-        fx[p] = __ffma2_rn(f, dx, fx[p]);
-        fy[p] = __ffma2_rn(f, dy, fy[p]);
-        fz[p] = __ffma2_rn(f, dz, fz[p]);
-        gx = __ffma2_rn(f, dx, gx);
-        gy = __ffma2_rn(f, dy, gy);
-        gz = __ffma2_rn(f, dz, gz);
-      }
-      fjx = gx.x + gx.y;
-      fjy = gy.x + gy.y;
-      fjz = gz.x + gz.y;
-    };
-    const bool masked = (gd >> min(e0 >> 3, 31)) & 1u;
-    if (!masked) {
-      one_image(std::false_type{});
-    } else if (!__any_sync(0xffffffffu, exact)) {
-      one_image(std::true_type{});
-    } else {
-      // some entry of this group needs pair-by-pair minimum images
-      float2 gx = make_float2(0.f, 0.f), gy = gx, gz = gx;
-#pragma unroll
-      for (int p = 0; p < CL / 2; ++p) {
-        const float4 i0 = s_ip[wib][p][0], i1 = s_ip[wib][p][1];
-        const float4 cc = row[p * TS];
-        float2 f2v, dx2, dy2, dz2;
-#pragma unroll
-        for (int hh = 0; hh < 2; ++hh) {
-          const float pen = (mb & (1u << (8 * p + 4 * hh))) ? 0.0f : MASK_PEN;
-          float dx = __fadd_rn(xj, hh ? i0.y : i0.x), dy = __fadd_rn(yj, hh ? i0.w : i0.z),
-                dz = __fadd_rn(zj, hh ? i1.y : i1.x);
-          if (exact) {
-            dx = __fmaf_rn(-L, rintf(__fmul_rn(dx, iL)), dx);
-            dy = __fmaf_rn(-L, rintf(__fmul_rn(dy, iL)), dy);
-            dz = __fmaf_rn(-L, rintf(__fmul_rn(dz, iL)), dz);
-          }
-          const float r2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmaf_rn(dx, dx, pen)));
-          const float rinv = rsqrtf(r2);
-          const float rinv2 = __fmul_rn(rinv, rinv);
-          const float rinv6 = __fmul_rn(__fmul_rn(rinv2, rinv2), rinv2);
-          const float qq = __fmul_rn(hh ? i1.w : i1.z, qj);
-          float tt = __fmaf_rn(hh ? cc.y : cc.x, rinv6, hh ? cc.w : cc.z);
-          tt = __fmul_rn(tt, rinv6);
-          tt = __fmaf_rn(qq, rinv, tt);
-          tt = __fmul_rn(tt, rinv2);
-          float f = __fmaf_rn(qq, -c.two_krf, tt);
-          f = r2 < rc2 ? f : 0.0f;
-          if (hh) { f2v.y = f; dx2.y = dx; dy2.y = dy; dz2.y = dz; }
-          else { f2v.x = f; dx2.x = dx; dy2.x = dy; dz2.x = dz; }
-        }
-        fx[p] = __ffma2_rn(f2v, dx2, fx[p]);
-        fy[p] = __ffma2_rn(f2v, dy2, fy[p]);
-        fz[p] = __ffma2_rn(f2v, dz2, fz[p]);
-        gx = __ffma2_rn(f2v, dx2, gx);
-        gy = __ffma2_rn(f2v, dy2, gy);
-        gz = __ffma2_rn(f2v, dz2, gz);
-      }
-      fjx = gx.x + gx.y;
-      fjy = gy.x + gy.y;
-      fjz = gz.x + gz.y;
-    }
-    if (fjx != 0.f || fjy != 0.f || fjz != 0.f) {
-      red_add(d.fx + sj, fx_from(fjx));
-      red_add(d.fy + sj, fx_from(fjy));
-      red_add(d.fz + sj, fx_from(fjz));
-    }
-    ent = ent_n;
-    ent_n = ent_nn;
-  }
-
-  float fi[CL][3];
-#pragma unroll
-  for (int p = 0; p < CL / 2; ++p) {
-    fi[2 * p][0] = -fx[p].x; fi[2 * p][1] = -fy[p].x; fi[2 * p][2] = -fz[p].x;
-    fi[2 * p + 1][0] = -fx[p].y; fi[2 * p + 1][1] = -fy[p].y; fi[2 * p + 1][2] = -fz[p].y;
-  }
-  float *r = s_red[wib];
-#pragma unroll
-  for (int a = 0; a < CL; ++a)
-#pragma unroll
-    for (int k = 0; k < 3; ++k) r[(3 * a + k) * 33 + lane] = fi[a][k];
-  __syncwarp();
-  if (lane < 3 * CL) {
-    float sum = 0.f;
-    for (int l = 0; l < 32; ++l) sum += r[lane * 33 + l];
-    const int a = lane / 3, comp = lane - 3 * a;
-    const long long val = fx_from(sum);
-    if (val != 0) red_add((comp == 0 ? d.fx : comp == 1 ? d.fy : d.fz) + I * CL + a, val);
-  }
-  }  // for each cluster
 }
-
-// Bonded forces, one thread per (trial, group of terms over at most 3 atoms;
-// a water's angle and bonds form one group): every term's forces are
-// converted to fixed point and summed per atom, exactly, so the group issues
-// one reduction per atom and component (exact action-reaction: a bond's
-// second atom and an angle's vertex take minus the others' forces).  The
-// arithmetic of a term is that of bonded_force for the bond's first atom and
-// for the angle's vertex.  A kernel of its own, beside the pair kernel: inside
-// the pair kernel's warps the per-atom term loops ran on 8 of 32 lanes behind
-// chains of dependent loads.
-__device__ __forceinline__ void add3(long long (&F)[3][3], int m, long long x, long long y, long long z) {
-#pragma unroll
-  for (int q = 0; q < 3; ++q)
-    if (q == m) { F[q][0] += x; F[q][1] += y; F[q][2] += z; }
-}
-
-__device__ __forceinline__ float4 pick3(const float4 (&p)[3], int m) { return m == 0 ? p[0] : m == 1 ? p[1] : p[2]; }
 
 __global__ void __launch_bounds__(256) k_bonded(Dev d) {
-  const int t = blockIdx.y;
-  const TrialInfo T = d.tinfo[t];
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= d.sys_nbg[T.sys]) return;
-  const BGroup G = d.bgrp[d.sys_bg0[T.sys] + k];
-  const float L = T.box, iL = T.inv_box;
-  int sl[3];
-  float4 p[3];
-#pragma unroll
-  for (int m = 0; m < 3; ++m) {
-    sl[m] = G.at[m] >= 0 ? d.slot_of[T.atom0 + G.at[m]] : -1;
-    p[m] = sl[m] >= 0 ? d.pos[sl[m]] : make_float4(0.f, 0.f, 0.f, 0.f);
-  }
-  long long F[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
-#pragma unroll
-  for (int q = 0; q < 3; ++q) {
-    if (q >= G.n) break;
-    const int code = G.code[q];
-    const float4 par = G.par[q];
-    const int li = (code >> 1) & 3, lj = (code >> 3) & 3, ll = (code >> 5) & 3;
-    const float4 pa = pick3(p, li), pb = pick3(p, lj);
-    if ((code & 1) == 0) {
-      // bond a-b, V = k/2 (r - r0)^2: the stretch in float-float (exact coordinate differences)
-      const float nx = rintf((pb.x - pa.x) * iL), ny = rintf((pb.y - pa.y) * iL), nz = rintf((pb.z - pa.z) * iL);
-      const ff dx = ff_diff(pb.x - L * nx, pa.x), dy = ff_diff(pb.y - L * ny, pa.y), dz = ff_diff(pb.z - L * nz, pa.z);
-      const ff r = ff_sqrt(ff_add(ff_add(ff_sqr(dx), ff_sqr(dy)), ff_sqr(dz)));
-      const float dr = ff_add_f(ff_add_f(r, -par.x), -par.z).hi;  // r - r0 with r0 in float-float
-      const float fs = par.y * dr / r.hi;  // force on a = +k dr (b - a)/r
-      const long long fx = fx_from(fs * dx.hi), fy = fx_from(fs * dy.hi), fz = fx_from(fs * dz.hi);
-      add3(F, li, fx, fy, fz);
-      add3(F, lj, -fx, -fy, -fz);
-    } else {
-      // angle a-b-c (vertex b), V = k/2 (theta - theta0)^2
-      const float4 pc = pick3(p, ll);
-      const float3 u = min_disp(pb, pa, L, iL), v = min_disp(pb, pc, L, iL);
-      const float uu = u.x * u.x + u.y * u.y + u.z * u.z, vv = v.x * v.x + v.y * v.y + v.z * v.z;
-      const float iuv = rsqrtf(uu * vv);
-      float cs = (u.x * v.x + u.y * v.y + u.z * v.z) * iuv;
-      cs = fminf(1.0f, fmaxf(-1.0f, cs));
-      const float dth = acosf(cs) - par.x;
-      const float sn = fmaxf(sqrtf(fmaxf(0.0f, 1.0f - cs * cs)), 1e-6f);
-      const float g = par.y * dth / sn;
-      const float iuu = 1.0f / uu, ivv = 1.0f / vv;
-      // forces on the ends: g d cos / d u and g d cos / d v
-      const long long ax = fx_from(g * (v.x * iuv - cs * u.x * iuu)), ay = fx_from(g * (v.y * iuv - cs * u.y * iuu)),
-                      az = fx_from(g * (v.z * iuv - cs * u.z * iuu));
-      const long long cx = fx_from(g * (u.x * iuv - cs * v.x * ivv)), cy = fx_from(g * (u.y * iuv - cs * v.y * ivv)),
-                      cz = fx_from(g * (u.z * iuv - cs * v.z * ivv));
-      add3(F, li, ax, ay, az);
-      add3(F, ll, cx, cy, cz);
-      add3(F, lj, -(ax + cx), -(ay + cy), -(az + cz));
-    }
-  }
-#pragma unroll
-  for (int m = 0; m < 3; ++m)
-    if (sl[m] >= 0) {
-      red_add(d.fx + sl[m], F[m][0]);
-      red_add(d.fy + sl[m], F[m][1]);
-      red_add(d.fz + sl[m], F[m][2]);
-    }
+  bonded_group(d, blockIdx.y, blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 void launch_bonded(const Dev &d, cudaStream_t s) {
