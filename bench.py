@@ -158,9 +158,10 @@ def make_batch(B, S, prep_steps: int, stream_ptr=0, rank: int = 0, world: int = 
     return s, p, seeds, batch
 
 
-def cpu_baseline(S, steps: int = 60):
+def cpu_baseline(S, steps: int = 60, one_core_steps: int = 0):
     """The FP64 oracle as it stands on the host cores: one trial of the same
-    11 040-atom system for a bounded number of MD steps."""
+    11 040-atom system for a bounded number of MD steps, on all cores and
+    (one_core_steps > 0) on one core."""
     import oracle as O
     s, p = S.plain_single(1)
     O.run(s, p, 1000, 1)  # build and warm
@@ -168,9 +169,21 @@ def cpu_baseline(S, steps: int = 60):
     r = O.run(s, p, 1000, steps)
     dt = time.perf_counter() - t0
     assert r["status"] == 0
-    return {"value": s.n_atoms * steps / dt, "unit": "atom-steps/s", "cores": O.num_threads(), "kind": "oracle",
-            "sample": f"1 trial x {steps} MD steps of the 11040-atom system (FP64, O(N^2) list rebuild every 10 steps)",
-            "seconds": dt}
+    out = {"value": s.n_atoms * steps / dt, "unit": "atom-steps/s", "cores": O.num_threads(), "kind": "oracle",
+           "sample": f"1 trial x {steps} MD steps of the 11040-atom system (FP64; its O(N^2) list rebuild at the "
+                     "displacement rule)", "seconds": dt}
+    if one_core_steps > 0:
+        all_cores = O.num_threads()
+        O.set_num_threads(1)
+        try:
+            t1 = time.perf_counter()
+            O.run(s, p, 1000, one_core_steps)
+            d1 = time.perf_counter() - t1
+        finally:
+            O.set_num_threads(all_cores)
+        out["one_core"] = {"value": s.n_atoms * one_core_steps / d1, "unit": "atom-steps/s", "cores": 1,
+                           "sample": f"1 trial x {one_core_steps} MD steps", "seconds": d1}
+    return out
 
 
 def run_reference(args):
@@ -332,7 +345,7 @@ def run_gpu(args):
     if rank == 0:
         with B.TrialBatch(s, p, [1], trial_seeds=seeds[:1]) as one:
             B.sim_autotune(one.h, 5, None)
-            plain_form = B.sim_autotune_step(one.h, 3)
+            plain_form, plain_forms_ms = B.sim_autotune_step(one.h, 3, times=True)
             ostream = torch.cuda.ExternalStream(one.stream)
             for _ in range(args.warmup):
                 one.step(nst)
@@ -348,6 +361,8 @@ def run_gpu(args):
             plain = {"value": pv, "unit": "atom-steps/s",
                      "workload": f"1 trial x {s.n_atoms} atoms, same kernels, {n_plain} x {nst} MD steps",
                      "step_form": "one cooperative kernel per step" if plain_form else "kernel per phase, graph replays",
+                     "ms_per_md_step_by_form": {"kernel per phase": plain_forms_ms[0],
+                                                "one kernel": plain_forms_ms[1]},
                      "batching_speedup": value / world / pv}
 
     if rank == 0:
@@ -362,7 +377,7 @@ def run_gpu(args):
         step_s = ms_per_step * 1e-3 / nst
         hbm_achieved = atoms * BYTES_PER_ATOM_STEP / step_s / 1e9
         try:
-            cb = cpu_baseline(S)
+            cb = cpu_baseline(S, one_core_steps=10)
         except Exception as exc:  # the baseline must not sink the GPU line
             cb = {"value": None, "unit": "atom-steps/s", "cores": None, "kind": "oracle", "sample": f"failed: {exc}"}
         line = {
@@ -504,7 +519,7 @@ def run_adjoint(args):
     n_frames, every = 500, 50
     with B.TrialBatch(s, p, [1], trial_seeds=[3]) as b:
         B.sim_autotune(b.h, 3, None)
-        fwd_form = B.sim_autotune_step(b.h, 2)
+        fwd_form, fwd_forms_ms = B.sim_autotune_step(b.h, 2, times=True)
         stream = torch.cuda.ExternalStream(b.stream)
         for _ in range(args.warmup):
             trajectory_adjoint(b, 0, n_frames, every=every)
@@ -558,7 +573,8 @@ def run_adjoint(args):
         "config": {"workload": f"30 000 atoms (1800-atom solute, 9400 waters), {n_frames} frames (1 per step), "
                                f"checkpoints every {every} steps, k_R 5", "phi": float(phi),
                    "grad_max": float(np.abs(G).max()),
-                   "forward_step_form": "one cooperative kernel per step" if fwd_form else "kernel per phase"},
+                   "forward_step_form": "one cooperative kernel per step" if fwd_form else "kernel per phase",
+                   "forward_ms_per_md_step_by_form": {"kernel per phase": fwd_forms_ms[0], "one kernel": fwd_forms_ms[1]}},
         "wall_s_per_step": wall / args.steps,
         "md_kernels_ms_per_step": md_ms,
         "md_kernel_share": md_ms / (t_kt * 1e3),

@@ -319,12 +319,13 @@ int sim_set_variants(sim_handle *h, int32_t pair_variant, int32_t cv_variant);
  * for fault-injection tests), for batches too small to fill the GPU.  Both
  * forms give bit-identical states.  SIM_EINVAL for another mode.
  * sim_step_mode returns the current form.  sim_autotune_step times reps
- * chunks of nstlist steps in each form, keeps the faster (*mode, may be NULL)
+ * chunks of nstlist steps in each form, keeps the faster (*mode, may be NULL;
+ * ms_per_step[2], may be NULL, receives both forms' milliseconds per step)
  * and restores the state it started from (positions, velocities, z_m, Phi,
  * step counter; the lists are rebuilt). */
 int sim_set_step_mode(sim_handle *h, int32_t mode);
 int32_t sim_step_mode(const sim_handle *h);
-int sim_autotune_step(sim_handle *h, int32_t reps, int32_t *mode);
+int sim_autotune_step(sim_handle *h, int32_t reps, int32_t *mode, double *ms_per_step);
 
 /* Kernel timing.  on = 1: the next sim_step_batch calls launch kernels
  * directly and time each launch with CUDA events on the library stream.

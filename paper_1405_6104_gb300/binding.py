@@ -103,7 +103,7 @@ _SIGS = {
     "sim_set_class_variants": ([C.c_void_p, C.c_void_p, C.c_int32], C.c_int),
     "sim_set_step_mode": ([C.c_void_p, C.c_int32], C.c_int),
     "sim_step_mode": ([C.c_void_p], C.c_int32),
-    "sim_autotune_step": ([C.c_void_p, C.c_int32, C.c_void_p], C.c_int),
+    "sim_autotune_step": ([C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p], C.c_int),
     "sim_kernel_times": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32], C.c_int),
     "sim_philox_normals": ([C.c_uint64, C.c_int64, C.c_uint32, C.c_int32, C.c_void_p, C.c_void_p], C.c_int),
     "cv_eval_noalloc": ([C.c_void_p, C.c_void_p, C.c_int32, C.c_double, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
@@ -405,11 +405,13 @@ def sim_step_mode(h) -> int:
     return int(load().sim_step_mode(h))
 
 
-def sim_autotune_step(h, reps: int = 3) -> int:
-    """Times both step forms on this batch, keeps the faster; the state is restored."""
+def sim_autotune_step(h, reps: int = 3, times: bool = False):
+    """Times both step forms on this batch, keeps the faster; the state is
+    restored.  Returns the form (and, with times, both forms' ms per step)."""
     m = C.c_int32(0)
-    _check(h, load().sim_autotune_step(h, int(reps), C.byref(m)))
-    return int(m.value)
+    ms = np.full(2, np.nan)
+    _check(h, load().sim_autotune_step(h, int(reps), C.byref(m), ms.ctypes.data))
+    return (int(m.value), [float(x) for x in ms]) if times else int(m.value)
 
 
 def sim_set_timing(h, on):

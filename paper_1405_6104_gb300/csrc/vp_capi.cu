@@ -1517,7 +1517,7 @@ VP_API int sim_set_step_mode(sim_handle *h, int32_t mode) {
 
 VP_API int32_t sim_step_mode(const sim_handle *h) { return h ? (h->fused ? 1 : 0) : SIM_EINVAL; }
 
-VP_API int sim_autotune_step(sim_handle *h, int32_t reps, int32_t *mode) {
+VP_API int sim_autotune_step(sim_handle *h, int32_t reps, int32_t *mode, double *ms_per_step) {
   int r = enter(h);
   if (r) return r;
   if (reps < 1) reps = 3;
@@ -1588,6 +1588,7 @@ VP_API int sim_autotune_step(sim_handle *h, int32_t reps, int32_t *mode) {
       float ms = 0.f;
       cudaEventElapsedTime(&ms, e0, e1);
       if (!r && ms < best) { best = ms; pick = m; }
+      if (!r && ms_per_step) ms_per_step[m] = ms / ((double)reps * nst);
     }
     if (!r) r = restore();
   }

@@ -77,7 +77,7 @@ struct Dev {
                                        // pair masks); bit 31: some group from the 31st on does
   double *rec;                         // [n_trials * rec_cap * 5]: z, z_m, a, phi, Q
   unsigned *pair_next;                 // work counters: [0] the persistent pair kernel; [1] the
-                                       // one-kernel step's pair phase, [2] its CV phase
+                                       // one-kernel step's forces phase; [2] spare
   unsigned *bar;                       // [2] grid barrier of the one-kernel step: arrivals, generation
   int32_t n_sm;                        // multiprocessors of the device
 };

@@ -10,6 +10,8 @@
 // occupancy of this kernel), so a grid barrier cannot deadlock; still every
 // barrier polls a bounded number of times and, if it gives up, records
 // ERR_TIMEOUT and ends the kernel (the host reports SIM_ETIMEOUT).
+#include <algorithm>
+
 #include "vp_cv_dev.cuh"
 #include "vp_dev.cuh"
 #include "vp_pair_dev.cuh"
@@ -22,10 +24,14 @@ constexpr int STEP_THREADS = PF_WARPS * 32;
 static_assert(STEP_THREADS == LIST_WARPS * 32, "the list phase assumes one warp per cluster in 4-warp blocks");
 
 union StepShared {
-  PairF2Shared pair;
+  // the forces phase: a warp works on reaction-coordinate tiles and on pair
+  // clusters in any order, so both have their own tables
+  struct {
+    PairF2Shared pair;
+    CvWarpShared cv[PF_WARPS];
+  } force;
   ListShared list;
   ColsortShared colsort;
-  CvWarpShared cv[PF_WARPS];
   CvfinShared cvfin;
   struct {
     int a[STEP_THREADS], c[STEP_THREADS];
@@ -78,14 +84,10 @@ __global__ void __launch_bounds__(STEP_THREADS, MINB)
   __shared__ int s_ok;
   const unsigned limit = c.spin_limit;
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  const int gthreads = gridDim.x * STEP_THREADS;
 
   // ---- update (B-A-O-A of Eq. Lang); the work counters of later phases start at 0 ----
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    d.pair_next[1] = 0u;
-    d.pair_next[2] = 0u;
-  }
-  for (int slot = blockIdx.x * STEP_THREADS + threadIdx.x; slot < d.total_slots; slot += gthreads)
+  if (blockIdx.x == 0 && threadIdx.x == 0) d.pair_next[1] = 0u;
+  for (int slot = blockIdx.x * STEP_THREADS + threadIdx.x; slot < d.total_slots; slot += gridDim.x * STEP_THREADS)
     update_slot<UPD_DRIFT>(d, c, slot);
   if (!grid_sync(d.bar, d.err, limit, &s_ok)) return;
 
@@ -128,26 +130,30 @@ __global__ void __launch_bounds__(STEP_THREADS, MINB)
     if (!grid_sync(d.bar, d.err, limit, &s_ok)) return;
   }
 
-  // ---- forces: nonbonded pairs, reaction coordinate, bonded terms ----
-  for (;;) {
-    __syncwarp();
-    unsigned got = 0u;
-    if (lane == 0) got = atomicAdd(d.pair_next + 1, 1u);
-    const int I = (int)__shfl_sync(0xffffffffu, got, 0);
-    if (I >= d.total_clus) break;
-    pair_cluster_f2(d, c, sh.pair, I);
+  // ---- forces: one queue of warp items, the longest first: reaction-
+  // coordinate tiles (costliest first), pair clusters, then the bonded
+  // groups 32 at a time (a lane each), so that the short items fill in
+  // around the long ones ----
+  {
+    const int n_cv = d.total_work, n_pair = d.total_clus;
+    const int n_bond = (d.n_trials * d.max_nbg + 31) / 32;
+    for (;;) {
+      __syncwarp();
+      unsigned got = 0u;
+      if (lane == 0) got = atomicAdd(d.pair_next + 1, 1u);
+      const int item = (int)__shfl_sync(0xffffffffu, got, 0);
+      if (item < n_cv) {
+        cv_tile(d, c, sh.force.cv[wib], item);
+      } else if (item < n_cv + n_pair) {
+        pair_cluster_f2(d, c, sh.force.pair, item - n_cv);
+      } else if (item < n_cv + n_pair + n_bond) {
+        const int k = (item - n_cv - n_pair) * 32 + lane;
+        if (k < d.n_trials * d.max_nbg) bonded_group(d, k / d.max_nbg, k % d.max_nbg);
+      } else {
+        break;
+      }
+    }
   }
-  __syncthreads();  // the block's pair tables are no longer read
-  for (;;) {
-    __syncwarp();
-    unsigned got = 0u;
-    if (lane == 0) got = atomicAdd(d.pair_next + 2, 1u);
-    const int wq = (int)__shfl_sync(0xffffffffu, got, 0);
-    if (wq >= d.total_work) break;
-    cv_tile(d, c, sh.cv[wib], wq);
-  }
-  for (int k = blockIdx.x * STEP_THREADS + threadIdx.x; k < d.n_trials * d.max_nbg; k += gthreads)
-    bonded_group(d, k / d.max_nbg, k % d.max_nbg);
   if (!grid_sync(d.bar, d.err, limit, &s_ok)) return;
 
   // ---- per trial: z, the ratchet, Phi; the last trial advances the step ----
@@ -166,8 +172,11 @@ cudaError_t launch_step_fused(const Dev &d, const SimConst &c, float rl2_bbox, f
     per_sm = v;
   }
   if (per_sm < 1) return cudaErrorLaunchOutOfResources;
+  // no more blocks than the pair phase has four-warp shares of i-clusters:
+  // a small batch then has fewer blocks to gather at each barrier
+  const long long shares = ((long long)d.total_clus + PF_WARPS - 1) / PF_WARPS;
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((unsigned)(d.n_sm * per_sm));
+  cfg.gridDim = dim3((unsigned)std::max(1LL, std::min((long long)d.n_sm * per_sm, shares)));
   cfg.blockDim = dim3(STEP_THREADS);
   cfg.dynamicSmemBytes = 0;
   cfg.stream = s;
