@@ -37,9 +37,9 @@ FLOPS_PER_PAIR = 35.0                # LJ + reaction field, FP32
 # dram__bytes_write.sum of one ncu capture, variant 8) and the sources it was
 # taken on (the kernel and its headers): reported as roofline.traffic only
 # while those sources are unchanged
-PAIR_TRAFFIC = {"bytes": 141.665792e6 + 10.504192e6, "variant": 8,
-                "sources": ["vp_pair.cu", "vp_internal.cuh", "vp_dev.cuh"],
-                "source_sha256": "1e8a3e483a10d632845a985bb0aaf685aa7131c271bae3b8a5ca738c058c8870"}
+PAIR_TRAFFIC = {"bytes": 141.751296e6 + 9.755904e6, "variant": 8,
+                "sources": ["vp_pair.cu", "vp_pair_dev.cuh", "vp_internal.cuh", "vp_dev.cuh"],
+                "source_sha256": "d80a703dc8204e290146b0510c3261261419da21a66037dbcb3a2fdce7db7587"}
 
 
 def pair_traffic():
@@ -297,6 +297,15 @@ def run_gpu(args):
     B.sim_set_timing(batch.h, False)
     clk = clocks.stop(t_begin, t_end) if clocks else None
 
+    # the method's selection over every rank's trials, on the functional
+    # accumulated since the start (warm-up, timed region, kernel-timing pass):
+    # one double per trial gathered on the host
+    from paper_1405_6104_gb300.shard import global_selection
+    phi_loc, _ = batch.bias_functional()
+    sel_trial, sel_phi = global_selection(phi_loc, batch.global_trials)
+    sel_steps = (args.warmup + args.steps + kt_steps) * nst
+    phi_all = np.asarray(phi_loc, np.float64)
+
     # end to end through the C ABI with host buffers: per step the state of
     # every trial is uploaded from pinned memory, nstlist steps are taken and
     # the functional plus the selected trial are read back
@@ -332,11 +341,6 @@ def run_gpu(args):
         "trial_rebuilds": rb, "trial_steps": trial_steps,
         "mean_steps_between_rebuilds": round(trial_steps / max(rb, 1), 2),
         "displacement_triggered": diag1["displacement_rebuilds"] - diag0["displacement_rebuilds"]}
-    # the method's selection over every rank's trials: one double per trial
-    # gathered on the host (outside the timed region)
-    from paper_1405_6104_gb300.shard import global_selection
-    phi_loc, _ = batch.bias_functional()
-    sel_trial, sel_phi = global_selection(phi_loc, batch.global_trials)
     batch.close()
 
     # plain: one trial of the same system on the same kernels (graph replay),
@@ -408,7 +412,9 @@ def run_gpu(args):
             "gpu_launches": int(round(args.steps * sum(v[1] for v in kt.values()) / kt_steps)),
             "clocks": clk,
             "diagnostics": diag,
-            "selection": {"trial": sel_trial, "phi": sel_phi, "over_trials": n_trials * world},
+            "selection": {"trial": sel_trial, "phi": sel_phi, "over_trials": n_trials * world,
+                          "md_steps": sel_steps,
+                          "phi_quartiles_rank0": [float(x) for x in np.percentile(phi_all, [0, 25, 50, 75, 100])]},
         }
         print(json.dumps(line))
     if world > 1:
@@ -708,19 +714,44 @@ def run_uneven(args):
     per nm^3), one trial each, 5 000 MD steps (500 bench steps of 10) after a
     relaxation; launch shapes from the autotuner, chosen per size class."""
     import torch
+    import torch.distributed as dist
     rank, world, local = rank_info()
     torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
     import __graft_entry__
+    if world > 1:  # one rank per node compiles
+        if local == 0:
+            __graft_entry__.build()
+        dist.barrier()
     __graft_entry__.build()
     from paper_1405_6104_gb300 import binding as B
     from paper_1405_6104_gb300 import systems as S
+    from paper_1405_6104_gb300.shard import shard_by_cost
     steps = args.steps if args.steps is not None else 500
-    systems, p = S.uneven_32(2)
+    all_systems, p = S.uneven_32(2)
+    nst = p.nstlist
+    atoms_all = int(sum(s.n_atoms for s in all_systems))
+    # a fixed ensemble split over the ranks by its cost (atoms x steps): strong scaling
+    mine = shard_by_cost([s.n_atoms * steps * nst for s in all_systems], world, rank)
+    systems = [all_systems[k] for k in mine]
     if args.prep_steps > 0:
         systems = equilibrate_batch(B, S, systems, p, min(args.prep_steps, 1000))
     atoms = int(sum(s.n_atoms for s in systems))
-    nst = p.nstlist
-    seeds = [2000 + k for k in range(len(systems))]
+    seeds = [2000 + int(k) for k in mine]
+
+    def max_over_ranks(x: float) -> float:
+        if world == 1:
+            return x
+        t = torch.tensor([x], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
     with B.TrialBatch(systems, p, [1] * len(systems), trial_seeds=seeds) as b:
         tuned = B.sim_autotune(b.h, 5, None)
         classes = B.sim_tune_classes(b.h)
@@ -732,9 +763,12 @@ def run_uneven(args):
         torch.cuda.synchronize()
         B.sim_kernel_times(b.h)
         diag0 = B.sim_diagnostics(b.h)
+        barrier()
         t_begin = time.time()
         ms = _timed_batch(B, b, steps, nst, stream)
+        barrier()
         t_end = time.time()
+        ms = max_over_ranks(ms)
         diag1 = B.sim_diagnostics(b.h)
         pair_ms, pair_n = B.sim_kernel_times(b.h).get("pair_in_graph", (float("nan"), 0))
         B.sim_set_timing(b.h, 0)
@@ -744,19 +778,26 @@ def run_uneven(args):
         P = np.concatenate([b.get_state(k)[0] for k in range(len(systems))])
         V = np.concatenate([b.get_state(k)[1] for k in range(len(systems))])
         e2e_calls = 10
+        barrier()
         t0 = time.perf_counter()
         for _ in range(e2e_calls):
             b.set_state(-1, P, V)
             b.step(nst)
             phi_e, _ = b.bias_functional()
-        t1 = time.perf_counter()
+        t1 = t0 + max_over_ranks(time.perf_counter() - t0)
         B.sim_set_timing(b.h, 1)
         B.sim_kernel_times(b.h)
         for _ in range(3):
             b.step(nst)
         kt = B.sim_kernel_times(b.h)
         B.sim_set_timing(b.h, 0)
-    value = atoms * nst * steps / (ms * 1e-3)
+    value = atoms_all * nst * steps / (ms * 1e-3)
+    from paper_1405_6104_gb300.shard import global_selection
+    best, best_phi = global_selection(phi, np.asarray(mine, np.int64))
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return 0
     pk, src = peaks()
     sm_mhz = pk.get("sm_max_mhz", 2070.0)
     fp32_peak = 152 * 128 * 2 * sm_mhz * 1e6
@@ -764,18 +805,20 @@ def run_uneven(args):
     flops = atoms * PAIRS_PER_ATOM_STEP * FLOPS_PER_PAIR  # the same water density in every system
     # the oracle on the host cores: a bounded sample (the smallest system, a few steps)
     import oracle as O
-    small = min(range(len(systems)), key=lambda k: systems[k].n_atoms)
-    O.run(systems[small], p, seeds[small], 1)
+    small = min(range(len(all_systems)), key=lambda k: all_systems[k].n_atoms)
+    O.run(all_systems[small], p, 2000 + small, 1)
     tc = time.perf_counter()
-    r = O.run(systems[small], p, seeds[small], 20)
+    O.run(all_systems[small], p, 2000 + small, 20)
     t_or = time.perf_counter() - tc
     line = {
-        "metric": METRIC, "value": value, "unit": "atom-steps/s", "n_gpus": 1, "steps": steps,
-        "warmup": args.warmup, "ms_per_step": ms / steps, "higher_is_better": True, "scaling": "weak",
+        "metric": METRIC, "value": value, "unit": "atom-steps/s", "n_gpus": world, "steps": steps,
+        "warmup": args.warmup, "ms_per_step": ms / steps, "higher_is_better": True,
+        "scaling": "strong" if world > 1 else "weak",
         "vs_baseline": None, "dtype": "f32+i64-fixed+ff-cv", "data": "synthetic",
-        "config": {"workload": f"uneven batch: 32 systems of {min(s.n_atoms for s in systems)} to "
-                               f"{max(s.n_atoms for s in systems)} atoms ({atoms} in all), one trial each, "
+        "config": {"workload": f"uneven batch: 32 systems of {min(s.n_atoms for s in all_systems)} to "
+                               f"{max(s.n_atoms for s in all_systems)} atoms ({atoms_all} in all), one trial each, "
                                f"{steps * nst} MD steps timed", "md_steps_per_bench_step": nst,
+                   "parallelism": f"trials sharded over {world} rank(s) by atoms x steps",
                    "start": f"generated, relaxed {min(args.prep_steps, 1000)} steps at gamma 20/ps (untimed)",
                    "autotuned": {"pair_variant": tuned[0], "cv_variant": tuned[1], "size_classes": classes},
                    "l2": "working set > L2"},
@@ -786,18 +829,24 @@ def run_uneven(args):
                      "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz",
                      "work": f"{PAIRS_PER_ATOM_STEP:.0f} half pairs x {FLOPS_PER_PAIR:.0f} flops per atom-step"},
         "kernel_ms": {k: v[0] / v[1] for k, v in kt.items() if v[1] > 0},
-        "cpu_baseline": {"value": systems[small].n_atoms * 20 / t_or, "unit": "atom-steps/s", "cores": O.num_threads(),
-                         "kind": "oracle", "sample": f"the smallest system ({systems[small].n_atoms} atoms), 20 MD steps"},
-        "e2e": {"value": atoms * nst * e2e_calls / (t1 - t0), "unit": "atom-steps/s",
-                "h2d_bytes_per_step": int(P.nbytes + V.nbytes), "d2h_bytes_per_step": int(phi_e.nbytes + 8)},
+        "cpu_baseline": {"value": all_systems[small].n_atoms * 20 / t_or, "unit": "atom-steps/s",
+                         "cores": O.num_threads(), "kind": "oracle",
+                         "sample": f"the smallest system ({all_systems[small].n_atoms} atoms), 20 MD steps"},
+        "e2e": {"value": atoms_all * nst * e2e_calls / (t1 - t0), "unit": "atom-steps/s",
+                "h2d_bytes_per_step": int(P.nbytes + V.nbytes) * atoms_all // atoms,
+                "d2h_bytes_per_step": int(phi_e.nbytes + 8) * atoms_all // atoms if world == 1 else
+                8 * len(all_systems) + 8 * world},
         "gpu_launches": int(round(steps * sum(v[1] for v in kt.values()) / 3)),
         "clocks": clk,
         "diagnostics": {"skin_violations": diag1["skin_violations"] - diag0["skin_violations"],
                         "trial_rebuilds": diag1["trial_rebuilds"] - diag0["trial_rebuilds"],
                         "trial_steps": len(systems) * nst * steps},
-        "selection": {"trial": int(best), "phi": float(phi[best]), "phi_per_trial": [float(x) for x in phi]},
+        "selection": {"trial": int(best), "phi": float(best_phi),
+                      "phi_per_trial": [float(x) for x in phi] if world == 1 else None},
     }
     print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
     return 0
 
 
