@@ -199,12 +199,11 @@ int harvest_graph_timers(sim_handle *h) {
   return SIM_OK;
 }
 
-// cell binning and the spatial sort (the new atom slots)
-void rebuild_cols(sim_handle *h) {
+// which trials rebuild, their cell binning and the spatial sort (the new
+// atom slots); forced_only: the trials with a forced request alone
+void rebuild_cols(sim_handle *h, bool forced_only) {
   cudaStream_t s = h->stream;
-  timed(h, "bin", [&] { launch_bin(h->d, h->c, h->half_skin2, h->strict_skin, s); });
-  timed(h, "colscan", [&] { launch_colscan(h->d, h->c, s); });
-  timed(h, "colfill", [&] { launch_colfill(h->d, s); });
+  timed(h, "front", [&] { launch_front(h->d, h->c, h->half_skin2, h->strict_skin, forced_only, s); });
   timed(h, "colsort", [&] { launch_colsort(h->d, s); });
 }
 
@@ -271,8 +270,8 @@ constexpr int NO_REQUEST = -2;  // forces(): no forced list rebuild
 // nothing they read, and pair and bonded forces meet only in
 // order-independent fixed-point sums, so both orders give bit-identical states.
 void forces(sim_handle *h, FinMode mode, int request) {
-  if (request != NO_REQUEST) launch_rebuild_request(h->d, h->c, request, h->stream);
-  rebuild_cols(h);
+  if (request != NO_REQUEST) launch_rebuild_request(h->d, request, h->stream);
+  rebuild_cols(h, request != NO_REQUEST);
   if (h->side && !h->timing) {
     cudaEventRecord(h->ev_fork, h->stream);
     cudaStreamWaitEvent(h->side, h->ev_fork, 0);
@@ -1110,8 +1109,7 @@ VP_API int sim_potential_device(sim_handle *h, const double *d_pos, double *d_en
   CK(cudaMemsetAsync(d.fz, 0, sizeof(long long) * d.total_slots, s));
   CK(cudaMemsetAsync(d.energy, 0, sizeof(long long) * 5 * (size_t)h->n_trials, s));
   launch_scatter_positions(d, h->c, d_pos, n, s);
-  launch_decide(d, h->c, s);
-  rebuild_cols(h);
+  rebuild_cols(h, false);
   rebuild_list(h);
   launch_pair_hot(h, d, s);
   launch_bonded(d, s);

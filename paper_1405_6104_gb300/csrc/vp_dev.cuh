@@ -82,29 +82,32 @@ struct Dev {
   int32_t n_sm;                        // multiprocessors of the device
 };
 
-// Which trials rebuild their lists in step n (executed by one whole block,
-// in a kernel of its own after the update kernel): a displacement or forced
-// request for this step, or the longest interval reached (fixed-interval
-// lists: steps that are multiples of nstlist); forced_only: the forced
-// requests alone (a new state between steps).  The chosen trials go to
-// rb_list.
+// whether trial t rebuilds its list in step n: a forced request, or (unless
+// forced_only) a displacement request, or nstlist steps since its last
+// rebuild (with fixed intervals: every nstlist-th step)
+__device__ __forceinline__ bool trial_due(const Dev &d, const SimConst &c, int t, unsigned long long n,
+                                          bool forced_only) {
+  const uint32_t n32 = (uint32_t)n;
+  if (d.rb[d.n_trials + t] == n32) return true;
+  if (forced_only) return false;
+  if (d.rb[t] == n32) return true;
+  if (c.list_fixed) return n % (unsigned long long)c.nstlist == 0ull;
+  return n32 - d.last_rb[t] >= (uint32_t)c.nstlist;
+}
+
+// Which trials rebuild their lists in step n (executed by one whole block:
+// block 0 of the rebuild front kernel, or of the one-kernel step): the
+// trials for which trial_due holds go to rb_list, which the later rebuild
+// kernels walk.
 __device__ __forceinline__ void decide_rebuilds(const Dev &d, const SimConst &c, unsigned long long n,
                                                 bool forced_only) {
-  const uint32_t n32 = (uint32_t)n;
   if (threadIdx.x == 0) {
     d.rb_cnt[0] = 0u;
     d.rb_cnt[1] = 0u;
   }
   __syncthreads();
-  for (int t = threadIdx.x; t < d.n_trials; t += blockDim.x) {
-    bool go = d.rb[d.n_trials + t] == n32;
-    if (!forced_only && !go) {
-      if (d.rb[t] == n32) go = true;
-      else if (c.list_fixed) go = n % (unsigned long long)c.nstlist == 0ull;
-      else go = n32 - d.last_rb[t] >= (uint32_t)c.nstlist;
-    }
-    if (go) d.rb_list[atomicAdd(d.rb_cnt, 1u)] = t;
-  }
+  for (int t = threadIdx.x; t < d.n_trials; t += blockDim.x)
+    if (trial_due(d, c, t, n, forced_only)) d.rb_list[atomicAdd(d.rb_cnt, 1u)] = t;
 }
 
 enum UpdateMode { UPD_DRIFT = 0, UPD_FINAL = 1 };
@@ -132,10 +135,12 @@ struct CvfinShared {
 enum FinMode { FIN_STEP = 0, FIN_INIT = 1, FIN_RESTORE = 2, FIN_KEEP = 3 };
 
 // rebuild (vp_rebuild.cu)
-void launch_rebuild_request(const Dev &d, const SimConst &c, int32_t trial, cudaStream_t s);
-void launch_bin(const Dev &d, const SimConst &c, float half_skin2, int strict_skin, cudaStream_t s);
-void launch_colscan(const Dev &d, const SimConst &c, cudaStream_t s);
-void launch_colfill(const Dev &d, cudaStream_t s);
+// a forced rebuild of one trial (trial >= 0) or of all in the step held now
+void launch_rebuild_request(const Dev &d, int32_t trial, cudaStream_t s);
+// which trials rebuild (forced_only: those with a forced request), then
+// binning, column scans and bucket fills of those trials
+void launch_front(const Dev &d, const SimConst &c, float half_skin2, int strict_skin, bool forced_only,
+                  cudaStream_t s);
 void launch_colsort(const Dev &d, cudaStream_t s);
 void launch_list(const Dev &d, const SimConst &c, float rl2_bbox, cudaStream_t s);
 void launch_list_positions(const Dev &d, int32_t trial, double *out, int32_t n, cudaStream_t s);
@@ -163,7 +168,6 @@ void launch_forces_out(const Dev &d, const SimConst &c, int32_t trial, double *o
 void launch_kinetic(const Dev &d, int32_t trial, cudaStream_t s);
 void launch_scatter_positions(const Dev &d, const SimConst &c, const double *pos, int32_t n, cudaStream_t s);
 void launch_potential_out(const Dev &d, double *energy, double *forces, int32_t n, cudaStream_t s);
-void launch_decide(const Dev &d, const SimConst &c, cudaStream_t s);
 void launch_extract_pairs(const Dev &d, int32_t list_cap, int32_t trial, int32_t n_clus, int32_t *pairs,
                           long long cap, unsigned long long *count, cudaStream_t s);
 void launch_philox_normals(uint64_t seed, unsigned long long step, uint32_t stream, int n, uint32_t *raw,

@@ -2,9 +2,10 @@
 // cluster-pair Verlet list of the trials whose list is due.
 //
 // Every kernel here runs in every step and works only on the trials whose
-// list is due in that step: the update kernel's last block (or, for a new
-// state, k_rebuild_request) lists them in d.rb_list, and the kernels take
-// their work items (slot chunks, columns, clusters) from that list.  A trial's list is due when one of its atoms has moved
+// list is due in that step: the front kernel (one block per trial) decides,
+// bins, scans and fills per trial and lists the rebuilding trials in
+// d.rb_list; the later kernels take their work items (columns, slot chunks,
+// clusters) from that list.  A trial's list is due when one of its atoms has moved
 // farther than skin/2 - 1e-5 nm from where its list was built (the update
 // kernel requests it), after nstlist steps, or on request from the host
 // (creation, a new state).  The first rule keeps every pair closer than r_cut
@@ -30,13 +31,11 @@ namespace vp {
 // binning: wrap into the box, pick the column, count, skin check
 // ---------------------------------------------------------------------------
 // forced rebuild of one trial (trial >= 0) or of all, in the step held now
-// (one block)
-__global__ void k_rebuild_request(Dev d, SimConst c, int trial) {
+// (the front kernel that follows rebuilds exactly those trials)
+__global__ void k_rebuild_request(Dev d, int trial) {
   const unsigned long long n = *d.cur_step;
-  for (int t = threadIdx.x; t < d.n_trials; t += blockDim.x)
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < d.n_trials; t += gridDim.x * blockDim.x)
     if (trial < 0 || t == trial) d.rb[d.n_trials + t] = (uint32_t)n;
-  __syncthreads();
-  decide_rebuilds(d, c, n, true);
 }
 
 // work items of the rebuilding trials: each trial cut into `per` pieces,
@@ -46,29 +45,23 @@ __global__ void k_rebuild_request(Dev d, SimConst c, int trial) {
        item_ += gridDim.x)                                                                 \
     if (const int t = d.rb_list[item_ / (per)], piece = item_ % (per); true)
 
-
-__global__ void k_bin(Dev d, SimConst c, float half_skin2, int strict) {
+// ---------------------------------------------------------------------------
+// the decision and the first part of the rebuild: one block per trial; a
+// block whose trial is due bins its atoms, scans the columns and fills the
+// column buckets; block 0 also writes the list of rebuilding trials that
+// the later kernels walk.  No block writes what another reads to decide (the
+// requests, the last-rebuild stamps: the copy-back stamps them).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(FRONT_THREADS, 1)
+    k_front(Dev d, SimConst c, float half_skin2, int strict, int forced_only) {
+  __shared__ FrontShared sh;
   const unsigned long long n = *d.cur_step;
-  const int per = (d.max_trial_slots + 255) / 256;
-  FOR_REBUILD_ITEMS(per, t, piece) bin_slot(d, c, half_skin2, strict, t, piece * 256 + threadIdx.x, n);
-}
-
-// ---------------------------------------------------------------------------
-// per trial: exclusive scans of column atom counts and cluster counts
-// ---------------------------------------------------------------------------
-__global__ void k_colscan(Dev d) {
-  __shared__ int s_a[256], s_c[256];
-  if (blockIdx.x >= d.rb_cnt[0]) return;
-  colscan_trial<256>(d, s_a, s_c, d.rb_list[blockIdx.x]);
-}
-
-// ---------------------------------------------------------------------------
-// scatter slot indices into their column buckets (unordered)
-// ---------------------------------------------------------------------------
-
-__global__ void k_colfill(Dev d) {
-  const int per = (d.max_trial_slots + 255) / 256;
-  FOR_REBUILD_ITEMS(per, t, piece) colfill_slot(d, t, piece * 256 + threadIdx.x);
+  if (blockIdx.x == 0) decide_rebuilds(d, c, n, forced_only != 0);
+  for (int t = blockIdx.x; t < d.n_trials; t += gridDim.x) {
+    if (!trial_due(d, c, t, n, forced_only != 0)) continue;
+    __syncthreads();  // the shared arrays of the block's previous trial are no longer read
+    front_trial(d, c, half_skin2, strict, sh, t, n);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -106,7 +99,11 @@ __global__ void __launch_bounds__(LIST_WARPS * 32, 8) k_list(Dev d, SimConst c, 
 
 __global__ void k_copyback(Dev d) {
   const int per = (d.max_trial_slots + 255) / 256;
-  FOR_REBUILD_ITEMS(per, t, piece) copyback_slot(d, t, piece * 256 + threadIdx.x);
+  const uint32_t n32 = (uint32_t)*d.cur_step;
+  FOR_REBUILD_ITEMS(per, t, piece) {
+    if (piece == 0 && threadIdx.x == 0) d.last_rb[t] = n32;  // the trial's last rebuild
+    copyback_slot(d, t, piece * 256 + threadIdx.x);
+  }
 }
 
 // positions the current list of one trial was built from, caller order
@@ -130,21 +127,16 @@ static unsigned rebuild_grid(const Dev &d, int per_sm, long long per_trial) {
   return (unsigned)std::max(1LL, std::min((long long)d.n_sm * per_sm, per_trial * d.n_trials));
 }
 
-void launch_rebuild_request(const Dev &d, const SimConst &c, int32_t trial, cudaStream_t s) {
-  k_rebuild_request<<<1, 1024, 0, s>>>(d, c, trial);
+void launch_rebuild_request(const Dev &d, int32_t trial, cudaStream_t s) {
+  k_rebuild_request<<<(d.n_trials + 255) / 256, 256, 0, s>>>(d, trial);
 }
-void launch_bin(const Dev &d, const SimConst &c, float half_skin2, int strict_skin, cudaStream_t s) {
-  k_bin<<<rebuild_grid(d, 4, (d.max_trial_slots + 255) / 256), 256, 0, s>>>(d, c, half_skin2, strict_skin);
-}
-void launch_colscan(const Dev &d, const SimConst &c, cudaStream_t s) {
-  (void)c;
-  k_colscan<<<d.n_trials, 256, 0, s>>>(d);
+void launch_front(const Dev &d, const SimConst &c, float half_skin2, int strict_skin, bool forced_only,
+                  cudaStream_t s) {
+  k_front<<<(unsigned)std::min(d.n_trials, 65535), FRONT_THREADS, 0, s>>>(d, c, half_skin2, strict_skin,
+                                                                          forced_only ? 1 : 0);
 }
 void launch_list_positions(const Dev &d, int32_t trial, double *out, int32_t n, cudaStream_t s) {
   if (n > 0) k_list_positions<<<(n + 255) / 256, 256, 0, s>>>(d, trial, out, n);
-}
-void launch_colfill(const Dev &d, cudaStream_t s) {
-  k_colfill<<<rebuild_grid(d, 4, (d.max_trial_slots + 255) / 256), 256, 0, s>>>(d);
 }
 void launch_colsort(const Dev &d, cudaStream_t s) {
   // columns hold about 100 atoms: 128 threads keep every thread busy in the sort

@@ -6,14 +6,13 @@
 
 namespace vp {
 
-__device__ __forceinline__ void bin_slot(const Dev &d, const SimConst &c, float half_skin2, int strict, int t,
-                                         int local, unsigned long long n) {
-  const TrialInfo T = d.tinfo[t];
-  if (local >= T.max_clus * CL) return;
-  const int slot = T.slot0 + local;
-  int o = d.orig[slot];
-  if (local >= d.tstate[t].n_clus * CL || o < 0) { d.slot_col[slot] = -1; return; }
-  float4 p = d.pos[slot];
+// Slot `slot` of trial t, its position p already loaded (live: the slot
+// holds an atom): wrapped into the box, its grid column picked and recorded
+// in slot_col; returns the trial's column offset plus the column (the index
+// into the per-column arrays), or -1 for a slot without an atom.
+__device__ __forceinline__ int bin_loaded(const Dev &d, const SimConst &c, const TrialInfo &T, float half_skin2,
+                                          int strict, int t, int slot, bool live, float4 p, unsigned long long n) {
+  if (!live) { d.slot_col[slot] = -1; return -1; }
   const float L = T.box, iL = T.inv_box;
   if (c.list_fixed && d.rb[d.n_trials + t] != (uint32_t)n) {
     // fixed-interval lists: an atom farther than skin/2 from where the list
@@ -43,14 +42,34 @@ __device__ __forceinline__ void bin_slot(const Dev &d, const SimConst &c, float 
   int cy = max(0, min((int)(y * T.inv_col_w), T.ncol - 1));
   const int col = cx * T.ncol + cy;
   d.slot_col[slot] = col;
+  return T.col0 + col;
+}
+
+// the same for slot `local` of the trial (loads included)
+__device__ __forceinline__ int bin_slot_col(const Dev &d, const SimConst &c, const TrialInfo &T, float half_skin2,
+                                            int strict, int t, int local, int n_clus, unsigned long long n) {
+  if (local >= T.max_clus * CL) return -1;
+  const int slot = T.slot0 + local;
+  const int o = d.orig[slot];
+  const bool live = local < n_clus * CL && o >= 0;
+  return bin_loaded(d, c, T, half_skin2, strict, t, slot, live, live ? d.pos[slot] : make_float4(0.f, 0.f, 0.f, 0.f), n);
+}
+
+// ... and counted in its column (global counters)
+__device__ __forceinline__ void bin_slot(const Dev &d, const SimConst &c, float half_skin2, int strict, int t,
+                                         int local, unsigned long long n) {
+  const TrialInfo T = d.tinfo[t];
+  const int cg = bin_slot_col(d, c, T, half_skin2, strict, t, local, d.tstate[t].n_clus, n);
+  if (cg < 0) return;
   // slots are in column order from the last rebuild, so a warp's atoms fall
   // into one or two columns: one atomic per column and warp
-  const int cg = T.col0 + col;
   const unsigned peers = __match_any_sync(__activemask(), cg);
   if ((threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&d.col_count[cg], __popc(peers));
 }
 
-template <int NT>
+// STAMP: record this step as the trial's last rebuild here (the front kernel
+// leaves that to the copy-back: its blocks still read the stamps to decide)
+template <int NT, bool STAMP = true>
 __device__ __forceinline__ void colscan_trial(const Dev &d, int (&s_a)[NT], int (&s_c)[NT], int t) {
   const TrialInfo T = d.tinfo[t];
   int nc = T.ncol * T.ncol;
@@ -93,7 +112,7 @@ __device__ __forceinline__ void colscan_trial(const Dev &d, int (&s_a)[NT], int 
   if (threadIdx.x == NT - 1) {
     d.tstate[t].n_clus = total;
     const uint32_t n32 = (uint32_t)*d.cur_step;
-    d.last_rb[t] = n32;
+    if (STAMP) d.last_rb[t] = n32;
     atomicAdd(reinterpret_cast<unsigned long long *>(d.diag + 1), 1ull);
     if (d.rb[t] == n32) atomicAdd(reinterpret_cast<unsigned long long *>(d.diag + 2), 1ull);
   }
@@ -124,6 +143,84 @@ __device__ __forceinline__ void colfill_slot(const Dev &d, int t, int local) {
   base = __shfl_sync(act, base, leader);
   const int p = base + __popc(peers & ((1u << lane) - 1u));
   if (p < COL_CAP && d.col_count[cg] <= COL_CAP) d.bucket[T.atom0 + d.col_start[cg] + p] = slot;
+}
+
+// The first part of trial t's rebuild by one block of FRONT_THREADS threads,
+// in place of three grid-wide kernels: binning (bin_loaded, the column counts
+// in shared memory), the column scans (colscan_trial) and the bucket fill
+// (places from shared-memory counters).  The order inside a column's bucket
+// differs from the separate kernels' (it depends on timing in both), but the
+// column sort orders every column by (z, atom index), so the layout is the
+// same.  Loads of FRONT_UNROLL slots per thread are issued together.
+constexpr int FRONT_THREADS = 1024;
+constexpr int FRONT_UNROLL = 4;
+constexpr int MAX_COLS = 64 * 64;  // columns per trial (the host caps the grid at 64 x 64)
+struct FrontShared {
+  int cnt[MAX_COLS];   // atoms per column
+  int fill[MAX_COLS];  // places taken in each column's bucket
+  int a[FRONT_THREADS], c[FRONT_THREADS];
+};
+
+__device__ __forceinline__ void front_trial(const Dev &d, const SimConst &c, float half_skin2, int strict,
+                                            FrontShared &sh, int t, unsigned long long n) {
+  const TrialInfo T = d.tinfo[t];
+  const int nc = T.ncol * T.ncol;
+  const int n_clus = d.tstate[t].n_clus;
+  const int n_slots = T.max_clus * CL;
+  for (int k = threadIdx.x; k < nc; k += FRONT_THREADS) {
+    sh.cnt[k] = 0;
+    sh.fill[k] = 0;
+  }
+  __syncthreads();
+  for (int base = threadIdx.x; base < n_slots; base += FRONT_THREADS * FRONT_UNROLL) {
+    int o[FRONT_UNROLL];
+    float4 p[FRONT_UNROLL];
+#pragma unroll
+    for (int u = 0; u < FRONT_UNROLL; ++u) {
+      const int local = base + u * FRONT_THREADS;
+      o[u] = local < n_slots ? d.orig[T.slot0 + local] : -1;
+      p[u] = local < n_slots ? d.pos[T.slot0 + local] : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+#pragma unroll
+    for (int u = 0; u < FRONT_UNROLL; ++u) {
+      const int local = base + u * FRONT_THREADS;
+      if (local < n_slots) {
+        const bool live = local < n_clus * CL && o[u] >= 0;
+        const int cg = bin_loaded(d, c, T, half_skin2, strict, t, T.slot0 + local, live, p[u], n);
+        if (cg >= 0) {
+          const unsigned peers = __match_any_sync(__activemask(), cg);
+          if ((threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&sh.cnt[cg - T.col0], __popc(peers));
+        }
+      }
+    }
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < nc; k += FRONT_THREADS) d.col_count[T.col0 + k] = sh.cnt[k];
+  __syncthreads();
+  colscan_trial<FRONT_THREADS, false>(d, sh.a, sh.c, t);
+  __syncthreads();
+  for (int base = threadIdx.x; base < n_slots; base += FRONT_THREADS * FRONT_UNROLL) {
+    int col[FRONT_UNROLL];
+#pragma unroll
+    for (int u = 0; u < FRONT_UNROLL; ++u) {
+      const int local = base + u * FRONT_THREADS;
+      col[u] = local < n_slots ? d.slot_col[T.slot0 + local] : -1;
+    }
+#pragma unroll
+    for (int u = 0; u < FRONT_UNROLL; ++u) {
+      if (col[u] >= 0) {
+        const unsigned act = __activemask();
+        const unsigned peers = __match_any_sync(act, col[u]);
+        const int lane = threadIdx.x & 31, leader = __ffs(peers) - 1;
+        int b = 0;
+        if (lane == leader) b = atomicAdd(&sh.fill[col[u]], __popc(peers));
+        b = __shfl_sync(act, b, leader);
+        const int q = b + __popc(peers & ((1u << lane) - 1u));
+        const int cg = T.col0 + col[u];
+        if (q < COL_CAP && sh.cnt[col[u]] <= COL_CAP) d.bucket[T.atom0 + d.col_start[cg] + q] = T.slot0 + base + u * FRONT_THREADS;
+      }
+    }
+  }
 }
 
 struct ColsortShared {
@@ -280,6 +377,10 @@ static __device__ __noinline__ unsigned list_mixed_images(const Dev &d, int I, i
 
 constexpr int LIST_WARPS = 4;
 constexpr int CAND_MAX = 1024;  // candidate 4-atom j-clusters per i-cluster (bounding-box pass)
+// a candidate word: the half index (J_BITS bits), the shared-image flag, the image key
+constexpr int CAND_SAME_BIT = (int)J_BITS;
+constexpr int CAND_KEY_SHIFT = (int)J_BITS + 1;
+static_assert(J_BITS + 6 <= 31, "candidate word: half index, flag and a 5-bit key in a non-negative int");
 
 // One warp per i-cluster.  Phase 1: lanes test columns, then the 4-atom
 // halves of the clusters of each passing column, against the i-cluster's
@@ -351,6 +452,7 @@ __device__ __forceinline__ void list_cluster(const Dev &d, const SimConst &c, fl
     return e <= 0 ? a + k : (k < e ? k : a + (k - e));
   };
   const int nwin = wnx * wny;
+  const int n_clus_t = d.tstate[t].n_clus;
   for (int cb = 0; cb < nwin; cb += 32) {
     const int wi = cb + lane;
     // this lane's column: up to two ranges [a1, a1 + n1), [a2, a2 + n2) of
@@ -361,39 +463,43 @@ __device__ __forceinline__ void list_cluster(const Dev &d, const SimConst &c, fl
     int a1 = 0, n1 = 0, a2 = 0, n2 = 0;
     const int cc = wi < nwin ? kth(wx0, wnx, wi / wny) * T.ncol + kth(wy0, wny, wi % wny) : 0;
     if (wi < nwin) {
-      const int ccs = d.col_cstart[T.col0 + cc];
-      const int ncl = max(0, (cc + 1 < nc2 ? d.col_cstart[T.col0 + cc + 1] : d.tstate[t].n_clus) - ccs);
-      const int jlo = max(ccs, Il);
-      if (ccs + ncl > jlo) {
-        const int cx = cc / T.ncol, cy = cc - cx * T.ncol;
-        const float gx = periodic_gap(lo.x, hi.x, cx * w, (cx + 1) * w, L);
-        const float gy = periodic_gap(lo.y, hi.y, cy * w, (cy + 1) * w, L);
-        const float g2 = gx * gx + gy * gy;
-        if (g2 < rl2_bbox) {
+      // the geometry first, then every load of the column at once (one
+      // memory round trip instead of two)
+      const int cx = cc / T.ncol, cy = cc - cx * T.ncol;
+      const float gx = periodic_gap(lo.x, hi.x, cx * w, (cx + 1) * w, L);
+      const float gy = periodic_gap(lo.y, hi.y, cy * w, (cy + 1) * w, L);
+      const float g2 = gx * gx + gy * gy;
+      if (g2 < rl2_bbox) {
+        const float rz = sqrtf(rl2_bbox - g2) * 1.001f + 1e-3f;
+        const float za = lo.z - rz, zb = hi.z + rz;
+        const bool whole = zb - za >= L;
+        // z-bins of the halves that may meet [u, v] (0 <= u <= v <= L): one
+        // or two intervals (the periodic image)
+        const float zs = ZBINS * iL;
+        const bool two = za < 0.f || zb > L;
+        const float u1 = 0.f, v1 = za < 0.f ? zb : (zb > L ? zb - L : zb);
+        const float u1r = two ? u1 : za;
+        const float u2 = za < 0.f ? za + L : za, v2 = L;
+        auto bin_lo = [&](float u) { return max(0, min(ZBINS, (int)floorf(u * zs) - 1)); };
+        auto bin_hi = [&](float v) { return max(0, min(ZBINS, (int)floorf(v * zs) + 2)); };
+        const int bu1 = bin_lo(u1r), bv1 = bin_hi(v1), bu2 = bin_lo(u2), bv2 = bin_hi(v2);
+        const int *tab = d.col_ztab + (size_t)(T.col0 + cc) * (ZBINS + 1);
+        const int ccs = d.col_cstart[T.col0 + cc];
+        const int cnext = cc + 1 < nc2 ? d.col_cstart[T.col0 + cc + 1] : n_clus_t;
+        const int t1a = tab[bu1], t1b = tab[bv1];
+        const int t2a = two ? tab[bu2] : 0, t2b = two ? tab[bv2] : 0;
+        const int ncl = max(0, cnext - ccs);
+        const int jlo = max(ccs, Il);
+        if (ccs + ncl > jlo) {
           const int hs = 2 * (jlo - ccs), he = 2 * ncl;  // local half range of the half list
-          const float rz = sqrtf(rl2_bbox - g2) * 1.001f + 1e-3f;
-          const float za = lo.z - rz, zb = hi.z + rz;
-          if (zb - za >= L) {
+          if (whole) {
             a1 = hs; n1 = he - hs;
           } else {
-            const int *tab = d.col_ztab + (size_t)(T.col0 + cc) * (ZBINS + 1);
-            const float zs = ZBINS * iL;
-            // halves that may meet [u, v] (0 <= u <= v <= L)
-            auto range = [&](float u, float v, int &ra, int &rb) {
-              const int bu = max(0, min(ZBINS, (int)floorf(u * zs) - 1));
-              const int bv = max(0, min(ZBINS, (int)floorf(v * zs) + 2));
-              ra = max(tab[bu] - 1, 0);
-              rb = bv >= ZBINS ? he : tab[bv];
-            };
-            int r1a, r1b, r2a = 0, r2b = 0;
-            if (za < 0.f) {          // [0, zb] and [za + L, L]
-              range(0.f, zb, r1a, r1b);
-              range(za + L, L, r2a, r2b);
-            } else if (zb > L) {     // [0, zb - L] and [za, L]
-              range(0.f, zb - L, r1a, r1b);
-              range(za, L, r2a, r2b);
-            } else {
-              range(za, zb, r1a, r1b);
+            int r1a = max(t1a - 1, 0), r1b = bv1 >= ZBINS ? he : t1b;
+            int r2a = 0, r2b = 0;
+            if (two) {
+              r2a = max(t2a - 1, 0);
+              r2b = bv2 >= ZBINS ? he : t2b;
             }
             r1a = max(r1a, hs); r1b = min(r1b, he);
             r2a = max(max(r2a, hs), r1b); r2b = min(r2b, he);  // ascending, no half twice
@@ -440,6 +546,17 @@ __device__ __forceinline__ void list_cluster(const Dev &d, const SimConst &c, fl
         const float gy = periodic_gap(lo.y, hi.y, jlo4.y, jhi4.y, L);
         const float gz = periodic_gap(lo.z, hi.z, jlo4.z, jhi4.z, L);
         ok = gx * gx + gy * gy + gz * gz < rl2_bbox;
+        // image counts at the two bounding-box extremes (each -1, 0 or 1: the
+        // positions lie in [0, L)); when they agree in every dimension, every
+        // atom pair of the candidate has them.  Carried in the candidate word
+        // (shared image flag, key 9 (nx+1) + 3 (ny+1) + (nz+1)) so that phase 2
+        // need not load the box again.
+        const float qlx = rintf(__fmul_rn(__fsub_rn(jlo4.x, hi.x), iL)), qhx = rintf(__fmul_rn(__fsub_rn(jhi4.x, lo.x), iL));
+        const float qly = rintf(__fmul_rn(__fsub_rn(jlo4.y, hi.y), iL)), qhy = rintf(__fmul_rn(__fsub_rn(jhi4.y, lo.y), iL));
+        const float qlz = rintf(__fmul_rn(__fsub_rn(jlo4.z, hi.z), iL)), qhz = rintf(__fmul_rn(__fsub_rn(jhi4.z, lo.z), iL));
+        const int same = qlx == qhx && qly == qhy && qlz == qhz;
+        const int key = 9 * ((int)qlx + 1) + 3 * ((int)qly + 1) + ((int)qlz + 1);
+        J4 |= (same << CAND_SAME_BIT) | (key << CAND_KEY_SHIFT);
       }
       const unsigned m = __ballot_sync(0xffffffffu, ok);
       const int pos = n_cand + __popc(m & ((1u << lane) - 1u));
@@ -485,16 +602,15 @@ __device__ __forceinline__ void list_cluster(const Dev &d, const SimConst &c, fl
     const int k = k0 + lane;
     unsigned mask = 0u, w0 = 0u;
     if (k < n_cand) {
-      const int J4 = cand[k];
+      const int cw = cand[k];
+      const int J4 = cw & (int)J_MASK;
       const int J8 = J4 >> 1, h = J4 & 1;
       const int JG = T.clus0 + J8;
       const int sj0 = JG * CL + h * CJ;
       float kmin = 3e38f, kmax = -3e38f;
-      const float4 jlo4 = d.bb_lo[2 * T.clus0 + J4], jhi4 = d.bb_hi[2 * T.clus0 + J4];
-      const float qlx = rintf(__fmul_rn(__fsub_rn(jlo4.x, hi.x), iL)), qhx = rintf(__fmul_rn(__fsub_rn(jhi4.x, lo.x), iL));
-      const float qly = rintf(__fmul_rn(__fsub_rn(jlo4.y, hi.y), iL)), qhy = rintf(__fmul_rn(__fsub_rn(jhi4.y, lo.y), iL));
-      const float qlz = rintf(__fmul_rn(__fsub_rn(jlo4.z, hi.z), iL)), qhz = rintf(__fmul_rn(__fsub_rn(jhi4.z, lo.z), iL));
-      if (qlx == qhx && qly == qhy && qlz == qhz) {
+      const int ckey = (cw >> CAND_KEY_SHIFT) & 31;
+      const float qlx = (float)(ckey / 9 - 1), qly = (float)((ckey / 3) % 3 - 1), qlz = (float)(ckey % 3 - 1);
+      if ((cw >> CAND_SAME_BIT) & 1) {
         // two i-atoms per packed FP32x2 operation; every operation rounds on
         // its own exactly as the per-pair rule does (d = xj + (-xi) is xj - xi)
         const float sx = __fmul_rn(L, qlx), sy = __fmul_rn(L, qly), sz = __fmul_rn(L, qlz);

@@ -22,11 +22,6 @@ __global__ void __launch_bounds__(256, 6) k_update(Dev d, SimConst c) {
   update_slot<MODE>(d, c, blockIdx.x * blockDim.x + threadIdx.x);
 }
 
-// which trials rebuild their lists in this step (one block, after the update)
-__global__ void __launch_bounds__(1024) k_decide(Dev d, SimConst c) {
-  decide_rebuilds(d, c, *d.cur_step, false);
-}
-
 // Maxwell-Boltzmann velocities (Philox stream 1, step 0) with the centre of
 // mass at rest; one block per trial, only trials with need[t] != 0
 __global__ void __launch_bounds__(256) k_init_vel(Dev d, float kT, const int32_t *need) {
@@ -241,7 +236,6 @@ void launch_update(const Dev &d, const SimConst &c, UpdateMode mode, cudaStream_
   unsigned blocks = (unsigned)((d.total_slots + 255) / 256);
   if (mode == UPD_DRIFT) {
     k_update<UPD_DRIFT><<<blocks, 256, 0, s>>>(d, c);
-    k_decide<<<1, 1024, 0, s>>>(d, c);
   } else {
     k_update<UPD_FINAL><<<blocks, 256, 0, s>>>(d, c);
   }
@@ -270,7 +264,6 @@ void launch_potential_out(const Dev &d, double *energy, double *forces, int32_t 
   const int m = n > d.n_trials ? n : d.n_trials;
   if (m > 0) k_potential_out<<<(m + 255) / 256, 256, 0, s>>>(d, energy, forces, n);
 }
-void launch_decide(const Dev &d, const SimConst &c, cudaStream_t s) { k_decide<<<1, 1024, 0, s>>>(d, c); }
 void launch_extract_pairs(const Dev &d, int32_t list_cap, int32_t trial, int32_t n_clus, int32_t *pairs,
                           long long cap, unsigned long long *count, cudaStream_t s) {
   if (n_clus > 0) k_extract_pairs<<<(n_clus + 3) / 4, 128, 0, s>>>(d, list_cap, trial, pairs, cap, count);
