@@ -46,20 +46,21 @@ __global__ void k_rebuild_request(Dev d, int trial) {
     if (const int t = d.rb_list[item_ / (per)], piece = item_ % (per); true)
 
 // ---------------------------------------------------------------------------
-// the decision and the first part of the rebuild: one block per trial; a
-// block whose trial is due bins its atoms, scans the columns and fills the
-// column buckets; block 0 also writes the list of rebuilding trials that
-// the later kernels walk.  No block writes what another reads to decide (the
-// requests, the last-rebuild stamps: the copy-back stamps them).
+// the decision and the first part of the rebuild: one cluster of blocks per
+// trial; a cluster whose trial is due bins its atoms, scans the columns and
+// fills the column buckets; block 0 also writes the list of rebuilding
+// trials that the later kernels walk.  No block writes what another reads to
+// decide (the requests, the last-rebuild stamps: the copy-back stamps them).
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(FRONT_THREADS, 1)
+__global__ void __cluster_dims__(FRONT_CLUSTER, 1, 1) __launch_bounds__(FRONT_THREADS, 1)
     k_front(Dev d, SimConst c, float half_skin2, int strict, int forced_only) {
   __shared__ FrontShared sh;
   const unsigned long long n = *d.cur_step;
   if (blockIdx.x == 0) decide_rebuilds(d, c, n, forced_only != 0);
-  for (int t = blockIdx.x; t < d.n_trials; t += gridDim.x) {
+  const int n_clusters = (int)gridDim.x / FRONT_CLUSTER;
+  // the whole cluster takes the same trials (the same decision in every block)
+  for (int t = (int)blockIdx.x / FRONT_CLUSTER; t < d.n_trials; t += n_clusters) {
     if (!trial_due(d, c, t, n, forced_only != 0)) continue;
-    __syncthreads();  // the shared arrays of the block's previous trial are no longer read
     front_trial(d, c, half_skin2, strict, sh, t, n);
   }
 }
@@ -132,8 +133,8 @@ void launch_rebuild_request(const Dev &d, int32_t trial, cudaStream_t s) {
 }
 void launch_front(const Dev &d, const SimConst &c, float half_skin2, int strict_skin, bool forced_only,
                   cudaStream_t s) {
-  k_front<<<(unsigned)std::min(d.n_trials, 65535), FRONT_THREADS, 0, s>>>(d, c, half_skin2, strict_skin,
-                                                                          forced_only ? 1 : 0);
+  const unsigned clusters = (unsigned)std::min(d.n_trials, 16384);
+  k_front<<<clusters * FRONT_CLUSTER, FRONT_THREADS, 0, s>>>(d, c, half_skin2, strict_skin, forced_only ? 1 : 0);
 }
 void launch_list_positions(const Dev &d, int32_t trial, double *out, int32_t n, cudaStream_t s) {
   if (n > 0) k_list_positions<<<(n + 255) / 256, 256, 0, s>>>(d, trial, out, n);

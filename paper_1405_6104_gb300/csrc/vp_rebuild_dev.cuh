@@ -2,6 +2,8 @@
 // column scan, bucket fill, column sort, copy-back, cluster-pair list of one
 // i-cluster), shared by the separate kernels and the one-kernel step.
 #pragma once
+#include <cooperative_groups.h>
+
 #include "vp_dev.cuh"
 
 namespace vp {
@@ -145,65 +147,78 @@ __device__ __forceinline__ void colfill_slot(const Dev &d, int t, int local) {
   if (p < COL_CAP && d.col_count[cg] <= COL_CAP) d.bucket[T.atom0 + d.col_start[cg] + p] = slot;
 }
 
-// The first part of trial t's rebuild by one block of FRONT_THREADS threads,
-// in place of three grid-wide kernels: binning (bin_loaded, the column counts
-// in shared memory), the column scans (colscan_trial) and the bucket fill
-// (places from shared-memory counters).  The order inside a column's bucket
-// differs from the separate kernels' (it depends on timing in both), but the
-// column sort orders every column by (z, atom index), so the layout is the
-// same.  Loads of FRONT_UNROLL slots per thread are issued together.
+// The first part of trial t's rebuild by one thread-block cluster of
+// FRONT_CLUSTER blocks of FRONT_THREADS threads, in place of three grid-wide
+// kernels: binning (bin_loaded), the column scans (colscan_trial) and the
+// bucket fill.  The column counters live in the shared memory of the
+// cluster's first block; the others reach them through distributed shared
+// memory.  The order inside a column's bucket depends on timing (as with the
+// separate kernels), but the column sort orders every column by (z, atom
+// index), so the layout is the same.  Each thread issues the loads of
+// FRONT_UNROLL slots together.
 constexpr int FRONT_THREADS = 1024;
+constexpr int FRONT_CLUSTER = 4;
 constexpr int FRONT_UNROLL = 4;
 constexpr int MAX_COLS = 64 * 64;  // columns per trial (the host caps the grid at 64 x 64)
 struct FrontShared {
-  int cnt[MAX_COLS];   // atoms per column
-  int fill[MAX_COLS];  // places taken in each column's bucket
+  int cnt[MAX_COLS];   // atoms per column (used in the cluster's first block)
+  int fill[MAX_COLS];  // places taken in each column's bucket (idem)
   int a[FRONT_THREADS], c[FRONT_THREADS];
 };
 
 __device__ __forceinline__ void front_trial(const Dev &d, const SimConst &c, float half_skin2, int strict,
                                             FrontShared &sh, int t, unsigned long long n) {
+  namespace cgr = cooperative_groups;
+  cgr::cluster_group cl = cgr::this_cluster();
+  const int rank = (int)cl.block_rank();
+  int *cnt0 = cl.map_shared_rank(sh.cnt, 0);
+  int *fill0 = cl.map_shared_rank(sh.fill, 0);
   const TrialInfo T = d.tinfo[t];
   const int nc = T.ncol * T.ncol;
   const int n_clus = d.tstate[t].n_clus;
   const int n_slots = T.max_clus * CL;
-  for (int k = threadIdx.x; k < nc; k += FRONT_THREADS) {
-    sh.cnt[k] = 0;
-    sh.fill[k] = 0;
-  }
-  __syncthreads();
-  for (int base = threadIdx.x; base < n_slots; base += FRONT_THREADS * FRONT_UNROLL) {
+  constexpr int STRIDE = FRONT_CLUSTER * FRONT_THREADS;
+  const int first = rank * FRONT_THREADS + threadIdx.x;
+  if (rank == 0)
+    for (int k = threadIdx.x; k < nc; k += FRONT_THREADS) {
+      sh.cnt[k] = 0;
+      sh.fill[k] = 0;
+    }
+  cl.sync();
+  for (int base = first; base < n_slots; base += STRIDE * FRONT_UNROLL) {
     int o[FRONT_UNROLL];
     float4 p[FRONT_UNROLL];
 #pragma unroll
     for (int u = 0; u < FRONT_UNROLL; ++u) {
-      const int local = base + u * FRONT_THREADS;
+      const int local = base + u * STRIDE;
       o[u] = local < n_slots ? d.orig[T.slot0 + local] : -1;
       p[u] = local < n_slots ? d.pos[T.slot0 + local] : make_float4(0.f, 0.f, 0.f, 0.f);
     }
 #pragma unroll
     for (int u = 0; u < FRONT_UNROLL; ++u) {
-      const int local = base + u * FRONT_THREADS;
+      const int local = base + u * STRIDE;
       if (local < n_slots) {
         const bool live = local < n_clus * CL && o[u] >= 0;
         const int cg = bin_loaded(d, c, T, half_skin2, strict, t, T.slot0 + local, live, p[u], n);
         if (cg >= 0) {
           const unsigned peers = __match_any_sync(__activemask(), cg);
-          if ((threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&sh.cnt[cg - T.col0], __popc(peers));
+          if ((threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(cnt0 + (cg - T.col0), __popc(peers));
         }
       }
     }
   }
-  __syncthreads();
-  for (int k = threadIdx.x; k < nc; k += FRONT_THREADS) d.col_count[T.col0 + k] = sh.cnt[k];
-  __syncthreads();
-  colscan_trial<FRONT_THREADS, false>(d, sh.a, sh.c, t);
-  __syncthreads();
-  for (int base = threadIdx.x; base < n_slots; base += FRONT_THREADS * FRONT_UNROLL) {
+  cl.sync();
+  if (rank == 0) {
+    for (int k = threadIdx.x; k < nc; k += FRONT_THREADS) d.col_count[T.col0 + k] = sh.cnt[k];
+    __syncthreads();
+    colscan_trial<FRONT_THREADS, false>(d, sh.a, sh.c, t);
+  }
+  cl.sync();  // the column starts are written (release and acquire at cluster scope)
+  for (int base = first; base < n_slots; base += STRIDE * FRONT_UNROLL) {
     int col[FRONT_UNROLL];
 #pragma unroll
     for (int u = 0; u < FRONT_UNROLL; ++u) {
-      const int local = base + u * FRONT_THREADS;
+      const int local = base + u * STRIDE;
       col[u] = local < n_slots ? d.slot_col[T.slot0 + local] : -1;
     }
 #pragma unroll
@@ -213,14 +228,16 @@ __device__ __forceinline__ void front_trial(const Dev &d, const SimConst &c, flo
         const unsigned peers = __match_any_sync(act, col[u]);
         const int lane = threadIdx.x & 31, leader = __ffs(peers) - 1;
         int b = 0;
-        if (lane == leader) b = atomicAdd(&sh.fill[col[u]], __popc(peers));
+        if (lane == leader) b = atomicAdd(fill0 + col[u], __popc(peers));
         b = __shfl_sync(act, b, leader);
         const int q = b + __popc(peers & ((1u << lane) - 1u));
         const int cg = T.col0 + col[u];
-        if (q < COL_CAP && sh.cnt[col[u]] <= COL_CAP) d.bucket[T.atom0 + d.col_start[cg] + q] = T.slot0 + base + u * FRONT_THREADS;
+        if (q < COL_CAP && d.col_count[cg] <= COL_CAP)
+          d.bucket[T.atom0 + d.col_start[cg] + q] = T.slot0 + base + u * STRIDE;
       }
     }
   }
+  cl.sync();  // the first block's counters stay alive until every block is done with them
 }
 
 struct ColsortShared {
