@@ -34,7 +34,7 @@
  * Units: nm, ps, amu, kJ/mol, e, K.
  *
  * Build: cc -O2 -fopenmp -ffp-contract=off -shared -fPIC (the list rule
- * relies on no FMA contraction).
+ * takes its two fused steps from fmaf and relies on no other contraction).
  */
 #include <math.h>
 #include <stdint.h>
@@ -245,10 +245,11 @@ static void excl_free(excl_t *e) { free(e->cnt); free(e->lst); }
 
 /* ------------------------------------------------------------------------ */
 /* Verlet-list membership, restated bit for bit in IEEE single precision:    */
-/*   d_k = x_j,k - x_i,k;  d_k = d_k - L * rint(d_k * invL)   (k = x, y, z)  */
-/*   r2 = (d_x*d_x + d_y*d_y) + d_z*d_z;  member iff r2 < rl2                */
+/*   n_k = rint((x_j,k - x_i,k) * invL);  d_k = (x_j,k - L * n_k) - x_i,k     */
+/*   r2 = fma(d_z, d_z, fma(d_y, d_y, d_x*d_x));  member iff r2 < rl2        */
 /* with L = (float)box, invL = (float)(1.0/(double)L) and                    */
-/* rl2 = (float)(r_list*r_list) in double, no fused multiply-add anywhere.   */
+/* rl2 = (float)(r_list*r_list) in double; no other fused multiply-add (the  */
+/* image of x_j is formed first, as the force evaluation forms it).          */
 /* ------------------------------------------------------------------------ */
 static int list_rule(const float *xi, const float *xj, float L, float invL, float rl2) {
   float d[3];
@@ -257,13 +258,12 @@ static int list_rule(const float *xi, const float *xj, float L, float invL, floa
     float q = t * invL;
     float n = rintf(q);
     float sh = L * n;
-    d[k] = t - sh;
+    float u = xj[k] - sh;
+    d[k] = u - xi[k];
   }
-  float a = d[0] * d[0];
-  float b = d[1] * d[1];
-  float c = d[2] * d[2];
-  float r2 = a + b;
-  r2 = r2 + c;
+  float r2 = d[0] * d[0];
+  r2 = fmaf(d[1], d[1], r2);
+  r2 = fmaf(d[2], d[2], r2);
   return r2 < rl2;
 }
 

@@ -353,16 +353,17 @@ __device__ __forceinline__ float periodic_gap(float a0, float a1, float b0, floa
   return g;
 }
 
-// the FP32 list rule (no contraction): d = xj - xi; d -= L*rint(d*invL);
-// r2 = (dx*dx + dy*dy) + dz*dz; member iff r2 < rl2.  Also returns the image
-// key 9 nx + 3 ny + nz of the counts n (x_j image = x_j - L n).
+// the FP32 list rule: n = rint((xj - xi) * invL); d = (xj - L n) - xi (the
+// image of x_j first, as the force kernel forms it); r2 = fma(dz, dz,
+// fma(dy, dy, dx*dx)); member iff r2 < rl2.  Also returns the image key
+// 9 nx + 3 ny + nz of the counts n (x_j image = x_j - L n).
 __device__ __forceinline__ bool list_rule(float4 pi, float4 pj, float L, float iL, float rl2, float &key) {
-  float dx = __fsub_rn(pj.x, pi.x), dy = __fsub_rn(pj.y, pi.y), dz = __fsub_rn(pj.z, pi.z);
-  const float qx = rintf(__fmul_rn(dx, iL)), qy = rintf(__fmul_rn(dy, iL)), qz = rintf(__fmul_rn(dz, iL));
-  dx = __fsub_rn(dx, __fmul_rn(L, qx));
-  dy = __fsub_rn(dy, __fmul_rn(L, qy));
-  dz = __fsub_rn(dz, __fmul_rn(L, qz));
-  const float r2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+  const float tx = __fsub_rn(pj.x, pi.x), ty = __fsub_rn(pj.y, pi.y), tz = __fsub_rn(pj.z, pi.z);
+  const float qx = rintf(__fmul_rn(tx, iL)), qy = rintf(__fmul_rn(ty, iL)), qz = rintf(__fmul_rn(tz, iL));
+  const float dx = __fsub_rn(__fsub_rn(pj.x, __fmul_rn(L, qx)), pi.x);
+  const float dy = __fsub_rn(__fsub_rn(pj.y, __fmul_rn(L, qy)), pi.y);
+  const float dz = __fsub_rn(__fsub_rn(pj.z, __fmul_rn(L, qz)), pi.z);
+  const float r2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
   key = __fmaf_rn(9.0f, qx, __fmaf_rn(3.0f, qy, qz));
   return r2 < rl2;
 }
@@ -628,21 +629,22 @@ __device__ __forceinline__ void list_cluster(const Dev &d, const SimConst &c, fl
       const int ckey = (cw >> CAND_KEY_SHIFT) & 31;
       const float qlx = (float)(ckey / 9 - 1), qly = (float)((ckey / 3) % 3 - 1), qlz = (float)(ckey % 3 - 1);
       if ((cw >> CAND_SAME_BIT) & 1) {
-        // two i-atoms per packed FP32x2 operation; every operation rounds on
-        // its own exactly as the per-pair rule does (d = xj + (-xi) is xj - xi)
+        // the j-atom's image once, then two i-atoms per packed FP32x2
+        // operation; every operation rounds on its own exactly as the
+        // per-pair rule does (d = (xj - L n) + (-xi) is (xj - L n) - xi)
         const float sx = __fmul_rn(L, qlx), sy = __fmul_rn(L, qly), sz = __fmul_rn(L, qlz);
-        const float2 nsx = make_float2(-sx, -sx), nsy = make_float2(-sy, -sy), nsz = make_float2(-sz, -sz);
 #pragma unroll
         for (int b = 0; b < CJ; ++b) {
           const float4 pj = d.pos[sj0 + b];
-          const float2 xj2 = make_float2(pj.x, pj.x), yj2 = make_float2(pj.y, pj.y), zj2 = make_float2(pj.z, pj.z);
+          const float ux = __fsub_rn(pj.x, sx), uy = __fsub_rn(pj.y, sy), uz = __fsub_rn(pj.z, sz);
+          const float2 xj2 = make_float2(ux, ux), yj2 = make_float2(uy, uy), zj2 = make_float2(uz, uz);
 #pragma unroll
           for (int p = 0; p < CL / 2; ++p) {
             const float4 i0 = s_xp[wib][p][0], i1 = s_xp[wib][p][1];
-            const float2 dx = __fadd2_rn(__fadd2_rn(xj2, make_float2(i0.x, i0.y)), nsx);
-            const float2 dy = __fadd2_rn(__fadd2_rn(yj2, make_float2(i0.z, i0.w)), nsy);
-            const float2 dz = __fadd2_rn(__fadd2_rn(zj2, make_float2(i1.x, i1.y)), nsz);
-            const float2 r2 = __fadd2_rn(__fadd2_rn(__fmul2_rn(dx, dx), __fmul2_rn(dy, dy)), __fmul2_rn(dz, dz));
+            const float2 dx = __fadd2_rn(xj2, make_float2(i0.x, i0.y));
+            const float2 dy = __fadd2_rn(yj2, make_float2(i0.z, i0.w));
+            const float2 dz = __fadd2_rn(zj2, make_float2(i1.x, i1.y));
+            const float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
             if (r2.x < rl2) mask |= 1u << (2 * p * CJ + b);
             if (r2.y < rl2) mask |= 1u << ((2 * p + 1) * CJ + b);
           }
