@@ -205,6 +205,7 @@ void rebuild_cols(sim_handle *h, bool forced_only) {
   cudaStream_t s = h->stream;
   timed(h, "front", [&] { launch_front(h->d, h->c, h->half_skin2, h->strict_skin, forced_only, s); });
   timed(h, "colsort", [&] { launch_colsort(h->d, s); });
+  timed(h, "copyback", [&] { launch_copyback(h->d, s); });
 }
 
 void rebuild_list(sim_handle *h) {

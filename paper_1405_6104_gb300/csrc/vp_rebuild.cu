@@ -142,6 +142,8 @@ void launch_list_positions(const Dev &d, int32_t trial, double *out, int32_t n, 
 void launch_colsort(const Dev &d, cudaStream_t s) {
   // columns hold about 100 atoms: 128 threads keep every thread busy in the sort
   k_colsort<<<rebuild_grid(d, 8, d.max_trial_cols), 128, 0, s>>>(d);
+}
+void launch_copyback(const Dev &d, cudaStream_t s) {
   k_copyback<<<rebuild_grid(d, 4, (d.max_trial_slots + 255) / 256), 256, 0, s>>>(d);
 }
 void launch_list(const Dev &d, const SimConst &c, float rl2_bbox, cudaStream_t s) {
