@@ -254,8 +254,10 @@ def run_gpu(args):
         tuned = B.sim_autotune(batch.h, 1, probe)
         os.unlink(probe)
         step_form = 0
-    if step_form != 0:  # the roofline times the pair launches of the kernel-per-phase form
-        B.sim_set_step_mode(batch.h, 0)
+    # the roofline times the pair launches of the timed region: the one-kernel
+    # form has none, so it is timed in the kernel-per-phase form
+    timed_form = 0 if step_form == 1 else step_form
+    B.sim_set_step_mode(batch.h, timed_form)
     clocks = ClockSampler(local) if rank == 0 else None
     # event-record nodes around the pair kernel inside the chunk graph: the
     # roofline's launch duration is measured over the timed region itself
@@ -364,9 +366,8 @@ def run_gpu(args):
             pv = s.n_atoms * nst * n_plain / (e0.elapsed_time(e1) * 1e-3)
             plain = {"value": pv, "unit": "atom-steps/s",
                      "workload": f"1 trial x {s.n_atoms} atoms, same kernels, {n_plain} x {nst} MD steps",
-                     "step_form": "one cooperative kernel per step" if plain_form else "kernel per phase, graph replays",
-                     "ms_per_md_step_by_form": {"kernel per phase": plain_forms_ms[0],
-                                                "one kernel": plain_forms_ms[1]},
+                     "step_form": B.STEP_FORM_NAMES[plain_form],
+                     "ms_per_md_step_by_form": dict(zip(B.STEP_FORM_NAMES, plain_forms_ms)),
                      "batching_speedup": value / world / pv}
 
     if rank == 0:
@@ -392,8 +393,8 @@ def run_gpu(args):
                        "start": f"generated, relaxed {args.prep_steps} steps at gamma 20/ps (untimed)",
                        "md_steps_per_bench_step": nst, "parallelism": f"replicas x{world}",
                        "autotuned": {"pair_variant": tuned[0], "cv_variant": tuned[1],
-                                     "step_form": "one cooperative kernel per step" if step_form else
-                                     "kernel per phase, graph replays"},
+                                     "step_form": B.STEP_FORM_NAMES[step_form],
+                                     "timed_form": B.STEP_FORM_NAMES[timed_form]},
                        "l2": "working set > L2 (lists + state ~0.5 GB)"},
             "roofline": {"bound": "alu", "kernel": "pair", "achieved": achieved / 1e12, "peak": fp32_peak / 1e12,
                          "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": pair_traffic(),
@@ -579,8 +580,8 @@ def run_adjoint(args):
         "config": {"workload": f"30 000 atoms (1800-atom solute, 9400 waters), {n_frames} frames (1 per step), "
                                f"checkpoints every {every} steps, k_R 5", "phi": float(phi),
                    "grad_max": float(np.abs(G).max()),
-                   "forward_step_form": "one cooperative kernel per step" if fwd_form else "kernel per phase",
-                   "forward_ms_per_md_step_by_form": {"kernel per phase": fwd_forms_ms[0], "one kernel": fwd_forms_ms[1]}},
+                   "forward_step_form": B.STEP_FORM_NAMES[fwd_form],
+                   "forward_ms_per_md_step_by_form": dict(zip(B.STEP_FORM_NAMES, fwd_forms_ms))},
         "wall_s_per_step": wall / args.steps,
         "md_kernels_ms_per_step": md_ms,
         "md_kernel_share": md_ms / (t_kt * 1e3),
@@ -755,6 +756,10 @@ def run_uneven(args):
     with B.TrialBatch(systems, p, [1] * len(systems), trial_seeds=seeds) as b:
         tuned = B.sim_autotune(b.h, 5, None)
         classes = B.sim_tune_classes(b.h)
+        # the roofline times pair launches: the one-kernel form has none
+        form = B.sim_autotune_step(b.h, 2)
+        timed_form = 0 if form == 1 else form
+        B.sim_set_step_mode(b.h, timed_form)
         stream = torch.cuda.ExternalStream(b.stream)
         clocks = ClockSampler(local) if rank == 0 else None
         B.sim_set_timing(b.h, 2)
@@ -820,7 +825,8 @@ def run_uneven(args):
                                f"{steps * nst} MD steps timed", "md_steps_per_bench_step": nst,
                    "parallelism": f"trials sharded over {world} rank(s) by atoms x steps",
                    "start": f"generated, relaxed {min(args.prep_steps, 1000)} steps at gamma 20/ps (untimed)",
-                   "autotuned": {"pair_variant": tuned[0], "cv_variant": tuned[1], "size_classes": classes},
+                   "autotuned": {"pair_variant": tuned[0], "cv_variant": tuned[1], "size_classes": classes,
+                                 "step_form": B.STEP_FORM_NAMES[form], "timed_form": B.STEP_FORM_NAMES[timed_form]},
                    "l2": "working set > L2"},
         "roofline": {"bound": "alu", "kernel": "pair", "achieved": flops / pair_avg_s / 1e12,
                      "peak": fp32_peak / 1e12, "unit": "TFLOP/s", "frac": flops / pair_avg_s / fp32_peak,
@@ -870,6 +876,7 @@ def run_long(args):
     for name, n_trials, n_md in (("batch64_10000", 64, 10000), ("single_20000", 1, 20000)):
         with B.TrialBatch(s, p, [n_trials], trial_seeds=seeds[:n_trials]) as b:
             B.sim_autotune(b.h, 3, None)
+            form = B.sim_autotune_step(b.h, 2)
             stream = torch.cuda.ExternalStream(b.stream)
             b.step(p.nstlist)  # captures the chunk graph
             ms = _timed_batch(B, b, (n_md - p.nstlist) // p.nstlist, p.nstlist, stream)
@@ -882,7 +889,8 @@ def run_long(args):
             "ms": ms, "status": "ok (no error flag)", "phi": [float(x) for x in phi], "argmin": int(best),
             "phi_min": float(phi[best]), "z_final": [float(z[0]) for z in zs], "z_min": [float(z[1]) for z in zs],
             "skin_violations": diag["skin_violations"], "trial_rebuilds": diag["trial_rebuilds"],
-            "mean_steps_between_rebuilds": round(n_trials * n_md / max(diag["trial_rebuilds"], 1), 2)}
+            "mean_steps_between_rebuilds": round(n_trials * n_md / max(diag["trial_rebuilds"], 1), 2),
+            "step_form": B.STEP_FORM_NAMES[form]}
     t_end = time.time()
     clk = clocks.stop(t_begin, t_end) if clocks else None
     line = {"metric": METRIC, "value": out["batch64_10000"]["atom_steps_per_s"], "unit": "atom-steps/s",

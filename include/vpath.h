@@ -316,13 +316,19 @@ int sim_set_variants(sim_handle *h, int32_t pair_variant, int32_t cv_variant);
  * barriers between phases, each polling a bounded number of times: when one
  * gives up the call returns SIM_ETIMEOUT and the step is incomplete; the
  * environment variable VPATH_SPIN_LIMIT, read at sim_create, sets the bound
- * for fault-injection tests), for batches too small to fill the GPU.  Both
- * forms give bit-identical states.  SIM_EINVAL for another mode.
+ * for fault-injection tests), for batches too small to fill the GPU;
+ * mode 2: as mode 0, but in the captured chunks the column sort, copy-back
+ * and list build of a step sit in conditional graph nodes that the rebuild
+ * front opens only when some trial rebuilds in that step (small batches,
+ * where most steps rebuild nothing and those launches are pure latency).
+ * All forms give bit-identical states.  SIM_EINVAL for another mode.
  * sim_step_mode returns the current form.  sim_autotune_step times reps
- * chunks of nstlist steps in each form, keeps the faster (*mode, may be NULL;
- * ms_per_step[2], may be NULL, receives both forms' milliseconds per step)
- * and restores the state it started from (positions, velocities, z_m, Phi,
- * step counter; the lists are rebuilt). */
+ * chunks of nstlist steps in each form, keeps the fastest (*mode, may be NULL;
+ * ms_per_step[SIM_STEP_MODES], may be NULL, receives every form's
+ * milliseconds per step, indexed by mode) and restores the state it started
+ * from (positions, velocities, z_m, Phi, step counter; the lists are
+ * rebuilt). */
+#define SIM_STEP_MODES 3
 int sim_set_step_mode(sim_handle *h, int32_t mode);
 int32_t sim_step_mode(const sim_handle *h);
 int sim_autotune_step(sim_handle *h, int32_t reps, int32_t *mode, double *ms_per_step);

@@ -396,8 +396,14 @@ def sim_set_class_variants(h, variants):
     _check(h, load().sim_set_class_variants(h, v.ctypes.data, len(v)))
 
 
+STEP_MODES = 3
+STEP_FORM_NAMES = ("kernel per phase", "one kernel", "kernel per phase, rebuild kernels only in rebuild steps")
+
+
 def sim_set_step_mode(h, mode: int):
-    """0: one kernel per phase (graph replays); 1: one cooperative kernel per step."""
+    """0: one kernel per phase (graph replays); 1: one cooperative kernel per
+    step; 2: as 0, the rebuild kernels in conditional graph nodes opened only
+    in steps in which a trial rebuilds."""
     _check(h, load().sim_set_step_mode(h, int(mode)))
 
 
@@ -406,10 +412,10 @@ def sim_step_mode(h) -> int:
 
 
 def sim_autotune_step(h, reps: int = 3, times: bool = False):
-    """Times both step forms on this batch, keeps the faster; the state is
-    restored.  Returns the form (and, with times, both forms' ms per step)."""
+    """Times every step form on this batch, keeps the fastest; the state is
+    restored.  Returns the form (and, with times, every form's ms per step)."""
     m = C.c_int32(0)
-    ms = np.full(2, np.nan)
+    ms = np.full(STEP_MODES, np.nan)
     _check(h, load().sim_autotune_step(h, int(reps), C.byref(m), ms.ctypes.data))
     return (int(m.value), [float(x) for x in ms]) if times else int(m.value)
 

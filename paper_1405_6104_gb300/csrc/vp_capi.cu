@@ -6,6 +6,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <functional>
 #include <map>
 #include <string>
 #include <vector>
@@ -39,6 +40,7 @@ struct sim_handle {
   // finaliser) reads only positions, so it runs beside the list build and the
   // pair forces, joined before the next update
   cudaStream_t side = nullptr;
+  cudaStream_t cstream = nullptr;  // captures the bodies of conditional nodes (step form 2)
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   Dev d{};
   SimConst c{};
@@ -76,6 +78,8 @@ struct sim_handle {
   // true = one cooperative kernel per step (replayed in graphs when the
   // capture succeeds, else launched directly)
   bool fused = false, fused_no_graph = false;
+  bool skip_empty = false;  // step form 2: graph nodes of the later rebuild kernels only when a trial rebuilds
+  bool capture_failed = false;  // a conditional node could not be added while capturing a chunk
   // CV-frame recorder (one trial)
   int frame_trial = -1, frame_cap = 0;
   float *frames = nullptr;
@@ -260,6 +264,42 @@ void after_forces(sim_handle *h, FinMode mode) {
 }
 
 constexpr int NO_REQUEST = -2;  // forces(): no forced list rebuild
+constexpr int STEP_MODES = SIM_STEP_MODES;
+
+// Adds to the graph being captured on h->stream a conditional node whose body
+// is captured from `body` (launches on the stream given to it); returns the
+// handle (the kernel that sets it must come earlier in the same graph).
+int add_conditional(sim_handle *h, cudaGraphConditionalHandle hc, const std::function<void(cudaStream_t)> &body) {
+  cudaStreamCaptureStatus st;
+  cudaGraph_t g;
+  const cudaGraphNode_t *deps = nullptr;
+  const cudaGraphEdgeData *ed = nullptr;
+  size_t nd = 0;
+  CK(cudaStreamGetCaptureInfo(h->stream, &st, nullptr, &g, &deps, &ed, &nd));
+  cudaGraphNodeParams cp = {};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = hc;
+  cp.conditional.type = cudaGraphCondTypeIf;
+  cp.conditional.size = 1;
+  cudaGraphNode_t node;
+  CK(cudaGraphAddNode(&node, g, deps, ed, nd, &cp));
+  cudaGraph_t bg = cp.conditional.phGraph_out[0];
+  CK(cudaStreamUpdateCaptureDependencies(h->stream, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+  CK(cudaStreamBeginCaptureToGraph(h->cstream, bg, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  body(h->cstream);
+  CK(cudaStreamEndCapture(h->cstream, &bg));
+  return SIM_OK;
+}
+
+// a new conditional handle of the graph being captured on h->stream (its
+// value is 1 unless a kernel of the graph sets it)
+int new_conditional(sim_handle *h, cudaGraphConditionalHandle *hc) {
+  cudaStreamCaptureStatus st;
+  cudaGraph_t g;
+  CK(cudaStreamGetCaptureInfo(h->stream, &st, nullptr, &g, nullptr, nullptr, nullptr));
+  CK(cudaGraphConditionalHandleCreate(hc, g, 1u, cudaGraphCondAssignDefault));
+  return SIM_OK;
+}
 
 // forces of the current positions.  The rebuild kernels run every time and
 // rebuild the lists that are due (a displacement beyond the buffer, the
@@ -272,6 +312,37 @@ constexpr int NO_REQUEST = -2;  // forces(): no forced list rebuild
 // order-independent fixed-point sums, so both orders give bit-identical states.
 void forces(sim_handle *h, FinMode mode, int request) {
   if (request != NO_REQUEST) launch_rebuild_request(h->d, request, h->stream);
+  if (h->skip_empty && h->cap_k >= 0 && request == NO_REQUEST && h->side && !h->timing) {
+    // step form 2 inside a captured chunk: the column sort, copy-back and
+    // list build sit in conditional nodes that the front kernel opens only
+    // when a trial rebuilds in this step (the same kernels otherwise)
+    cudaGraphConditionalHandle hc[2];
+    if (new_conditional(h, &hc[0]) || new_conditional(h, &hc[1])) {
+      h->capture_failed = true;
+      return;
+    }
+    launch_front(h->d, h->c, h->half_skin2, h->strict_skin, false, h->stream, hc);
+    if (add_conditional(h, hc[0], [&](cudaStream_t cs) {
+          launch_colsort(h->d, cs);
+          launch_copyback(h->d, cs);
+        })) {
+      h->capture_failed = true;
+      return;
+    }
+    cudaEventRecord(h->ev_fork, h->stream);
+    cudaStreamWaitEvent(h->side, h->ev_fork, 0);
+    cv_forces(h, mode, h->side);
+    cudaEventRecord(h->ev_join, h->side);
+    if (add_conditional(h, hc[1], [&](cudaStream_t cs) { launch_list(h->d, h->c, h->rl2_bbox, cs); })) {
+      h->capture_failed = true;
+      cudaStreamWaitEvent(h->stream, h->ev_join, 0);  // the side branch still joins the capture
+      return;
+    }
+    pair_forces(h);
+    cudaStreamWaitEvent(h->stream, h->ev_join, 0);
+    after_forces(h, mode);
+    return;
+  }
   rebuild_cols(h, request != NO_REQUEST);
   if (h->side && !h->timing) {
     cudaEventRecord(h->ev_fork, h->stream);
@@ -352,12 +423,18 @@ int capture_chunk(sim_handle *h) {
   // to rebuild, so a chunk replays from any step
   const int nst = h->params.nstlist;
   CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+  h->capture_failed = false;
   for (int k = 0; k < nst; ++k) {
     h->cap_k = k;
     one_step(h);
   }
   h->cap_k = -1;
   CK(cudaStreamEndCapture(h->stream, &g));
+  if (h->capture_failed) {
+    cudaGraphDestroy(g);
+    const std::string why = h->err;
+    return fail(h, SIM_ECUDA, "a conditional graph node could not be captured: " + why);
+  }
   cudaError_t e = cudaGraphInstantiate(&h->chunk, g, 0);
   cudaGraphDestroy(g);
   if (e != cudaSuccess) {
@@ -434,6 +511,7 @@ VP_API int sim_create(const sim_system *systems, int32_t n_systems, const int32_
   cudaEventCreateWithFlags(&h->entry_ev, cudaEventDisableTiming);
   cudaEventCreateWithFlags(&h->exit_ev, cudaEventDisableTiming);
   if (cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&h->cstream, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) != cudaSuccess)
     return bail(fail(h, SIM_ECUDA, "cudaStreamCreate / cudaEventCreate failed"));
@@ -1505,8 +1583,12 @@ VP_API int sim_set_class_variants(sim_handle *h, const int32_t *variants, int32_
 
 VP_API int sim_set_step_mode(sim_handle *h, int32_t mode) {
   if (!h) return SIM_EINVAL;
-  if (mode != 0 && mode != 1) return fail(h, SIM_EINVAL, "step mode must be 0 (kernel per phase) or 1 (one kernel)");
+  if (mode < 0 || mode >= STEP_MODES)
+    return fail(h, SIM_EINVAL,
+                "step mode must be 0 (kernel per phase), 1 (one kernel) or 2 (kernel per phase, rebuild kernels "
+                "only in steps with a rebuild)");
   h->fused = mode == 1;
+  h->skip_empty = mode == 2;
   if (h->chunk) {
     cudaGraphExecDestroy(h->chunk);
     h->chunk = nullptr;
@@ -1514,7 +1596,9 @@ VP_API int sim_set_step_mode(sim_handle *h, int32_t mode) {
   return SIM_OK;
 }
 
-VP_API int32_t sim_step_mode(const sim_handle *h) { return h ? (h->fused ? 1 : 0) : SIM_EINVAL; }
+VP_API int32_t sim_step_mode(const sim_handle *h) {
+  return h ? (h->fused ? 1 : h->skip_empty ? 2 : 0) : SIM_EINVAL;
+}
 
 VP_API int sim_autotune_step(sim_handle *h, int32_t reps, int32_t *mode, double *ms_per_step) {
   int r = enter(h);
@@ -1572,11 +1656,11 @@ VP_API int sim_autotune_step(sim_handle *h, int32_t reps, int32_t *mode, double 
     return check_flags(h);
   };
   float best = 3e38f;
-  int pick = h->fused ? 1 : 0;
+  int pick = sim_step_mode(h);
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  for (int m = 0; m < 2 && r == SIM_OK; ++m) {
+  for (int m = 0; m < STEP_MODES && r == SIM_OK; ++m) {
     r = sim_set_step_mode(h, m);
     if (!r) r = sim_step_batch(h, nst);  // captures the chunk graph
     if (!r) {
@@ -1873,6 +1957,7 @@ VP_API void sim_destroy(sim_handle *h) {
   if (h->ev_fork) cudaEventDestroy(h->ev_fork);
   if (h->ev_join) cudaEventDestroy(h->ev_join);
   if (h->side) cudaStreamDestroy(h->side);
+  if (h->cstream) cudaStreamDestroy(h->cstream);
   if (h->stream) cudaStreamDestroy(h->stream);
   delete h;
 }

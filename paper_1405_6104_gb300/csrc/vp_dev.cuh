@@ -140,7 +140,7 @@ void launch_rebuild_request(const Dev &d, int32_t trial, cudaStream_t s);
 // which trials rebuild (forced_only: those with a forced request), then
 // binning, column scans and bucket fills of those trials
 void launch_front(const Dev &d, const SimConst &c, float half_skin2, int strict_skin, bool forced_only,
-                  cudaStream_t s);
+                  cudaStream_t s, const cudaGraphConditionalHandle *cond = nullptr);  // cond: two handles, or none
 void launch_colsort(const Dev &d, cudaStream_t s);
 // the re-sorted layout replaces the current one; stamps the rebuild step
 void launch_copyback(const Dev &d, cudaStream_t s);

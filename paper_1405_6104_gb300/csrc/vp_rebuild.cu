@@ -52,11 +52,24 @@ __global__ void k_rebuild_request(Dev d, int trial) {
 // trials that the later kernels walk.  No block writes what another reads to
 // decide (the requests, the last-rebuild stamps: the copy-back stamps them).
 // ---------------------------------------------------------------------------
+// cond_a, cond_b (with set_cond): conditional nodes of a captured graph
+// around the later rebuild kernels, opened only when a trial rebuilds
 __global__ void __cluster_dims__(FRONT_CLUSTER, 1, 1) __launch_bounds__(FRONT_THREADS, 1)
-    k_front(Dev d, SimConst c, float half_skin2, int strict, int forced_only) {
+    k_front(Dev d, SimConst c, float half_skin2, int strict, int forced_only, cudaGraphConditionalHandle cond_a,
+            cudaGraphConditionalHandle cond_b, int set_cond) {
   __shared__ FrontShared sh;
   const unsigned long long n = *d.cur_step;
-  if (blockIdx.x == 0) decide_rebuilds(d, c, n, forced_only != 0);
+  if (blockIdx.x == 0) {
+    decide_rebuilds(d, c, n, forced_only != 0);
+    if (set_cond) {
+      __syncthreads();  // every decision is counted
+      if (threadIdx.x == 0) {
+        const unsigned any = d.rb_cnt[0] != 0u ? 1u : 0u;
+        cudaGraphSetConditional(cond_a, any);
+        cudaGraphSetConditional(cond_b, any);
+      }
+    }
+  }
   const int n_clusters = (int)gridDim.x / FRONT_CLUSTER;
   // the whole cluster takes the same trials (the same decision in every block)
   for (int t = (int)blockIdx.x / FRONT_CLUSTER; t < d.n_trials; t += n_clusters) {
@@ -132,9 +145,10 @@ void launch_rebuild_request(const Dev &d, int32_t trial, cudaStream_t s) {
   k_rebuild_request<<<(d.n_trials + 255) / 256, 256, 0, s>>>(d, trial);
 }
 void launch_front(const Dev &d, const SimConst &c, float half_skin2, int strict_skin, bool forced_only,
-                  cudaStream_t s) {
+                  cudaStream_t s, const cudaGraphConditionalHandle *cond) {
   const unsigned clusters = (unsigned)std::min(d.n_trials, 16384);
-  k_front<<<clusters * FRONT_CLUSTER, FRONT_THREADS, 0, s>>>(d, c, half_skin2, strict_skin, forced_only ? 1 : 0);
+  k_front<<<clusters * FRONT_CLUSTER, FRONT_THREADS, 0, s>>>(d, c, half_skin2, strict_skin, forced_only ? 1 : 0,
+                                                             cond ? cond[0] : 0, cond ? cond[1] : 0, cond ? 1 : 0);
 }
 void launch_list_positions(const Dev &d, int32_t trial, double *out, int32_t n, cudaStream_t s) {
   if (n > 0) k_list_positions<<<(n + 255) / 256, 256, 0, s>>>(d, trial, out, n);

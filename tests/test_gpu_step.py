@@ -1,7 +1,8 @@
 """The one-kernel step (every phase of every trial in one cooperative kernel,
-grid barriers between phases) against the kernel-per-phase step: the same
-device code per phase, so the states must agree bit for bit, with list
-rebuilds, on single trials and on a mixed batch; a grid barrier whose poll
+grid barriers between phases), and the kernel-per-phase step whose rebuild
+kernels sit in conditional graph nodes, against the kernel-per-phase step:
+the same device code per phase, so the states must agree bit for bit, with
+list rebuilds, on single trials and on a mixed batch; a grid barrier whose poll
 bound runs out ends the call with SIM_ETIMEOUT and leaves the GPU usable;
 the step-form autotuner restores the state it started from."""
 import numpy as np
@@ -29,8 +30,9 @@ def _run(systems, p, tps, seeds, mode, calls):
         return [b.get_state(t) for t in range(b.n_trials)], diag
 
 
+@pytest.mark.parametrize("mode", [1, 2])
 @pytest.mark.parametrize("which", ["small", "mixed", "benchmarked"])
-def test_one_kernel_step_is_bit_identical(which):
+def test_step_forms_are_bit_identical(which, mode):
     if which == "small":
         s, p = S.small_solvated()
         args = ([s], p, [1], [9])
@@ -43,7 +45,7 @@ def test_one_kernel_step_is_bit_identical(which):
         args = ([s], p, [1], [1000])
     calls = (20, 7, 13)  # graph chunks, direct steps, both
     ref, d0 = _run(*args, 0, calls)
-    got, d1 = _run(*args, 1, calls)
+    got, d1 = _run(*args, mode, calls)
     for x, y in zip(ref, got):
         assert np.array_equal(x[0], y[0]) and np.array_equal(x[1], y[1])
         assert x[2][3] == y[2][3] and x[2][1] == y[2][1]
@@ -74,7 +76,7 @@ def test_step_form_autotuner_restores_the_state():
         before = [b.get_state(t) for t in range(2)]
         step0 = B.sim_step_count(b.h)
         mode = B.sim_autotune_step(b.h, 2)
-        assert mode in (0, 1) and B.sim_step_mode(b.h) == mode
+        assert mode in (0, 1, 2) and B.sim_step_mode(b.h) == mode
         assert B.sim_step_count(b.h) == step0
         for t in range(2):
             pos, vel, cv = b.get_state(t)
