@@ -85,6 +85,7 @@ __global__ void k_zconst(Dev d, const int32_t *sys_tile0, const int32_t *sys_nti
 template <int CV_WARPS>
 __global__ void __launch_bounds__(CV_WARPS * 32) k_cv(Dev d, SimConst c) {
   __shared__ CvWarpShared sh[CV_WARPS];
+  PDL_WAIT();
   const int wib = threadIdx.x >> 5;
   const int wq = blockIdx.x * CV_WARPS + wib;
   if (wq >= d.total_work) return;
@@ -101,6 +102,7 @@ __global__ void __launch_bounds__(CV_WARPS * 32) k_cv(Dev d, SimConst c) {
 template <int MODE>
 __global__ void __launch_bounds__(CVFIN_THREADS) k_cvfin(Dev d, SimConst c) {
   __shared__ CvfinShared sh;
+  PDL_WAIT();
   cvfin_trial<MODE>(d, c, sh, blockIdx.x);
 }
 
@@ -139,15 +141,16 @@ void launch_zconst(const Dev &d, const int32_t *sys_tile0, const int32_t *sys_nt
 // variants: 0: 4 warps per block, 1: 2 warps, 2: 8 warps
 void launch_cv(const Dev &d, const SimConst &c, cudaStream_t s, int variant) {
   if (d.total_work <= 0) return;
-  if (variant == 1) k_cv<2><<<(unsigned)((d.total_work + 1) / 2), 64, 0, s>>>(d, c);
-  else if (variant == 2) k_cv<8><<<(unsigned)((d.total_work + 7) / 8), 256, 0, s>>>(d, c);
-  else k_cv<4><<<(unsigned)((d.total_work + 3) / 4), 128, 0, s>>>(d, c);
+  if (variant == 1) launch_pdl(k_cv<2>, dim3((unsigned)((d.total_work + 1) / 2)), dim3(64), s, d, c);
+  else if (variant == 2) launch_pdl(k_cv<8>, dim3((unsigned)((d.total_work + 7) / 8)), dim3(256), s, d, c);
+  else launch_pdl(k_cv<4>, dim3((unsigned)((d.total_work + 3) / 4)), dim3(128), s, d, c);
 }
 void launch_cvfin(const Dev &d, const SimConst &c, FinMode mode, cudaStream_t s) {
-  if (mode == FIN_STEP) k_cvfin<FIN_STEP><<<d.n_trials, CVFIN_THREADS, 0, s>>>(d, c);
-  else if (mode == FIN_INIT) k_cvfin<FIN_INIT><<<d.n_trials, CVFIN_THREADS, 0, s>>>(d, c);
-  else if (mode == FIN_RESTORE) k_cvfin<FIN_RESTORE><<<d.n_trials, CVFIN_THREADS, 0, s>>>(d, c);
-  else k_cvfin<FIN_KEEP><<<d.n_trials, CVFIN_THREADS, 0, s>>>(d, c);
+  const dim3 g((unsigned)d.n_trials), b(CVFIN_THREADS);
+  if (mode == FIN_STEP) launch_pdl(k_cvfin<FIN_STEP>, g, b, s, d, c);
+  else if (mode == FIN_INIT) launch_pdl(k_cvfin<FIN_INIT>, g, b, s, d, c);
+  else if (mode == FIN_RESTORE) launch_pdl(k_cvfin<FIN_RESTORE>, g, b, s, d, c);
+  else launch_pdl(k_cvfin<FIN_KEEP>, g, b, s, d, c);
 }
 
 }  // namespace vp

@@ -134,6 +134,28 @@ struct CvfinShared {
 // forced list rebuild (nothing recorded)
 enum FinMode { FIN_STEP = 0, FIN_INIT = 1, FIN_RESTORE = 2, FIN_KEEP = 3 };
 
+// Programmatic dependent launch: a kernel that follows another kernel on
+// the same stream may be launched while that one drains (its launch latency
+// then overlaps the other's tail); such a kernel starts with PDL_WAIT, which
+// returns once the preceding kernel has completed and its writes are
+// visible (a no-op for an ordinary launch).
+#define PDL_WAIT() cudaGridDependencySynchronize()
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, cudaStream_t s, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
 // rebuild (vp_rebuild.cu)
 // a forced rebuild of one trial (trial >= 0) or of all in the step held now
 void launch_rebuild_request(const Dev &d, int32_t trial, cudaStream_t s);

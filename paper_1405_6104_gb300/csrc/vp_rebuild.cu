@@ -58,6 +58,7 @@ __global__ void __cluster_dims__(FRONT_CLUSTER, 1, 1) __launch_bounds__(FRONT_TH
     k_front(Dev d, SimConst c, float half_skin2, int strict, int forced_only, cudaGraphConditionalHandle cond_a,
             cudaGraphConditionalHandle cond_b, int set_cond) {
   __shared__ FrontShared sh;
+  PDL_WAIT();
   const unsigned long long n = *d.cur_step;
   if (blockIdx.x == 0) {
     decide_rebuilds(d, c, n, forced_only != 0);
@@ -86,6 +87,7 @@ __global__ void __cluster_dims__(FRONT_CLUSTER, 1, 1) __launch_bounds__(FRONT_TH
 
 __global__ void __launch_bounds__(128) k_colsort(Dev d) {
   __shared__ ColsortShared sh;
+  PDL_WAIT();
   FOR_REBUILD_ITEMS(d.max_trial_cols, t, piece) {
     __syncthreads();  // the previous column's shared arrays are no longer read
     colsort_column(d, sh, t, piece);
@@ -96,6 +98,7 @@ __global__ void __launch_bounds__(128) k_colsort(Dev d) {
 // counter (their lists differ in length)
 __global__ void __launch_bounds__(LIST_WARPS * 32, 8) k_list(Dev d, SimConst c, float rl2_bbox) {
   __shared__ ListShared sh;
+  PDL_WAIT();
   const int lane = threadIdx.x & 31;
   const int n_items = (int)d.rb_cnt[0] * d.max_trial_clus;
   for (;;) {
@@ -112,6 +115,7 @@ __global__ void __launch_bounds__(LIST_WARPS * 32, 8) k_list(Dev d, SimConst c, 
 // and its positions are the ones the new list is built from
 
 __global__ void k_copyback(Dev d) {
+  PDL_WAIT();
   const int per = (d.max_trial_slots + 255) / 256;
   const uint32_t n32 = (uint32_t)*d.cur_step;
   FOR_REBUILD_ITEMS(per, t, piece) {
@@ -147,21 +151,23 @@ void launch_rebuild_request(const Dev &d, int32_t trial, cudaStream_t s) {
 void launch_front(const Dev &d, const SimConst &c, float half_skin2, int strict_skin, bool forced_only,
                   cudaStream_t s, const cudaGraphConditionalHandle *cond) {
   const unsigned clusters = (unsigned)std::min(d.n_trials, 16384);
-  k_front<<<clusters * FRONT_CLUSTER, FRONT_THREADS, 0, s>>>(d, c, half_skin2, strict_skin, forced_only ? 1 : 0,
-                                                             cond ? cond[0] : 0, cond ? cond[1] : 0, cond ? 1 : 0);
+  launch_pdl(k_front, dim3(clusters * FRONT_CLUSTER), dim3(FRONT_THREADS), s, d, c, half_skin2, strict_skin,
+             forced_only ? 1 : 0, cond ? cond[0] : cudaGraphConditionalHandle(0),
+             cond ? cond[1] : cudaGraphConditionalHandle(0), cond ? 1 : 0);
 }
 void launch_list_positions(const Dev &d, int32_t trial, double *out, int32_t n, cudaStream_t s) {
   if (n > 0) k_list_positions<<<(n + 255) / 256, 256, 0, s>>>(d, trial, out, n);
 }
 void launch_colsort(const Dev &d, cudaStream_t s) {
   // columns hold about 100 atoms: 128 threads keep every thread busy in the sort
-  k_colsort<<<rebuild_grid(d, 8, d.max_trial_cols), 128, 0, s>>>(d);
+  launch_pdl(k_colsort, dim3(rebuild_grid(d, 8, d.max_trial_cols)), dim3(128), s, d);
 }
 void launch_copyback(const Dev &d, cudaStream_t s) {
-  k_copyback<<<rebuild_grid(d, 4, (d.max_trial_slots + 255) / 256), 256, 0, s>>>(d);
+  launch_pdl(k_copyback, dim3(rebuild_grid(d, 4, (d.max_trial_slots + 255) / 256)), dim3(256), s, d);
 }
 void launch_list(const Dev &d, const SimConst &c, float rl2_bbox, cudaStream_t s) {
-  k_list<<<rebuild_grid(d, 8, (d.max_trial_clus + LIST_WARPS - 1) / LIST_WARPS), LIST_WARPS * 32, 0, s>>>(d, c, rl2_bbox);
+  launch_pdl(k_list, dim3(rebuild_grid(d, 8, (d.max_trial_clus + LIST_WARPS - 1) / LIST_WARPS)), dim3(LIST_WARPS * 32),
+             s, d, c, rl2_bbox);
 }
 
 }  // namespace vp
