@@ -42,6 +42,8 @@ struct sim_handle {
   cudaStream_t side = nullptr;
   cudaStream_t cstream = nullptr;  // captures the bodies of conditional nodes (step form 2)
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  cudaStream_t bstream = nullptr;  // the bonded forces, beside the reaction coordinate
+  cudaEvent_t ev_bjoin = nullptr;
   Dev d{};
   SimConst c{};
   sim_params params{};
@@ -237,12 +239,31 @@ void pair_forces(sim_handle *h) {
   }
 }
 
-// the second branch of a force evaluation: bonded forces, then the reaction
-// coordinate and its finaliser
+// the forces beside the pair kernel, on one stream: bonded forces, then the
+// reaction coordinate and its finaliser
 void cv_forces(sim_handle *h, FinMode mode, cudaStream_t s) {
   timed(h, "bonded", [&] { launch_bonded(h->d, s); });
   timed(h, "cv", [&] { launch_cv(h->d, h->c, s, h->cv_variant); });
   timed(h, "cvfin", [&] { launch_cvfin(h->d, h->c, mode, s); });
+}
+
+// ... or as two branches forked from the main stream: the reaction
+// coordinate and its finaliser on the second stream, the bonded forces on a
+// third (none reads what another writes; forces meet in order-independent
+// fixed-point sums); join_side brings both back
+void fork_side(sim_handle *h, FinMode mode) {
+  cudaEventRecord(h->ev_fork, h->stream);
+  cudaStreamWaitEvent(h->side, h->ev_fork, 0);
+  cudaStreamWaitEvent(h->bstream, h->ev_fork, 0);
+  launch_cv(h->d, h->c, h->side, h->cv_variant, false);
+  launch_cvfin(h->d, h->c, mode, h->side);
+  cudaEventRecord(h->ev_join, h->side);
+  launch_bonded(h->d, h->bstream);
+  cudaEventRecord(h->ev_bjoin, h->bstream);
+}
+void join_side(sim_handle *h) {
+  cudaStreamWaitEvent(h->stream, h->ev_join, 0);
+  cudaStreamWaitEvent(h->stream, h->ev_bjoin, 0);
 }
 
 // reaction-coordinate atoms per frame: of the recorded trial, or the largest
@@ -329,29 +350,23 @@ void forces(sim_handle *h, FinMode mode, int request) {
       h->capture_failed = true;
       return;
     }
-    cudaEventRecord(h->ev_fork, h->stream);
-    cudaStreamWaitEvent(h->side, h->ev_fork, 0);
-    cv_forces(h, mode, h->side);
-    cudaEventRecord(h->ev_join, h->side);
+    fork_side(h, mode);
     if (add_conditional(h, hc[1], [&](cudaStream_t cs) { launch_list(h->d, h->c, h->rl2_bbox, cs); })) {
       h->capture_failed = true;
-      cudaStreamWaitEvent(h->stream, h->ev_join, 0);  // the side branch still joins the capture
+      join_side(h);  // the side branches still join the capture
       return;
     }
     pair_forces(h);
-    cudaStreamWaitEvent(h->stream, h->ev_join, 0);
+    join_side(h);
     after_forces(h, mode);
     return;
   }
   rebuild_cols(h, request != NO_REQUEST);
   if (h->side && !h->timing) {
-    cudaEventRecord(h->ev_fork, h->stream);
-    cudaStreamWaitEvent(h->side, h->ev_fork, 0);
-    cv_forces(h, mode, h->side);
-    cudaEventRecord(h->ev_join, h->side);
+    fork_side(h, mode);
     rebuild_list(h);
     pair_forces(h);
-    cudaStreamWaitEvent(h->stream, h->ev_join, 0);
+    join_side(h);
   } else {
     rebuild_list(h);
     pair_forces(h);
@@ -512,6 +527,8 @@ VP_API int sim_create(const sim_system *systems, int32_t n_systems, const int32_
   cudaEventCreateWithFlags(&h->exit_ev, cudaEventDisableTiming);
   if (cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking) != cudaSuccess ||
       cudaStreamCreateWithFlags(&h->cstream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&h->bstream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_bjoin, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) != cudaSuccess)
     return bail(fail(h, SIM_ECUDA, "cudaStreamCreate / cudaEventCreate failed"));
@@ -1943,6 +1960,7 @@ VP_API void sim_destroy(sim_handle *h) {
   cudaSetDevice(h->device);
   if (h->stream) cudaStreamSynchronize(h->stream);
   if (h->side) cudaStreamSynchronize(h->side);
+  if (h->bstream) cudaStreamSynchronize(h->bstream);
   if (h->chunk) cudaGraphExecDestroy(h->chunk);
   for (auto &e : h->gev) cudaEventDestroy(e);
   for (void *p : h->callocs) cudaFree(p);
@@ -1956,7 +1974,9 @@ VP_API void sim_destroy(sim_handle *h) {
   if (h->exit_ev) cudaEventDestroy(h->exit_ev);
   if (h->ev_fork) cudaEventDestroy(h->ev_fork);
   if (h->ev_join) cudaEventDestroy(h->ev_join);
+  if (h->ev_bjoin) cudaEventDestroy(h->ev_bjoin);
   if (h->side) cudaStreamDestroy(h->side);
+  if (h->bstream) cudaStreamDestroy(h->bstream);
   if (h->cstream) cudaStreamDestroy(h->cstream);
   if (h->stream) cudaStreamDestroy(h->stream);
   delete h;

@@ -139,11 +139,21 @@ void launch_zconst(const Dev &d, const int32_t *sys_tile0, const int32_t *sys_nt
   k_zconst<<<d.n_trials, 256, 0, s>>>(d, sys_tile0, sys_ntiles);
 }
 // variants: 0: 4 warps per block, 1: 2 warps, 2: 8 warps
-void launch_cv(const Dev &d, const SimConst &c, cudaStream_t s, int variant) {
+void launch_cv(const Dev &d, const SimConst &c, cudaStream_t s, int variant, bool after_kernel) {
   if (d.total_work <= 0) return;
-  if (variant == 1) launch_pdl(k_cv<2>, dim3((unsigned)((d.total_work + 1) / 2)), dim3(64), s, d, c);
-  else if (variant == 2) launch_pdl(k_cv<8>, dim3((unsigned)((d.total_work + 7) / 8)), dim3(256), s, d, c);
-  else launch_pdl(k_cv<4>, dim3((unsigned)((d.total_work + 3) / 4)), dim3(128), s, d, c);
+  const int w = variant == 1 ? 2 : variant == 2 ? 8 : 4;
+  const dim3 g((unsigned)((d.total_work + w - 1) / w)), b((unsigned)(32 * w));
+  if (!after_kernel) {  // first on its stream: an ordinary launch
+    if (w == 2) k_cv<2><<<g, b, 0, s>>>(d, c);
+    else if (w == 8) k_cv<8><<<g, b, 0, s>>>(d, c);
+    else k_cv<4><<<g, b, 0, s>>>(d, c);
+  } else if (w == 2) {
+    launch_pdl(k_cv<2>, g, b, s, d, c);
+  } else if (w == 8) {
+    launch_pdl(k_cv<8>, g, b, s, d, c);
+  } else {
+    launch_pdl(k_cv<4>, g, b, s, d, c);
+  }
 }
 void launch_cvfin(const Dev &d, const SimConst &c, FinMode mode, cudaStream_t s) {
   const dim3 g((unsigned)d.n_trials), b(CVFIN_THREADS);

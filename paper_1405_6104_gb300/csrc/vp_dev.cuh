@@ -178,7 +178,8 @@ constexpr int PAIR_VARIANTS = 9;
 void launch_cnat(const Dev &d, const SimConst &c, const double *native, const int32_t *sys_nat0, int32_t n_tiles_total,
                  const int32_t *tile_sys, cudaStream_t s);
 void launch_zconst(const Dev &d, const int32_t *sys_tile0, const int32_t *sys_ntiles, cudaStream_t s);
-void launch_cv(const Dev &d, const SimConst &c, cudaStream_t s, int variant = 0);
+// after_kernel: the launch follows a kernel on its stream (a programmatic launch)
+void launch_cv(const Dev &d, const SimConst &c, cudaStream_t s, int variant = 0, bool after_kernel = true);
 constexpr int CV_VARIANTS = 3;
 void launch_cvfin(const Dev &d, const SimConst &c, FinMode mode, cudaStream_t s);
 void launch_rec_frames(const Dev &d, int trial, int n_cv, int cap, float *frames, cudaStream_t s);
