@@ -401,7 +401,7 @@ def run_gpu(args):
                          "traffic_unit": "bytes per launch (ncu, variant 8)",
                          "launch_ms": pair_avg_s * 1e3, "launches_timed": pair_n,
                          "launch_timing": "event-record nodes around each pair launch inside the replayed graphs of the timed region",
-                         "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz (SM max clock of MEASURED_PEAKS.json)",
+                         "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz (SM max clock: {src})",
                          "work": f"{PAIRS_PER_ATOM_STEP:.0f} half pairs x {FLOPS_PER_PAIR:.0f} flops per atom-step"},
             "hbm_model": {"bytes_per_atom_step": BYTES_PER_ATOM_STEP, "achieved": hbm_achieved,
                           "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": hbm_achieved / pk["hbm_gbs"],

@@ -317,8 +317,8 @@ int sim_set_variants(sim_handle *h, int32_t pair_variant, int32_t cv_variant);
  * gives up the call returns SIM_ETIMEOUT and the step is incomplete; the
  * environment variable VPATH_SPIN_LIMIT, read at sim_create, sets the bound
  * for fault-injection tests), for batches too small to fill the GPU;
- * mode 2: as mode 0, but in the captured chunks the column sort, copy-back
- * and list build of a step sit in conditional graph nodes that the rebuild
+ * mode 2: as mode 0, but in the captured chunks the column sort and the
+ * list build of a step sit in conditional graph nodes that the rebuild
  * front opens only when some trial rebuilds in that step (small batches,
  * where most steps rebuild nothing and those launches are pure latency).
  * All forms give bit-identical states.  SIM_EINVAL for another mode.

@@ -211,7 +211,6 @@ void rebuild_cols(sim_handle *h, bool forced_only) {
   cudaStream_t s = h->stream;
   timed(h, "front", [&] { launch_front(h->d, h->c, h->half_skin2, h->strict_skin, forced_only, s); });
   timed(h, "colsort", [&] { launch_colsort(h->d, s); });
-  timed(h, "copyback", [&] { launch_copyback(h->d, s); });
 }
 
 void rebuild_list(sim_handle *h) {
@@ -334,8 +333,8 @@ int new_conditional(sim_handle *h, cudaGraphConditionalHandle *hc) {
 void forces(sim_handle *h, FinMode mode, int request) {
   if (request != NO_REQUEST) launch_rebuild_request(h->d, request, h->stream);
   if (h->skip_empty && h->cap_k >= 0 && request == NO_REQUEST && h->side && !h->timing) {
-    // step form 2 inside a captured chunk: the column sort, copy-back and
-    // list build sit in conditional nodes that the front kernel opens only
+    // step form 2 inside a captured chunk: the column sort and the list
+    // build sit in conditional nodes that the front kernel opens only
     // when a trial rebuilds in this step (the same kernels otherwise)
     cudaGraphConditionalHandle hc[2];
     if (new_conditional(h, &hc[0]) || new_conditional(h, &hc[1])) {
@@ -345,7 +344,6 @@ void forces(sim_handle *h, FinMode mode, int request) {
     launch_front(h->d, h->c, h->half_skin2, h->strict_skin, false, h->stream, hc);
     if (add_conditional(h, hc[0], [&](cudaStream_t cs) {
           launch_colsort(h->d, cs);
-          launch_copyback(h->d, cs);
         })) {
       h->capture_failed = true;
       return;

@@ -164,8 +164,6 @@ void launch_rebuild_request(const Dev &d, int32_t trial, cudaStream_t s);
 void launch_front(const Dev &d, const SimConst &c, float half_skin2, int strict_skin, bool forced_only,
                   cudaStream_t s, const cudaGraphConditionalHandle *cond = nullptr);  // cond: two handles, or none
 void launch_colsort(const Dev &d, cudaStream_t s);
-// the re-sorted layout replaces the current one; stamps the rebuild step
-void launch_copyback(const Dev &d, cudaStream_t s);
 void launch_list(const Dev &d, const SimConst &c, float rl2_bbox, cudaStream_t s);
 void launch_list_positions(const Dev &d, int32_t trial, double *out, int32_t n, cudaStream_t s);
 // forces (vp_pair.cu)

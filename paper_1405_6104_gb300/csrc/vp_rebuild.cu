@@ -50,7 +50,7 @@ __global__ void k_rebuild_request(Dev d, int trial) {
 // trial; a cluster whose trial is due bins its atoms, scans the columns and
 // fills the column buckets; block 0 also writes the list of rebuilding
 // trials that the later kernels walk.  No block writes what another reads to
-// decide (the requests, the last-rebuild stamps: the copy-back stamps them).
+// decide (the requests, the last-rebuild stamps: the column sort stamps them).
 // ---------------------------------------------------------------------------
 // cond_a, cond_b (with set_cond): conditional nodes of a captured graph
 // around the later rebuild kernels, opened only when a trial rebuilds
@@ -83,14 +83,12 @@ __global__ void __cluster_dims__(FRONT_CLUSTER, 1, 1) __launch_bounds__(FRONT_TH
 // per column: sort by (z, atom index), write the new cluster layout, update
 // slot_of, pad the last cluster and compute cluster bounding boxes
 // ---------------------------------------------------------------------------
-
-
 __global__ void __launch_bounds__(128) k_colsort(Dev d) {
   __shared__ ColsortShared sh;
   PDL_WAIT();
   FOR_REBUILD_ITEMS(d.max_trial_cols, t, piece) {
     __syncthreads();  // the previous column's shared arrays are no longer read
-    colsort_column(d, sh, t, piece);
+    colsort_column<true>(d, sh, t, piece);
   }
 }
 
@@ -108,19 +106,6 @@ __global__ void __launch_bounds__(LIST_WARPS * 32, 8) k_list(Dev d, SimConst c, 
     const int item = (int)__shfl_sync(0xffffffffu, got, 0);
     if (item >= n_items) return;
     list_cluster(d, c, rl2_bbox, sh, d.rb_list[item / d.max_trial_clus], item % d.max_trial_clus);
-  }
-}
-
-// the re-sorted layout replaces the current one (slots of rebuilding trials),
-// and its positions are the ones the new list is built from
-
-__global__ void k_copyback(Dev d) {
-  PDL_WAIT();
-  const int per = (d.max_trial_slots + 255) / 256;
-  const uint32_t n32 = (uint32_t)*d.cur_step;
-  FOR_REBUILD_ITEMS(per, t, piece) {
-    if (piece == 0 && threadIdx.x == 0) d.last_rb[t] = n32;  // the trial's last rebuild
-    copyback_slot(d, t, piece * 256 + threadIdx.x);
   }
 }
 
@@ -161,9 +146,6 @@ void launch_list_positions(const Dev &d, int32_t trial, double *out, int32_t n, 
 void launch_colsort(const Dev &d, cudaStream_t s) {
   // columns hold about 100 atoms: 128 threads keep every thread busy in the sort
   launch_pdl(k_colsort, dim3(rebuild_grid(d, 8, d.max_trial_cols)), dim3(128), s, d);
-}
-void launch_copyback(const Dev &d, cudaStream_t s) {
-  launch_pdl(k_copyback, dim3(rebuild_grid(d, 4, (d.max_trial_slots + 255) / 256)), dim3(256), s, d);
 }
 void launch_list(const Dev &d, const SimConst &c, float rl2_bbox, cudaStream_t s) {
   launch_pdl(k_list, dim3(rebuild_grid(d, 8, (d.max_trial_clus + LIST_WARPS - 1) / LIST_WARPS)), dim3(LIST_WARPS * 32),

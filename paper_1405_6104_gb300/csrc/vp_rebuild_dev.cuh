@@ -1,6 +1,8 @@
 // vp_rebuild_dev.cuh -- device functions of the list rebuild (binning,
-// column scan, bucket fill, column sort, copy-back, cluster-pair list of one
-// i-cluster), shared by the separate kernels and the one-kernel step.
+// column scan, bucket fill, column sort, cluster-pair list of one i-cluster),
+// shared by the separate kernels and the one-kernel step.  The binning stages
+// each live atom (wrapped position, velocity, type, index) in the sort
+// buffers; the column sort writes the new layout from there into the arrays.
 #pragma once
 #include <cooperative_groups.h>
 
@@ -13,8 +15,14 @@ namespace vp {
 // in slot_col; returns the trial's column offset plus the column (the index
 // into the per-column arrays), or -1 for a slot without an atom.
 __device__ __forceinline__ int bin_loaded(const Dev &d, const SimConst &c, const TrialInfo &T, float half_skin2,
-                                          int strict, int t, int slot, bool live, float4 p, unsigned long long n) {
+                                          int strict, int t, int slot, bool live, int o, float4 p,
+                                          unsigned long long n) {
   if (!live) { d.slot_col[slot] = -1; return -1; }
+  // the slot's atom is staged in the sort buffers (the column sort reads it
+  // there and writes the new layout straight into the arrays themselves)
+  d.vel_b[slot] = d.vel[slot];
+  d.type_b[slot] = d.type[slot];
+  d.orig_b[slot] = o;
   const float L = T.box, iL = T.inv_box;
   if (c.list_fixed && d.rb[d.n_trials + t] != (uint32_t)n) {
     // fixed-interval lists: an atom farther than skin/2 from where the list
@@ -39,7 +47,7 @@ __device__ __forceinline__ int bin_loaded(const Dev &d, const SimConst &c, const
     atomicOr(d.err, ERR_NONFINITE);
     x = y = z = 0.0f;
   }
-  d.pos[slot] = make_float4(x, y, z, p.w);
+  d.pos_b[slot] = make_float4(x, y, z, p.w);
   int cx = max(0, min((int)(x * T.inv_col_w), T.ncol - 1));
   int cy = max(0, min((int)(y * T.inv_col_w), T.ncol - 1));
   const int col = cx * T.ncol + cy;
@@ -54,7 +62,8 @@ __device__ __forceinline__ int bin_slot_col(const Dev &d, const SimConst &c, con
   const int slot = T.slot0 + local;
   const int o = d.orig[slot];
   const bool live = local < n_clus * CL && o >= 0;
-  return bin_loaded(d, c, T, half_skin2, strict, t, slot, live, live ? d.pos[slot] : make_float4(0.f, 0.f, 0.f, 0.f), n);
+  return bin_loaded(d, c, T, half_skin2, strict, t, slot, live, o,
+                    live ? d.pos[slot] : make_float4(0.f, 0.f, 0.f, 0.f), n);
 }
 
 // ... and counted in its column (global counters)
@@ -70,7 +79,7 @@ __device__ __forceinline__ void bin_slot(const Dev &d, const SimConst &c, float 
 }
 
 // STAMP: record this step as the trial's last rebuild here (the front kernel
-// leaves that to the copy-back: its blocks still read the stamps to decide)
+// leaves that to the column sort: its blocks still read the stamps to decide)
 template <int NT, bool STAMP = true>
 __device__ __forceinline__ void colscan_trial(const Dev &d, int (&s_a)[NT], int (&s_c)[NT], int t) {
   const TrialInfo T = d.tinfo[t];
@@ -118,13 +127,15 @@ __device__ __forceinline__ void colscan_trial(const Dev &d, int (&s_a)[NT], int 
     atomicAdd(reinterpret_cast<unsigned long long *>(d.diag + 1), 1ull);
     if (d.rb[t] == n32) atomicAdd(reinterpret_cast<unsigned long long *>(d.diag + 2), 1ull);
   }
-  // slots past the new clusters become empty (the re-sorted layout is copied
-  // over the current one after k_colsort)
+  // slots past the new clusters become empty (their atoms, if any, are
+  // staged in the sort buffers already; the column sort fills the others)
   for (int sl = T.slot0 + total * CL + threadIdx.x; sl < T.slot0 + T.max_clus * CL; sl += NT) {
-    d.orig_b[sl] = -1;
-    d.pos_b[sl] = pad_pos(sl);
-    d.vel_b[sl] = make_float4(0.f, 0.f, 0.f, 0.f);
-    d.type_b[sl] = 0;
+    const float4 pad = pad_pos(sl);
+    d.orig[sl] = -1;
+    d.pos[sl] = pad;
+    d.ref_slot[sl] = pad;
+    d.vel[sl] = make_float4(0.f, 0.f, 0.f, 0.f);
+    d.type[sl] = 0;
   }
 }
 
@@ -199,7 +210,7 @@ __device__ __forceinline__ void front_trial(const Dev &d, const SimConst &c, flo
       const int local = base + u * STRIDE;
       if (local < n_slots) {
         const bool live = local < n_clus * CL && o[u] >= 0;
-        const int cg = bin_loaded(d, c, T, half_skin2, strict, t, T.slot0 + local, live, p[u], n);
+        const int cg = bin_loaded(d, c, T, half_skin2, strict, t, T.slot0 + local, live, o[u], p[u], n);
         if (cg >= 0) {
           const unsigned peers = __match_any_sync(__activemask(), cg);
           if ((threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(cnt0 + (cg - T.col0), __popc(peers));
@@ -247,12 +258,18 @@ struct ColsortShared {
 };
 
 
+// The column's atoms are read from the sort buffers (staged by the binning:
+// the layout before this rebuild) and written in the new order into the
+// arrays themselves.  STAMP: the block of column 0 records this step as the
+// trial's last rebuild.
+template <bool STAMP>
 __device__ __forceinline__ void colsort_column(const Dev &d, ColsortShared &sh, int t, int c) {
   unsigned long long *key = sh.key;
   int *s_old = sh.s_old;
   float *s_zlo = sh.s_zlo;
   const TrialInfo T = d.tinfo[t];
   if (c >= T.ncol * T.ncol) return;
+  if (STAMP && c == 0 && threadIdx.x == 0) d.last_rb[t] = (uint32_t)*d.cur_step;
   const int cg = T.col0 + c;
   int n = d.col_count[cg];
   __syncthreads();
@@ -266,8 +283,8 @@ __device__ __forceinline__ void colsort_column(const Dev &d, ColsortShared &sh, 
   for (int i = threadIdx.x; i < np2; i += blockDim.x) {
     if (i < n) {
       int s = d.bucket[T.atom0 + start + i];
-      float z = d.pos[s].z;
-      key[i] = ((unsigned long long)__float_as_uint(z) << 32) | (unsigned)d.orig[s];
+      float z = d.pos_b[s].z;
+      key[i] = ((unsigned long long)__float_as_uint(z) << 32) | (unsigned)d.orig_b[s];
     } else {
       key[i] = ~0ull;
     }
@@ -299,16 +316,20 @@ __device__ __forceinline__ void colsort_column(const Dev &d, ColsortShared &sh, 
     if (r < n) {
       int old = s_old[r];
       int o = (int)(key[r] & 0xffffffffu);
-      d.pos_b[ns] = d.pos[old];
-      d.vel_b[ns] = d.vel[old];
-      d.orig_b[ns] = o;
-      d.type_b[ns] = d.type[old];
+      const float4 p = d.pos_b[old];
+      d.pos[ns] = p;
+      d.ref_slot[ns] = p;  // the position the new list is built from
+      d.vel[ns] = d.vel_b[old];
+      d.orig[ns] = o;
+      d.type[ns] = d.type_b[old];
       d.slot_of[T.atom0 + o] = ns;
     } else {
-      d.pos_b[ns] = pad_pos(ns);
-      d.vel_b[ns] = make_float4(0.f, 0.f, 0.f, 0.f);
-      d.orig_b[ns] = -1;
-      d.type_b[ns] = 0;
+      const float4 pad = pad_pos(ns);
+      d.pos[ns] = pad;
+      d.ref_slot[ns] = pad;
+      d.vel[ns] = make_float4(0.f, 0.f, 0.f, 0.f);
+      d.orig[ns] = -1;
+      d.type[ns] = 0;
     }
   }
   // bounding boxes of the 4-atom halves of each cluster (real atoms only; an
@@ -318,7 +339,7 @@ __device__ __forceinline__ void colsort_column(const Dev &d, ColsortShared &sh, 
     for (int a = 0; a < CJ; ++a) {
       int r = k * CJ + a;
       if (r >= n) break;
-      float4 p = d.pos[s_old[r]];
+      float4 p = d.pos_b[s_old[r]];
       lo.x = fminf(lo.x, p.x); lo.y = fminf(lo.y, p.y); lo.z = fminf(lo.z, p.z);
       hi.x = fmaxf(hi.x, p.x); hi.y = fmaxf(hi.y, p.y); hi.z = fmaxf(hi.z, p.z);
     }
@@ -718,17 +739,5 @@ __device__ __forceinline__ void list_cluster(const Dev &d, const SimConst &c, fl
   }
 }
 
-
-__device__ __forceinline__ void copyback_slot(const Dev &d, int t, int local) {
-  const TrialInfo &T = d.tinfo[t];
-  if (local >= T.max_clus * CL) return;
-  const int slot = T.slot0 + local;
-  const float4 p = d.pos_b[slot];
-  d.pos[slot] = p;
-  d.ref_slot[slot] = p;
-  d.vel[slot] = d.vel_b[slot];
-  d.orig[slot] = d.orig_b[slot];
-  d.type[slot] = d.type_b[slot];
-}
 
 }  // namespace vp

@@ -112,11 +112,8 @@ __global__ void __launch_bounds__(STEP_THREADS, MINB)
     if (!grid_sync(d.bar, d.err, limit, &s_ok)) return;
     for (int it = blockIdx.x; it < n_rb * d.max_trial_cols; it += gridDim.x) {
       __syncthreads();
-      colsort_column(d, sh.colsort, d.rb_list[it / d.max_trial_cols], it % d.max_trial_cols);
+      colsort_column<false>(d, sh.colsort, d.rb_list[it / d.max_trial_cols], it % d.max_trial_cols);
     }
-    if (!grid_sync(d.bar, d.err, limit, &s_ok)) return;
-    for (int it = blockIdx.x; it < n_rb * per_slots; it += gridDim.x)
-      copyback_slot(d, d.rb_list[it / per_slots], (it % per_slots) * STEP_THREADS + threadIdx.x);
     if (!grid_sync(d.bar, d.err, limit, &s_ok)) return;
     const int n_items = n_rb * d.max_trial_clus;
     for (;;) {
