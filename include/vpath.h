@@ -44,9 +44,10 @@ extern "C" {
 #define SIM_EINVAL (-1)          /* invalid argument or system description */
 #define SIM_ECUDA (-2)           /* a CUDA call failed */
 #define SIM_ELIST_OVERFLOW (-3)  /* a cluster's neighbour list or a grid column exceeded capacity
-                                   (512 entries per cluster; the environment variable
-                                   VPATH_LIST_CAP, read at sim_create, lowers it to 8..511 for
-                                   fault-injection tests) */
+                                   (per 8-atom cluster 2 048 j-atoms with a listed pair, from at
+                                   most 512 4-atom j-clusters; the environment variable
+                                   VPATH_LIST_CAP, read at sim_create, lowers the first to
+                                   8..2047 for fault-injection tests) */
 #define SIM_ESKIN (-4)           /* an atom moved more than skin/2 between fixed-interval list rebuilds
                                    (SIM_FIXED_INTERVAL | SIM_STRICT_SKIN) */
 #define SIM_ENONFINITE (-5)      /* a position, velocity or z became non-finite, a force exceeded
@@ -274,9 +275,10 @@ int phi_frames_refine(sim_handle *h, int32_t trial, double *frames, int32_t n_fr
  *   atoms farther than skin/2 from where their list was built when it was
  *   rebuilt; 0 otherwise, where a list is rebuilt before that can happen), max
  *   list entries of a cluster, list capacity per cluster, clusters in use (all
- *   trials), list entries in use (all trials; each holds 8 x 4 atom pairs, so
- *   32 times this over the atoms is the pair evaluations per atom-step), list
- *   rebuilds of trials since creation, of them triggered by a displacement}. */
+ *   trials), list entries in use (all trials; each is one j-atom against the
+ *   8 atoms of its i-cluster, so 8 times this over the atoms is the pair
+ *   evaluations per atom-step), list rebuilds of trials since creation, of
+ *   them triggered by a displacement}. */
 int sim_pairlist(sim_handle *h, int32_t trial, int32_t *pairs, int64_t cap, int64_t *n_pairs);
 int sim_list_positions(sim_handle *h, int32_t trial, double *pos);
 int sim_diagnostics(sim_handle *h, int64_t *out);

@@ -560,11 +560,11 @@ VP_API int sim_create(const sim_system *systems, int32_t n_systems, const int32_
   c.two_krf = (float)(2.0 * krf);
   c.kR_half = (float)(0.5 * p.k_ratchet);
   c.kR_half_d = 0.5 * p.k_ratchet;
-  c.list_cap = 512;
-  // debug knob (fault injection): a smaller list capacity, 8..512 entries per cluster
+  c.list_cap = LIST_CAP;
+  // debug knob (fault injection): a smaller list capacity, 8..LIST_CAP j-atom entries per cluster
   if (const char *e = std::getenv("VPATH_LIST_CAP")) {
     const int v = std::atoi(e);
-    if (v >= 8 && v <= 512) c.list_cap = v;
+    if (v >= 8 && v <= LIST_CAP) c.list_cap = v;
   }
   ff_split(1.0 / (p.cv_r0 * p.cv_r0), c.cv_inv_r0sq_hi, c.cv_inv_r0sq_lo);
   ff_split(p.cv_r_switch, c.cv_rs_hi, c.cv_rs_lo);
@@ -833,8 +833,8 @@ VP_API int sim_create(const sim_system *systems, int32_t n_systems, const int32_
     }
   }
   Dev &d = h->d;
-  if ((long long)slot0 / CJ + 1 >= (1LL << J_BITS))
-    return bail(fail(h, SIM_EINVAL, "batch too large: list entries address at most 2^25 half clusters"));
+  if ((long long)slot0 + CJ >= (1LL << J_BITS))
+    return bail(fail(h, SIM_EINVAL, "batch too large: list entries address at most 2^25 atom slots"));
   d.n_trials = total_trials;
   d.n_sys = n_systems;
   d.total_slots = slot0;
@@ -847,7 +847,7 @@ VP_API int sim_create(const sim_system *systems, int32_t n_systems, const int32_
   std::vector<float4> pos(slot0 + CJ), vel(slot0);
   for (int k = 0; k < slot0; ++k) pos[k] = pad_pos(k);
   for (int k = slot0; k < slot0 + CJ; ++k) pos[k] = idle_pos();
-  d.idle_entry = make_uint2((uint32_t)(slot0 / CJ) | (NO_SHIFT << J_BITS), 0u);
+  d.idle_entry = (uint32_t)slot0 | (NO_SHIFT << J_BITS);
   std::vector<int32_t> orig(slot0, -1), type(slot0 + CJ, 0), slot_of(total_atoms > 0 ? total_atoms : 1);
   std::vector<TrialState> tstate(total_trials);
   std::vector<int32_t> need_vel(total_trials, 0);
@@ -891,7 +891,9 @@ VP_API int sim_create(const sim_system *systems, int32_t n_systems, const int32_
   r |= dalloc(h, &d.bb_lo, 2 * (size_t)d.total_clus);  // per 4-atom half cluster
   r |= dalloc(h, &d.bb_hi, 2 * (size_t)d.total_clus);
   r |= dalloc(h, &d.list, (size_t)d.total_clus * c.list_cap);
+  r |= dalloc(h, &d.list_m, (size_t)d.total_clus * c.list_cap);
   r |= dalloc(h, &d.list_n, d.total_clus);
+  r |= dalloc(h, &d.list_nm, d.total_clus);
   r |= upload(h, &d.col_trial, col_trial);
   r |= dalloc(h, &d.col_count, col0);
   r |= dalloc(h, &d.col_start, col0);
@@ -955,7 +957,6 @@ VP_API int sim_create(const sim_system *systems, int32_t n_systems, const int32_
     d.max_trial_clus = std::max(d.max_trial_clus, T.max_clus);
     d.max_trial_cols = std::max(d.max_trial_cols, T.ncol * T.ncol);
   }
-  r |= dalloc(h, &d.gdirty, d.total_clus);
   r |= dalloc(h, &h->d_argmin, 1);
   r |= dalloc(h, &h->d_count, 1);
   r |= dalloc(h, &h->d_flag, 1);

@@ -10,9 +10,9 @@ struct Dev {
   int32_t total_slots, total_clus, total_cols, total_work;
   // one 4-atom half cluster past the last slot (pos, type and force arrays
   // hold total_slots + 4 entries) sits at idle_pos(): the entry of a lane
-  // with no list entry to work on points there, so its pairs fall outside
-  // the cut-off with or without the pair masks
-  uint2 idle_entry;
+  // with no list entry to work on points there (with an empty mask), so its
+  // pairs fall outside the cut-off with or without the pair masks
+  uint32_t idle_entry;
   TrialInfo *tinfo;
   TrialState *tstate;
   // slots (cluster order); *_b are the targets of the re-sort at a rebuild
@@ -24,8 +24,12 @@ struct Dev {
   // clusters
   int32_t *clus_trial;                 // static: trial of every i-cluster
   float4 *bb_lo, *bb_hi;               // bounding boxes of the 4-atom half clusters (wrapped positions at rebuild)
-  uint2 *list;                         // [total_clus * list_cap] entries (see vp_internal.cuh)
-  int32_t *list_n;
+  uint32_t *list;                      // [total_clus * list_cap] j-atom entries (see vp_internal.cuh)
+  uint8_t *list_m;                     // [total_clus * list_cap] their pair masks
+  int32_t *list_n;                     // entries per i-cluster ...
+  int32_t *list_nm;                    // ... of which the first list_nm need the pair masks (exclusions,
+                                       // the cluster itself, mixed images); the pair kernels apply the
+                                       // masks in every group of 32 entries that starts below list_nm
   // grid columns
   int32_t *col_trial;                  // static
   int32_t *col_count, *col_start, *col_cstart, *col_fill;
@@ -72,9 +76,6 @@ struct Dev {
   int32_t *rb_list;                    // [n_trials] the trials rebuilding in this step (any order) ...
   uint32_t *rb_cnt;                    // [4]: ... their number, the list kernel's work counter, spare
   int32_t max_trial_slots, max_trial_cols, max_trial_clus;  // largest of any trial
-  uint32_t *gdirty;                    // [clusters] bit k < 31: entries 8k..8k+7 hold exclusions, the
-                                       // cluster itself or mixed images (the pair kernels then apply the
-                                       // pair masks); bit 31: some group from the 31st on does
   double *rec;                         // [n_trials * rec_cap * 5]: z, z_m, a, phi, Q
   unsigned *pair_next;                 // work counters: [0] the persistent pair kernel; [1] the
                                        // one-kernel step's forces phase; [2] spare

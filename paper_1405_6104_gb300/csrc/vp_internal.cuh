@@ -32,15 +32,23 @@ constexpr int ERR_CAPACITY = 8;
 constexpr int ERR_SKIN = 16;
 constexpr int ERR_TIMEOUT = 32;        // a bounded grid barrier of the one-kernel step gave up
 
-// list entry (uint2):
-//   x = 4-atom j-cluster index (bits 0-24) | image shift (bits 25-30: nx+1,
+// list entry of an 8-atom i-cluster: one j-atom, with at least one of the
+// eight pairs in the list --
+//   word (uint32) = j slot (bits 0-24) | image shift (bits 25-30: nx+1,
 //       ny+1, nz+1, two bits each; x_j image = x_j - L n) | E_EXACT (bit 31)
-//       when the pairs of the entry do not share one image (the kernel then
+//       when the j-atom's pairs do not share one image (the kernel then
 //       takes the minimum image pair by pair)
-//   y = mask: bit (a*4 + b) set when i-atom a and j-atom b satisfy the FP32
-//       list rule, are not excluded, are real atoms and (for the cluster
-//       with itself) b's slot follows a's -- the Verlet list proper
+//   mask (uint8, a parallel array): bit a set when i-atom a and the j-atom
+//       satisfy the FP32 list rule, are not excluded, are real atoms and
+//       (inside the i-cluster itself) the j slot follows a's -- the Verlet
+//       list proper.
+// The list build works on 4-atom j-clusters (the same fields, the j-cluster
+// index in bits 0-24 and a 32-bit mask, bit a*4 + b for j-atom b) and then
+// writes one entry per j-atom whose mask column is not empty: the entries
+// whose masks the pair kernels must apply (exclusions, the cluster itself,
+// mixed images) first, the others after them.
 constexpr uint32_t J_BITS = 25;
+constexpr int LIST_CAP = 2048;         // j-atom entries per i-cluster
 constexpr uint32_t J_MASK = (1u << J_BITS) - 1u;
 constexpr uint32_t E_EXACT = 1u << 31;
 // image code of no shift ((0+1) | (0+1) << 2 | (0+1) << 4)
@@ -116,7 +124,7 @@ struct SimConst {
   float kR_half;      // k_R / 2
   double dt_d, kR_half_d;
   int32_t n_types;
-  int32_t list_cap;   // entries per i-cluster
+  int32_t list_cap;   // j-atom entries per i-cluster
   float cv_inv_r0sq_hi, cv_inv_r0sq_lo;   // 1/r0^2 as float-float
   float cv_rs_hi, cv_rs_lo;               // switching start as float-float
   float cv_inv_w_hi, cv_inv_w_lo;         // 1/(r_cut^cv - r_switch) as float-float

@@ -1,10 +1,9 @@
 // vp_pair.cu -- nonbonded (LJ + reaction field) and bonded forces.
 //
-// One warp per 8-atom i-cluster.  Lane (g, b) = (lane >> 2, lane & 3) takes
-// list entry e0 + g and holds atom b of that entry's 4-atom j-cluster; it
-// loops over the 8 i-atoms (kept in registers), so the force on its j-atom
-// is complete after the loop and goes to memory with one 64-bit fixed-point
-// reduction per component.  i-forces stay in registers over the whole list
+// One warp per 8-atom i-cluster.  Lane l takes list entry e0 + l, one j-atom
+// (the list holds only j-atoms with at least one pair in it); it loops over
+// the 8 i-atoms, so the force on its j-atom is complete after the loop and
+// goes to memory with one 64-bit fixed-point reduction per component.  i-forces stay in registers over the whole list
 // and are reduced across the warp at the end.  FP32 pair arithmetic,
 // order-independent int64 accumulation (2^32 units per kJ/mol/nm), so the
 // forces are bit-reproducible.  Bonded forces (each atom computes its own
@@ -94,7 +93,7 @@ __device__ __forceinline__ void pair_block(const float (&xi)[CL], const float (&
       dz = __fmaf_rn(-L, rintf(__fmul_rn(dz, iL)), dz);
     }
     const float r2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
-    const bool in = ((mb >> (4 * a)) & 1u) && (r2 < c.rc2);
+    const bool in = ((mb >> a) & 1u) && (r2 < c.rc2);
     const float rinv = rsqrtf(r2);
     const float rinv2 = __fmul_rn(rinv, rinv);
     const float rinv6 = __fmul_rn(__fmul_rn(rinv2, rinv2), rinv2);
@@ -139,7 +138,6 @@ __global__ void __launch_bounds__(128, MINB) k_pair(Dev d, SimConst c, int only_
   const TrialInfo T = d.tinfo[t];
   if (I - T.clus0 >= d.tstate[t].n_clus) return;
   const float L = T.box, iL = T.inv_box;
-  const int g = lane >> 2, b = lane & 3;
 
   float xi[CL], yi[CL], zi[CL], qi[CL];
   int tio[CL];
@@ -155,26 +153,27 @@ __global__ void __launch_bounds__(128, MINB) k_pair(Dev d, SimConst c, int only_
   float elj = 0.0f, erf = 0.0f;
 
   const int n = d.list_n[I];
-  const uint2 *seg = d.list + (size_t)I * c.list_cap;
-  // software pipeline: the entry two groups ahead and the j-atom of the next
-  // group are in flight while the current group is evaluated; idle lanes get
-  // an empty mask
-  uint2 ent = g < n ? seg[g] : d.idle_entry;
-  uint2 ent_n = 8 + g < n ? seg[8 + g] : d.idle_entry;
-  float4 pj = d.pos[(int)(ent.x & J_MASK) * CJ + b];
-  int tj = d.type[(int)(ent.x & J_MASK) * CJ + b];
-  for (int e0 = 0; e0 < n; e0 += 8) {
-    const uint2 ent_nn = e0 + 16 + g < n ? seg[e0 + 16 + g] : d.idle_entry;
-    const int sj_n = (int)(ent_n.x & J_MASK) * CJ + b;
+  const uint32_t *seg = d.list + (size_t)I * c.list_cap;
+  const uint8_t *segm = d.list_m + (size_t)I * c.list_cap;
+  // one j-atom entry per lane; software pipeline: the entry two groups ahead
+  // and the j-atom of the next group are in flight while the current group is
+  // evaluated; idle lanes get an empty mask
+  uint32_t ent = lane < n ? seg[lane] : d.idle_entry;
+  uint32_t ent_n = 32 + lane < n ? seg[32 + lane] : d.idle_entry;
+  float4 pj = d.pos[(int)(ent & J_MASK)];
+  int tj = d.type[(int)(ent & J_MASK)];
+  for (int e0 = 0; e0 < n; e0 += 32) {
+    const uint32_t ent_nn = e0 + 64 + lane < n ? seg[e0 + 64 + lane] : d.idle_entry;
+    const int sj_n = (int)(ent_n & J_MASK);
     const float4 pj_n = d.pos[sj_n];
     const int tj_n = d.type[sj_n];
-    const int sj = (int)(ent.x & J_MASK) * CJ + b;
-    const unsigned sh = ent.x >> J_BITS;
+    const int sj = (int)(ent & J_MASK);
+    const unsigned sh = ent >> J_BITS;
     const float xj = pj.x - L * (float)((int)(sh & 3u) - 1);
     const float yj = pj.y - L * (float)((int)((sh >> 2) & 3u) - 1);
     const float zj = pj.z - L * (float)((int)((sh >> 4) & 3u) - 1);
-    const unsigned mb = ent.y >> b;
-    const bool exact = (ent.x & E_EXACT) != 0u;
+    const unsigned mb = e0 + lane < n ? segm[e0 + lane] : 0u;
+    const bool exact = (ent & E_EXACT) != 0u;
     float fjx = 0.f, fjy = 0.f, fjz = 0.f;
     if (!__any_sync(0xffffffffu, exact))
       pair_block<false, ENERGY>(xi, yi, zi, qi, tio, xj, yj, zj, pj.w, tj, mb, L, iL, c, tab, tshift, fi, fjx, fjy,
@@ -265,7 +264,6 @@ __global__ void __launch_bounds__(PF_WARPS * 32, MINB) k_pair_f(Dev d, SimConst 
   const TrialInfo T = d.tinfo[t];
   if (I - T.clus0 >= d.tstate[t].n_clus) return;
   const float L = T.box, iL = T.inv_box;
-  const int g = lane >> 2, b = lane & 3;
   const int NT = c.n_types;
 
   float xi[CL], yi[CL], zi[CL], qi[CL];
@@ -295,23 +293,24 @@ __global__ void __launch_bounds__(PF_WARPS * 32, MINB) k_pair_f(Dev d, SimConst 
 #pragma unroll
   for (int a = 0; a < CL; ++a) fi[a][0] = fi[a][1] = fi[a][2] = 0.0f;
 
-  const int n = d.list_n[I];
-  const uint2 *seg = d.list + (size_t)I * c.list_cap;
-  const uint32_t gd = d.gdirty[I];
-  uint2 ent = g < n ? seg[g] : d.idle_entry;
-  uint2 ent_n = 8 + g < n ? seg[8 + g] : d.idle_entry;
-  float4 pj = d.pos[(int)(ent.x & J_MASK) * CJ + b];
-  int tj = d.type[(int)(ent.x & J_MASK) * CJ + b];
-  for (int e0 = 0; e0 < n; e0 += 8) {
-    const uint2 ent_nn = e0 + 16 + g < n ? seg[e0 + 16 + g] : d.idle_entry;
-    const int sj_n = (int)(ent_n.x & J_MASK) * CJ + b;
+  const int n = d.list_n[I], nm = d.list_nm[I];
+  const uint32_t *seg = d.list + (size_t)I * c.list_cap;
+  const uint8_t *segm = d.list_m + (size_t)I * c.list_cap;
+  uint32_t ent = lane < n ? seg[lane] : d.idle_entry;
+  uint32_t ent_n = 32 + lane < n ? seg[32 + lane] : d.idle_entry;
+  float4 pj = d.pos[(int)(ent & J_MASK)];
+  int tj = d.type[(int)(ent & J_MASK)];
+  for (int e0 = 0; e0 < n; e0 += 32) {
+    const uint32_t ent_nn = e0 + 64 + lane < n ? seg[e0 + 64 + lane] : d.idle_entry;
+    const int sj_n = (int)(ent_n & J_MASK);
     const float4 pj_n = d.pos[sj_n];
     const int tj_n = d.type[sj_n];
-    const int sj = (int)(ent.x & J_MASK) * CJ + b;
-    const float4 shv = s_sh[wib][(ent.x >> J_BITS) & 63u];
+    const int sj = (int)(ent & J_MASK);
+    const float4 shv = s_sh[wib][(ent >> J_BITS) & 63u];
     const float xj = pj.x - shv.x, yj = pj.y - shv.y, zj = pj.z - shv.z, qj = pj.w;
-    const unsigned mb = ent.y >> b;
-    const bool exact = (ent.x & E_EXACT) != 0u;
+    const bool masked = e0 < nm;
+    const unsigned mb = masked && e0 + lane < n ? segm[e0 + lane] : 0u;
+    const bool exact = (ent & E_EXACT) != 0u;
     const float2 *row = &s_cij[wib][0][tj];
     // j-force: even and odd i-atoms in two partial sums (the packed variant's order)
     float fjx[2] = {0.f, 0.f}, fjy[2] = {0.f, 0.f}, fjz[2] = {0.f, 0.f};
@@ -324,7 +323,7 @@ __global__ void __launch_bounds__(PF_WARPS * 32, MINB) k_pair_f(Dev d, SimConst 
 #pragma unroll
       for (int a = 0; a < CL; ++a) {
         const float4 ia = SHI ? s_i[wib][a] : make_float4(xi[a], yi[a], zi[a], qi[a]);
-        const float pen = MASKED ? ((mb & (1u << (4 * a))) ? 0.0f : MASK_PEN) : 0.0f;
+        const float pen = MASKED ? ((mb & (1u << a)) ? 0.0f : MASK_PEN) : 0.0f;
         const float dx = __fsub_rn(xj, ia.x), dy = __fsub_rn(yj, ia.y), dz = __fsub_rn(zj, ia.z);
         const float r2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmaf_rn(dx, dx, pen)));
         const float rinv = rsqrtf(r2);
@@ -346,7 +345,6 @@ __global__ void __launch_bounds__(PF_WARPS * 32, MINB) k_pair_f(Dev d, SimConst 
         fjz[a & 1] = __fmaf_rn(f, dz, fjz[a & 1]);
       }
     };
-    const bool masked = (gd >> min(e0 >> 3, 31)) & 1u;
     if (!masked) {
       one_image(std::false_type{});
     } else if (!__any_sync(0xffffffffu, exact)) {
@@ -356,7 +354,7 @@ __global__ void __launch_bounds__(PF_WARPS * 32, MINB) k_pair_f(Dev d, SimConst 
 #pragma unroll
       for (int a = 0; a < CL; ++a) {
         const float4 ia = SHI ? s_i[wib][a] : make_float4(xi[a], yi[a], zi[a], qi[a]);
-        const float pen = (mb & (1u << (4 * a))) ? 0.0f : MASK_PEN;
+        const float pen = (mb & (1u << a)) ? 0.0f : MASK_PEN;
         float dx = __fsub_rn(xj, ia.x), dy = __fsub_rn(yj, ia.y), dz = __fsub_rn(zj, ia.z);
         if (exact) {
           dx = __fmaf_rn(-L, rintf(__fmul_rn(dx, iL)), dx);

@@ -43,7 +43,6 @@ __device__ __forceinline__ void pair_cluster_f2(const Dev &d, const SimConst &c,
   const TrialInfo T = d.tinfo[t];
   if (I - T.clus0 >= d.tstate[t].n_clus) return;
   const float L = T.box, iL = T.inv_box;
-  const int g = lane >> 2, b = lane & 3;
   const int NT = c.n_types;
 
   if (lane < CL / 2) {
@@ -69,23 +68,25 @@ __device__ __forceinline__ void pair_cluster_f2(const Dev &d, const SimConst &c,
   const float2 m2krf = make_float2(-c.two_krf, -c.two_krf);
   const float rc2 = c.rc2;
 
-  const int n = d.list_n[I];
-  const uint2 *seg = d.list + (size_t)I * c.list_cap;
-  const uint32_t gd = d.gdirty[I];
-  // list entries are fetched two groups ahead; the j-atom itself at the top
-  // of its iteration (fewer live registers: a higher block count per SM hides
-  // that load better than a prefetch does)
-  uint2 ent = g < n ? seg[g] : d.idle_entry;
-  uint2 ent_n = 8 + g < n ? seg[8 + g] : d.idle_entry;
-  for (int e0 = 0; e0 < n; e0 += 8) {
-    const uint2 ent_nn = e0 + 16 + g < n ? seg[e0 + 16 + g] : d.idle_entry;
-    const int sj = (int)(ent.x & J_MASK) * CJ + b;
+  const int n = d.list_n[I], nm = d.list_nm[I];
+  const uint32_t *seg = d.list + (size_t)I * c.list_cap;
+  const uint8_t *segm = d.list_m + (size_t)I * c.list_cap;
+  // one j-atom entry per lane; entries are fetched two groups ahead, the
+  // j-atom itself at the top of its iteration (fewer live registers: a higher
+  // block count per SM hides that load better than a prefetch does)
+  uint32_t ent = lane < n ? seg[lane] : d.idle_entry;
+  uint32_t ent_n = 32 + lane < n ? seg[32 + lane] : d.idle_entry;
+  for (int e0 = 0; e0 < n; e0 += 32) {
+    const uint32_t ent_nn = e0 + 64 + lane < n ? seg[e0 + 64 + lane] : d.idle_entry;
+    const int sj = (int)(ent & J_MASK);
     const float4 pj = d.pos[sj];
     const int tj = d.type[sj];
-    const float4 shv = s_sh[wib][(ent.x >> J_BITS) & 63u];
+    const float4 shv = s_sh[wib][(ent >> J_BITS) & 63u];
     const float xj = pj.x - shv.x, yj = pj.y - shv.y, zj = pj.z - shv.z, qj = pj.w;
-    const unsigned mb = ent.y >> b;
-    const bool exact = (ent.x & E_EXACT) != 0u;
+    // the pair masks, in the groups that need them (the first nm entries)
+    const bool masked = e0 < nm;
+    const unsigned mb = masked && e0 + lane < n ? segm[e0 + lane] : 0u;
+    const bool exact = (ent & E_EXACT) != 0u;
     const float4 *row = &s_c4[wib][0][tj];
     float fjx, fjy, fjz;
     // one image per entry; MASKED: the pair masks apply (a group with
@@ -115,8 +116,8 @@ __device__ __forceinline__ void pair_cluster_f2(const Dev &d, const SimConst &c,
         tt = __ffma2_rn(qq, rinv, tt);
         tt = __fmul2_rn(tt, rinv2);
         float2 f = __ffma2_rn(qq, m2krf, tt);
-        f.x = ((!MASKED || (mb & (1u << (8 * p)))) && r2.x < rc2) ? f.x : 0.0f;
-        f.y = ((!MASKED || (mb & (1u << (8 * p + 4)))) && r2.y < rc2) ? f.y : 0.0f;
+        f.x = ((!MASKED || (mb & (1u << (2 * p)))) && r2.x < rc2) ? f.x : 0.0f;
+        f.y = ((!MASKED || (mb & (1u << (2 * p + 1)))) && r2.y < rc2) ? f.y : 0.0f;
         fx[p] = __ffma2_rn(f, dx, fx[p]);
         fy[p] = __ffma2_rn(f, dy, fy[p]);
         fz[p] = __ffma2_rn(f, dz, fz[p]);
@@ -128,7 +129,6 @@ __device__ __forceinline__ void pair_cluster_f2(const Dev &d, const SimConst &c,
       fjy = gy.x + gy.y;
       fjz = gz.x + gz.y;
     };
-    const bool masked = (gd >> min(e0 >> 3, 31)) & 1u;
     if (!masked) {
       one_image(std::false_type{});
     } else if (!__any_sync(0xffffffffu, exact)) {
@@ -143,7 +143,7 @@ __device__ __forceinline__ void pair_cluster_f2(const Dev &d, const SimConst &c,
         float2 f2v, dx2, dy2, dz2;
 #pragma unroll
         for (int hh = 0; hh < 2; ++hh) {
-          const float pen = (mb & (1u << (8 * p + 4 * hh))) ? 0.0f : MASK_PEN;
+          const float pen = (mb & (1u << (2 * p + hh))) ? 0.0f : MASK_PEN;
           float dx = __fadd_rn(xj, hh ? i0.y : i0.x), dy = __fadd_rn(yj, hh ? i0.w : i0.z),
                 dz = __fadd_rn(zj, hh ? i1.y : i1.x);
           if (exact) {

@@ -416,6 +416,7 @@ static __device__ __noinline__ unsigned list_mixed_images(const Dev &d, int I, i
 
 constexpr int LIST_WARPS = 4;
 constexpr int CAND_MAX = 1024;  // candidate 4-atom j-clusters per i-cluster (bounding-box pass)
+constexpr int ENT_MAX = 512;    // 4-atom j-clusters with a listed pair per i-cluster
 // a candidate word: the half index (J_BITS bits), the shared-image flag, the image key
 constexpr int CAND_SAME_BIT = (int)J_BITS;
 constexpr int CAND_KEY_SHIFT = (int)J_BITS + 1;
@@ -429,13 +430,28 @@ static_assert(J_BITS + 6 <= 31, "candidate word: half index, flag and a 5-bit ke
 // the entry's mask, image code and exact flag; entries are written in
 // candidate order (deterministic).  Phase 3: the i-atoms' exclusions clear
 // their bits in the written entries (found by binary search).
+// the mask column of j-atom b of a 4-atom j-cluster entry: bit a of the
+// result is bit a*4 + b of the 32-bit mask
+__device__ __forceinline__ unsigned j_column(unsigned m, int b) {
+  unsigned x = (m >> b) & 0x11111111u;
+  x = (x | (x >> 3)) & 0x03030303u;
+  x = (x | (x >> 6)) & 0x000f000fu;
+  return (x | (x >> 12)) & 0xffu;
+}
+// j-atoms of an entry with at least one listed pair
+__device__ __forceinline__ int j_columns(unsigned m) {
+  const unsigned any = m | (m >> 16);
+  const unsigned a2 = any | (any >> 8);
+  return __popc((a2 | (a2 >> 4)) & 0xfu);
+}
+
 struct ListShared {
   int s_cand[LIST_WARPS][CAND_MAX];
   int s_excl[LIST_WARPS][CL][MAX_EXCL];
   int s_nex[LIST_WARPS][CL];
   float4 s_xp[LIST_WARPS][CL / 2][2];  // i-atom pairs (2p, 2p+1): {-x, -x', -y, -y'} {-z, -z', 0, 0}
-  unsigned s_dirty[LIST_WARPS];        // groups of 8 entries that need the pair masks
-  unsigned s_mask[LIST_WARPS][512];    // masks of the entries (their first words overwrite s_cand)
+  unsigned s_dirty[LIST_WARPS][ENT_MAX / 32];  // entries whose j-atoms need the pair masks
+  unsigned s_mask[LIST_WARPS][ENT_MAX];        // masks of the entries (their first words overwrite s_cand)
 };
 
 __device__ __forceinline__ void list_cluster(const Dev &d, const SimConst &c, float rl2_bbox, ListShared &sh, int t,
@@ -618,7 +634,7 @@ __device__ __forceinline__ void list_cluster(const Dev &d, const SimConst &c, fl
     const int o = d.orig[I * CL + lane];
     s_nex[wib][lane] = o < 0 ? 0 : d.excl_n[T.sysatom0 + o];
   }
-  if (lane == 0) s_dirty[wib] = c.list_fixed ? ~0u : 0u;  // fixed-interval lists: masks everywhere
+  if (lane < ENT_MAX / 32) s_dirty[wib][lane] = c.list_fixed ? ~0u : 0u;  // fixed-interval lists: masks everywhere
   __syncwarp();
   // the slots of the i-atoms' excluded partners, all loads of the warp in flight together
   for (int k = lane; k < CL * MAX_EXCL; k += 32) {
@@ -634,7 +650,6 @@ __device__ __forceinline__ void list_cluster(const Dev &d, const SimConst &c, fl
   // every atom pair of the candidate has that q there and the rule reduces to
   // d - fl(L q) with the same rounding as the per-pair form.  Padding atoms
   // sit far outside every box and fail the distance test on that path.
-  uint2 *seg = d.list + (size_t)I * c.list_cap;
   const float rl2 = c.rl2;
   int cnt = 0;
   for (int k0 = 0; k0 < n_cand; k0 += 32) {
@@ -695,18 +710,18 @@ __device__ __forceinline__ void list_cluster(const Dev &d, const SimConst &c, fl
     const unsigned bal = __ballot_sync(0xffffffffu, mask != 0u);
     const int pos = cnt + __popc(bal & ((1u << lane) - 1u));
     __syncwarp();  // every lane has read its candidate before entries overwrite them
-    if (mask != 0u && pos < c.list_cap) {
+    if (mask != 0u && pos < ENT_MAX) {
       // entries are kept in shared memory until the exclusions are cleared:
       // the first word over the consumed candidates, the mask beside
       cand[pos] = (int)w0;
       s_mask[wib][pos] = mask;
       // the cluster with itself (pairs below the diagonal masked) and entries
       // whose pairs take images one by one need the masks in the pair kernel
-      if ((int)((w0 & J_MASK) >> 1) == I || (w0 & E_EXACT)) atomicOr(&s_dirty[wib], 1u << min(pos >> 3, 31));
+      if ((int)((w0 & J_MASK) >> 1) == I || (w0 & E_EXACT)) atomicOr(&s_dirty[wib][pos >> 5], 1u << (pos & 31));
     }
     cnt += __popc(bal);
   }
-  const int n_ent = min(cnt, c.list_cap);
+  const int n_ent = min(cnt, ENT_MAX);
   // ---- phase 3: exclusions ----
   // lane a < 8 clears, for each atom excluded from i-atom a, the bit of that
   // pair in the entry of its 4-atom j-cluster, if this list holds the pair
@@ -727,15 +742,58 @@ __device__ __forceinline__ void list_cluster(const Dev &d, const SimConst &c, fl
     }
     if (lo_e < n_ent && ((unsigned)cand[lo_e] & J_MASK) == j4) {
       atomicAnd(&s_mask[wib][lo_e], ~(1u << (a * CJ + (sj & 3))));
-      atomicOr(&s_dirty[wib], 1u << min(lo_e >> 3, 31));
+      atomicOr(&s_dirty[wib][lo_e >> 5], 1u << (lo_e & 31));
     }
   }
   __syncwarp();
-  for (int e = lane; e < n_ent; e += 32) seg[e] = make_uint2((unsigned)cand[e], s_mask[wib][e]);
+  // ---- phase 4: one entry per j-atom with a listed pair ----
+  // In entry order, j-atoms ascending; the j-atoms of entries that need the
+  // masks first, so that they fill as few groups of 32 entries as possible.
+  auto dirty_at = [&](int e) { return ((s_dirty[wib][e >> 5] >> (e & 31)) & 1u) != 0u; };
+  int n_dirty = 0;
+  for (int e0 = 0; e0 < n_ent; e0 += 32) {
+    const int e = e0 + lane;
+    const int nd = e < n_ent && dirty_at(e) ? j_columns(s_mask[wib][e]) : 0;
+    n_dirty += __reduce_add_sync(0xffffffffu, nd);
+  }
+  uint32_t *segw = d.list + (size_t)I * c.list_cap;
+  uint8_t *segm = d.list_m + (size_t)I * c.list_cap;
+  int pd = 0, pc = n_dirty;  // where the next j-atoms of either kind go
+  for (int e0 = 0; e0 < n_ent; e0 += 32) {
+    const int e = e0 + lane;
+    const unsigned m = e < n_ent ? s_mask[wib][e] : 0u;
+    const bool dirty = e < n_ent && dirty_at(e);
+    const int nj = j_columns(m);
+    const int nd = dirty ? nj : 0, nc = dirty ? 0 : nj;
+    int sd = nd, sc = nc;  // inclusive scans over the lanes
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const int vd = __shfl_up_sync(0xffffffffu, sd, off), vc = __shfl_up_sync(0xffffffffu, sc, off);
+      if (lane >= off) { sd += vd; sc += vc; }
+    }
+    int p = dirty ? pd + sd - nd : pc + sc - nc;
+    if (nj) {
+      const unsigned w = (unsigned)cand[e];
+      const unsigned s0 = (w & J_MASK) * CJ, rest = w & ~J_MASK;
+#pragma unroll
+      for (int b = 0; b < CJ; ++b) {
+        const unsigned col = j_column(m, b);
+        if (col) {
+          if (p < c.list_cap) {
+            segw[p] = (s0 + b) | rest;
+            segm[p] = (uint8_t)col;
+          }
+          ++p;
+        }
+      }
+    }
+    pd += __shfl_sync(0xffffffffu, sd, 31);
+    pc += __shfl_sync(0xffffffffu, sc, 31);
+  }
   if (lane == 0) {
-    d.gdirty[I] = s_dirty[wib];
-    d.list_n[I] = n_ent;
-    if (cnt > c.list_cap || overflow) atomicOr(d.err, ERR_LIST);
+    d.list_n[I] = min(pc, c.list_cap);
+    d.list_nm[I] = min(n_dirty, c.list_cap);
+    if (cnt > ENT_MAX || pc > c.list_cap || overflow) atomicOr(d.err, ERR_LIST);
   }
 }
 

@@ -186,12 +186,13 @@ __global__ void k_extract_pairs(Dev d, int list_cap, int trial, int32_t *pairs, 
   if (Il >= d.tstate[trial].n_clus) return;
   const int I = T.clus0 + Il;
   const int n = d.list_n[I];
-  const int a = lane >> 2, b = lane & 3;
-  const int oi = d.orig[I * CL + a];
-  for (int e = 0; e < n; ++e) {
-    const uint2 ent = d.list[(size_t)I * list_cap + e];
-    if ((ent.y >> lane) & 1u) {
-      const int oj = d.orig[(int)(ent.x & J_MASK) * CJ + b];
+  for (int e = lane; e < n; e += 32) {
+    const uint32_t ent = d.list[(size_t)I * list_cap + e];
+    const unsigned m = d.list_m[(size_t)I * list_cap + e];
+    const int oj = d.orig[(int)(ent & J_MASK)];
+    for (int a = 0; a < CL; ++a) {
+      if (!((m >> a) & 1u)) continue;
+      const int oi = d.orig[I * CL + a];
       unsigned long long k = atomicAdd(count, 1ull);
       if ((long long)k < cap) {
         pairs[2 * k] = min(oi, oj);
