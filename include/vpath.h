@@ -323,13 +323,14 @@ int sim_set_variants(sim_handle *h, int32_t pair_variant, int32_t cv_variant);
  * list build of a step sit in conditional graph nodes that the rebuild
  * front opens only when some trial rebuilds in that step (small batches,
  * where most steps rebuild nothing and those launches are pure latency).
- * All forms give bit-identical states.  SIM_EINVAL for another mode.
+ * All forms give bit-identical states.  SIM_EINVAL for another mode, and
+ * for mode 1 when the batch has more than 16 distinct LJ types.
  * sim_step_mode returns the current form.  sim_autotune_step times reps
- * chunks of nstlist steps in each form, keeps the fastest (*mode, may be NULL;
- * ms_per_step[SIM_STEP_MODES], may be NULL, receives every form's
- * milliseconds per step, indexed by mode) and restores the state it started
- * from (positions, velocities, z_m, Phi, step counter; the lists are
- * rebuilt). */
+ * chunks of nstlist steps in each form the batch can take, keeps the fastest
+ * (*mode, may be NULL; ms_per_step[SIM_STEP_MODES], may be NULL, receives
+ * every form's milliseconds per step, indexed by mode, -1 for a form not
+ * timed) and restores the state it started from (positions, velocities, z_m,
+ * Phi, step counter; the lists are rebuilt). */
 #define SIM_STEP_MODES 3
 int sim_set_step_mode(sim_handle *h, int32_t mode);
 int32_t sim_step_mode(const sim_handle *h);

@@ -1603,6 +1603,8 @@ VP_API int sim_set_step_mode(sim_handle *h, int32_t mode) {
     return fail(h, SIM_EINVAL,
                 "step mode must be 0 (kernel per phase), 1 (one kernel) or 2 (kernel per phase, rebuild kernels "
                 "only in steps with a rebuild)");
+  if (mode == 1 && h->c.n_types > SMALL_TYPES)
+    return fail(h, SIM_EINVAL, "the one-kernel step handles at most 16 distinct LJ types");
   h->fused = mode == 1;
   h->skip_empty = mode == 2;
   if (h->chunk) {
@@ -1677,6 +1679,8 @@ VP_API int sim_autotune_step(sim_handle *h, int32_t reps, int32_t *mode, double 
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   for (int m = 0; m < STEP_MODES && r == SIM_OK; ++m) {
+    if (ms_per_step) ms_per_step[m] = -1.0;
+    if (m == 1 && h->c.n_types > SMALL_TYPES) continue;  // a form this batch cannot take
     r = sim_set_step_mode(h, m);
     if (!r) r = sim_step_batch(h, nst);  // captures the chunk graph
     if (!r) {

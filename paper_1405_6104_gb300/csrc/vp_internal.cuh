@@ -18,6 +18,8 @@ constexpr int ZBINS = 16;             // z-bins of the per-column half table the
 constexpr int MAX_TRIALS = 65535;      // trials per batch (one grid row each in the per-trial kernels)
 constexpr int MAX_EXCL = 16;           // excluded partners per atom
 constexpr int MAX_TYPES = 64;          // distinct LJ types after de-duplication
+constexpr int SMALL_TYPES = 16;        // at most this many: the per-warp LJ tables of the shared-memory
+                                       // pair kernels and of the one-kernel step
 constexpr int COL_CAP = 1024;          // atoms per grid column
 constexpr float FX_SCALE = 4294967296.0f;        // fixed point: 2^32 units per kJ/mol/nm
 constexpr float FX_INV = 2.3283064365386963e-10f;  // 2^-32

@@ -15,10 +15,9 @@ __device__ __forceinline__ float3 min_disp(float4 self, float4 other, float L, f
   return make_float3((other.x - L * nx) - self.x, (other.y - L * ny) - self.y, (other.z - L * nz) - self.z);
 }
 
-// launch shape of the force-only pair kernels: warps per block, the type
-// count the packed kernels' tables hold, the penalty of a masked pair
+// launch shape of the force-only pair kernels: warps per block, the penalty
+// of a masked pair
 constexpr int PF_WARPS = 4;
-constexpr int SMALL_TYPES = 16;
 constexpr float MASK_PEN = 1.0e30f;
 
 // shared memory of the packed pair kernel's warps
@@ -39,23 +38,49 @@ __device__ __forceinline__ void pair_cluster_f2(const Dev &d, const SimConst &c,
   auto &s_red = sh.s_red;
   const int wib = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
+  const int NT = c.n_types;
   const int t = d.clus_trial[I];
+  // the loads that need only I go out before those that need the trial (one
+  // memory round trip less before the pair loop): the list's first two
+  // groups (taken only below list_n, read within the cluster's segment), the
+  // i-atoms and their types
+  const int n = d.list_n[I], nm = d.list_nm[I];
+  const uint32_t *seg = d.list + (size_t)I * c.list_cap;
+  const uint8_t *segm = d.list_m + (size_t)I * c.list_cap;
+  const uint32_t raw0 = lane < c.list_cap ? seg[lane] : d.idle_entry;
+  const uint32_t raw1 = 32 + lane < c.list_cap ? seg[32 + lane] : d.idle_entry;
+  float4 a0 = make_float4(0.f, 0.f, 0.f, 0.f), a1 = a0;
+  if (lane < CL / 2) {
+    a0 = d.pos[I * CL + 2 * lane];
+    a1 = d.pos[I * CL + 2 * lane + 1];
+  }
+  int ty[2][2] = {{0, 0}, {0, 0}};  // the i-atom types of this lane's table rows (at most two per lane)
+#pragma unroll
+  for (int r = 0; r < 2; ++r) {
+    const int k = lane + 32 * r;
+    if (k < (CL / 2) * NT) {
+      const int p = k / NT;
+      ty[r][0] = d.type[I * CL + 2 * p];
+      ty[r][1] = d.type[I * CL + 2 * p + 1];
+    }
+  }
   const TrialInfo T = d.tinfo[t];
   if (I - T.clus0 >= d.tstate[t].n_clus) return;
   const float L = T.box, iL = T.inv_box;
-  const int NT = c.n_types;
 
   if (lane < CL / 2) {
-    const float4 a0 = d.pos[I * CL + 2 * lane], a1 = d.pos[I * CL + 2 * lane + 1];
     // negated coordinates: d = xj + (-xi) in one FADD2 (a packed operand has no negate modifier)
     s_ip[wib][lane][0] = make_float4(-a0.x, -a1.x, -a0.y, -a1.y);
     s_ip[wib][lane][1] = make_float4(-a0.z, -a1.z, a0.w, a1.w);
   }
-  for (int k = lane; k < (CL / 2) * NT; k += 32) {
-    const int p = k / NT, tj = k - p * NT;
-    const int t0 = d.type[I * CL + 2 * p], t1 = d.type[I * CL + 2 * p + 1];
-    const float2 c0 = d.ljtab[t0 * NT + tj], c1 = d.ljtab[t1 * NT + tj];
-    s_c4[wib][p][tj] = make_float4(c0.y, c1.y, -c0.x, -c1.x);
+#pragma unroll
+  for (int r = 0; r < 2; ++r) {
+    const int k = lane + 32 * r;
+    if (k < (CL / 2) * NT) {
+      const int p = k / NT, tj = k - p * NT;
+      const float2 c0 = d.ljtab[ty[r][0] * NT + tj], c1 = d.ljtab[ty[r][1] * NT + tj];
+      s_c4[wib][p][tj] = make_float4(c0.y, c1.y, -c0.x, -c1.x);
+    }
   }
   for (int k = lane; k < 64; k += 32) {
     const int ix = (k & 3) - 1, iy = ((k >> 2) & 3) - 1, iz = ((k >> 4) & 3) - 1;
@@ -68,14 +93,11 @@ __device__ __forceinline__ void pair_cluster_f2(const Dev &d, const SimConst &c,
   const float2 m2krf = make_float2(-c.two_krf, -c.two_krf);
   const float rc2 = c.rc2;
 
-  const int n = d.list_n[I], nm = d.list_nm[I];
-  const uint32_t *seg = d.list + (size_t)I * c.list_cap;
-  const uint8_t *segm = d.list_m + (size_t)I * c.list_cap;
   // one j-atom entry per lane; entries are fetched two groups ahead, the
   // j-atom itself at the top of its iteration (fewer live registers: a higher
   // block count per SM hides that load better than a prefetch does)
-  uint32_t ent = lane < n ? seg[lane] : d.idle_entry;
-  uint32_t ent_n = 32 + lane < n ? seg[32 + lane] : d.idle_entry;
+  uint32_t ent = lane < n ? raw0 : d.idle_entry;
+  uint32_t ent_n = 32 + lane < n ? raw1 : d.idle_entry;
   for (int e0 = 0; e0 < n; e0 += 32) {
     const uint32_t ent_nn = e0 + 64 + lane < n ? seg[e0 + 64 + lane] : d.idle_entry;
     const int sj = (int)(ent & J_MASK);

@@ -422,14 +422,6 @@ constexpr int CAND_SAME_BIT = (int)J_BITS;
 constexpr int CAND_KEY_SHIFT = (int)J_BITS + 1;
 static_assert(J_BITS + 6 <= 31, "candidate word: half index, flag and a 5-bit key in a non-negative int");
 
-// One warp per i-cluster.  Phase 1: lanes test columns, then the 4-atom
-// halves of the clusters of each passing column, against the i-cluster's
-// bounding box and collect the candidates in order (column-major, then z,
-// i.e. ascending j-cluster index).  Phase 2: each lane takes one candidate
-// and evaluates the FP32 list rule for all 8 x 4 atom pairs itself, giving
-// the entry's mask, image code and exact flag; entries are written in
-// candidate order (deterministic).  Phase 3: the i-atoms' exclusions clear
-// their bits in the written entries (found by binary search).
 // the mask column of j-atom b of a 4-atom j-cluster entry: bit a of the
 // result is bit a*4 + b of the 32-bit mask
 __device__ __forceinline__ unsigned j_column(unsigned m, int b) {
@@ -445,6 +437,15 @@ __device__ __forceinline__ int j_columns(unsigned m) {
   return __popc((a2 | (a2 >> 4)) & 0xfu);
 }
 
+// One warp per i-cluster.  Phase 1: lanes test columns, then the 4-atom
+// halves of the clusters of each passing column, against the i-cluster's
+// bounding box and collect the candidates in order (column-major, then z,
+// i.e. ascending j-cluster index).  Phase 2: each lane takes one candidate
+// and evaluates the FP32 list rule for all 8 x 4 atom pairs itself, giving
+// the entry's mask, image code and exact flag; entries are written in
+// candidate order (deterministic).  Phase 3: the i-atoms' exclusions clear
+// their bits in the entries (found by binary search).  Phase 4: one list
+// entry per j-atom with a listed pair is written out.
 struct ListShared {
   int s_cand[LIST_WARPS][CAND_MAX];
   int s_excl[LIST_WARPS][CL][MAX_EXCL];
@@ -764,14 +765,16 @@ __device__ __forceinline__ void list_cluster(const Dev &d, const SimConst &c, fl
     const unsigned m = e < n_ent ? s_mask[wib][e] : 0u;
     const bool dirty = e < n_ent && dirty_at(e);
     const int nj = j_columns(m);
-    const int nd = dirty ? nj : 0, nc = dirty ? 0 : nj;
-    int sd = nd, sc = nc;  // inclusive scans over the lanes
+    // inclusive scan over the lanes of both counts at once (16 bits each)
+    const int own = dirty ? nj : nj << 16;
+    int sdc = own;
 #pragma unroll
     for (int off = 1; off < 32; off <<= 1) {
-      const int vd = __shfl_up_sync(0xffffffffu, sd, off), vc = __shfl_up_sync(0xffffffffu, sc, off);
-      if (lane >= off) { sd += vd; sc += vc; }
+      const int v = __shfl_up_sync(0xffffffffu, sdc, off);
+      if (lane >= off) sdc += v;
     }
-    int p = dirty ? pd + sd - nd : pc + sc - nc;
+    const int before = sdc - own;
+    int p = dirty ? pd + (before & 0xffff) : pc + (before >> 16);
     if (nj) {
       const unsigned w = (unsigned)cand[e];
       const unsigned s0 = (w & J_MASK) * CJ, rest = w & ~J_MASK;
@@ -787,8 +790,9 @@ __device__ __forceinline__ void list_cluster(const Dev &d, const SimConst &c, fl
         }
       }
     }
-    pd += __shfl_sync(0xffffffffu, sd, 31);
-    pc += __shfl_sync(0xffffffffu, sc, 31);
+    const int tot = __shfl_sync(0xffffffffu, sdc, 31);
+    pd += tot & 0xffff;
+    pc += tot >> 16;
   }
   if (lane == 0) {
     d.list_n[I] = min(pc, c.list_cap);

@@ -119,7 +119,9 @@ def test_bonded_forces_alone(name):
 def test_many_lj_types_take_the_general_kernel():
     """More distinct Lennard-Jones types than the packed kernels' tables hold
     (16): the general pair kernel runs, with the same parity to the oracle,
-    and graph replay and direct launches stay bit-identical."""
+    and graph replay and direct launches stay bit-identical; the one-kernel
+    step (whose tables hold 16 types) is refused, and the step-form
+    autotuner leaves it out."""
     s, p = S.small_solvated()
     s = s.copy()
     k = np.arange(s.n_solute) % 30
@@ -138,8 +140,14 @@ def test_many_lj_types_take_the_general_kernel():
             Fr, er = oracle_total_force(s, q, pos, cv[2])
             assert rel_rms(F, Fr) < 1e-5
             results.append([b.get_state(t) for t in range(2)])
+            with pytest.raises(B.SimError) as err:
+                B.sim_set_step_mode(b.h, 1)
+            assert err.value.code == B.SIM_EINVAL
     for x, y in zip(*results):
         assert np.array_equal(x[0], y[0]) and np.array_equal(x[1], y[1])
+    with B.TrialBatch(s, p, [2], trial_seeds=[21, 22]) as b:
+        mode, ms = B.sim_autotune_step(b.h, 1, times=True)
+        assert mode in (0, 2) and ms[1] < 0 and ms[0] > 0 and ms[2] > 0
 
 
 @pytest.mark.parametrize("name", ["tiny", "small"])
