@@ -47,8 +47,11 @@ __device__ __forceinline__ void pair_cluster_f2(const Dev &d, const SimConst &c,
   const int n = d.list_n[I], nm = d.list_nm[I];
   const uint32_t *seg = d.list + (size_t)I * c.list_cap;
   const uint8_t *segm = d.list_m + (size_t)I * c.list_cap;
-  const uint32_t raw0 = lane < c.list_cap ? seg[lane] : d.idle_entry;
-  const uint32_t raw1 = 32 + lane < c.list_cap ? seg[32 + lane] : d.idle_entry;
+  // the list words stream through L2 (the batch's lists are larger than L2)
+  // with the evict-first hint, so that they do not push out the positions
+  // and force accumulators every lane keeps coming back to
+  const uint32_t raw0 = lane < c.list_cap ? __ldcs(seg + lane) : d.idle_entry;
+  const uint32_t raw1 = 32 + lane < c.list_cap ? __ldcs(seg + 32 + lane) : d.idle_entry;
   float4 a0 = make_float4(0.f, 0.f, 0.f, 0.f), a1 = a0;
   if (lane < CL / 2) {
     a0 = d.pos[I * CL + 2 * lane];
@@ -99,7 +102,7 @@ __device__ __forceinline__ void pair_cluster_f2(const Dev &d, const SimConst &c,
   uint32_t ent = lane < n ? raw0 : d.idle_entry;
   uint32_t ent_n = 32 + lane < n ? raw1 : d.idle_entry;
   for (int e0 = 0; e0 < n; e0 += 32) {
-    const uint32_t ent_nn = e0 + 64 + lane < n ? seg[e0 + 64 + lane] : d.idle_entry;
+    const uint32_t ent_nn = e0 + 64 + lane < n ? __ldcs(seg + e0 + 64 + lane) : d.idle_entry;
     const int sj = (int)(ent & J_MASK);
     const float4 pj = d.pos[sj];
     const int tj = d.type[sj];
