@@ -34,23 +34,26 @@ BYTES_PER_ATOM_STEP = 1224.0         # 112 B of state + 278 int32 half-list entr
 PAIRS_PER_ATOM_STEP = 209.0          # half pairs inside r_cut = 1.0 nm
 FLOPS_PER_PAIR = 35.0                # LJ + reaction field, FP32
 # DRAM traffic of one pair-kernel launch on this workload (dram__bytes_read.sum +
-# dram__bytes_write.sum of one ncu capture, variant 8) and the sources it was
-# taken on (the kernel and its headers): reported as roofline.traffic only
-# while those sources are unchanged
-PAIR_TRAFFIC = {"bytes": 209.562112e6 + 12.741632e6, "variant": 8,
+# dram__bytes_write.sum of one ncu capture) per captured variant, and the
+# sources it was taken on (the kernel and its headers): reported as
+# roofline.traffic only for the variant the run timed and while those sources
+# are unchanged
+PAIR_TRAFFIC = {"bytes": {7: 209.478144e6 + 7.621120e6},
                 "sources": ["vp_pair.cu", "vp_pair_dev.cuh", "vp_internal.cuh", "vp_dev.cuh"],
-                "source_sha256": "beed35c6e90e2c10b354d00b7d07139d021810715c6ceefc88bdf3ef616af4e3"}
+                "source_sha256": "86bf29a2be4c3f89a6b649ade11c513d8430aa27292543f9b5049b829ba28b94"}
 
 
-def pair_traffic():
+def pair_traffic(variant):
     import hashlib
+    if variant not in PAIR_TRAFFIC["bytes"]:
+        return None
     h = hashlib.sha256()
     try:
         for f in PAIR_TRAFFIC["sources"]:
             h.update(open(os.path.join(ROOT, "paper_1405_6104_gb300", "csrc", f), "rb").read())
     except OSError:
         return None
-    return PAIR_TRAFFIC["bytes"] if h.hexdigest() == PAIR_TRAFFIC["source_sha256"] else None
+    return PAIR_TRAFFIC["bytes"][variant] if h.hexdigest() == PAIR_TRAFFIC["source_sha256"] else None
 
 
 def rank_info():
@@ -397,8 +400,8 @@ def run_gpu(args):
                                      "timed_form": B.STEP_FORM_NAMES[timed_form]},
                        "l2": "working set > L2 (lists + state ~0.5 GB)"},
             "roofline": {"bound": "alu", "kernel": "pair", "achieved": achieved / 1e12, "peak": fp32_peak / 1e12,
-                         "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": pair_traffic(),
-                         "traffic_unit": "bytes per launch (ncu, variant 8)",
+                         "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": pair_traffic(tuned[0]),
+                         "traffic_unit": f"bytes per launch (ncu, variant {tuned[0]})",
                          "launch_ms": pair_avg_s * 1e3, "launches_timed": pair_n,
                          "launch_timing": "event-record nodes around each pair launch inside the replayed graphs of the timed region",
                          "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz (SM max clock: {src})",
