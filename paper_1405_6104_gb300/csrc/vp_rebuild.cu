@@ -1,5 +1,6 @@
 // vp_rebuild.cu -- cell binning, spatial sort into 8-atom clusters and the
-// cluster-pair Verlet list of the trials whose list is due.
+// Verlet list (8-atom i-clusters, one entry per j-atom) of the trials whose
+// list is due.
 //
 // Every kernel here runs in every step and works only on the trials whose
 // list is due in that step: the front kernel (one block per trial) decides,
@@ -15,11 +16,12 @@
 //
 // Layout: per trial the box is cut into ncol x ncol columns along x and y;
 // atoms are sorted by (column, z) and cut into clusters of 8 (the last
-// cluster of a column is padded).  A list entry pairs an 8-atom i-cluster
-// with a 4-atom j-cluster (half of an i-cluster) and carries a 32-bit mask of
-// the atom pairs that satisfy the FP32 list rule and are not excluded; the
-// half list keeps j-clusters whose parent cluster index is >= the i-cluster
-// (upper triangle inside a cluster).
+// cluster of a column is padded).  The list build tests 4-atom j-clusters
+// (halves of i-clusters) against each 8-atom i-cluster and writes one list
+// entry per j-atom with at least one pair that satisfies the FP32 list rule
+// and is not excluded, with an 8-bit mask of those pairs; the half list keeps
+// j-clusters whose parent cluster index is >= the i-cluster (upper triangle
+// inside a cluster).
 #include <algorithm>
 
 #include "vp_dev.cuh"
